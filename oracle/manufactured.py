@@ -1,0 +1,151 @@
+"""Manufactured solution u_A, L2 projection and error norms (FP64).
+
+Test infrastructure only (see ``oracle/__init__.py``).
+
+Section "Numerical code verification with manufactured solution": for
+eps = mu = 1 the six-component fields u^1, u^2, u^3 (indices kappa, lambda)
+are exact source-free solutions on (0,1)^3, and
+u_A = gamma u^1_{1,1} + 2 gamma u^2_{1,1} + 3 gamma u^3_{1,1}, gamma = 2/sqrt(14),
+so that ||u_A(., 0)||_{L2} = 1.  As printed, u^2 carries the opposite sign of
+its H components (it solves dH/dt = +curl E); the reading used here negates
+that H part, which makes u^2 -- and so u_A -- an exact solution of the paper's
+equations.  The paper reports, on 16^3 elements over
+t in [0, 1], L2 errors below 0.08 (tau = 1/10) and 0.0002 (tau = 1/1280) and
+H(curl) errors below 0.35 and 0.015.  The norm reading used here: for each time
+level, ||E_h - E||_{L2} and ||H_h - H||_{L2} separately (and the H(curl) norm
+(||e||^2 + ||curl e||^2)^(1/2)), evaluated by Gauss quadrature with p + 3 points
+per element; the bound must hold at every time level.
+
+Pins: ``||u_A(.,0)|| = 1`` by quadrature (closed form of the paper), curl and
+time-derivative identities of u_A checked by finite differences
+(tests/test_oracle_manufactured.py), and the error bounds themselves.
+"""
+from functools import lru_cache
+
+import numpy as np
+
+from . import bspline
+from .banded import apply_1d, solve_lines
+from .maxwell_adi import E_DIRICHLET, H_DIRICHLET
+
+GAMMA = 2.0 / np.sqrt(14.0)
+
+
+def _mode(kind, kap, lam, x1, x2, x3, t):
+    """Six components of u^kind_{kap,lam} at points (x1, x2, x3) and time t."""
+    w = np.sqrt(kap * kap + lam * lam)
+    ct = np.cos(w * np.pi * t)
+    st = np.sin(w * np.pi * t)
+    z = np.zeros(np.broadcast(x1, x2, x3).shape)
+    if kind == 1:
+        a, b = x2, x3
+    elif kind == 2:
+        a, b = x1, x3
+    else:
+        a, b = x1, x2
+    s_ab = np.sin(kap * np.pi * a) * np.sin(lam * np.pi * b) * ct
+    h1 = -lam / w * np.sin(kap * np.pi * a) * np.cos(lam * np.pi * b) * st
+    h2 = kap / w * np.cos(kap * np.pi * a) * np.sin(lam * np.pi * b) * st
+    if kind == 1:
+        return [s_ab + z, z, z, z, h1 + z, h2 + z]
+    if kind == 2:
+        # As printed, u^2 has H = (h1, 0, h2), which satisfies dH/dt = +curl E
+        # and dE/dt = -curl H: the opposite orientation of the paper's own
+        # Maxwell system (u^1 and u^3 do satisfy it).  The exact solution of
+        # that system is the printed one with its H part negated.
+        return [z, s_ab + z, z, -h1 + z, z, -h2 + z]
+    return [z, z, s_ab + z, h1 + z, h2 + z, z]
+
+
+def u_A(x1, x2, x3, t):
+    """The paper's first manufactured solution (6 components)."""
+    out = [np.zeros(np.broadcast(x1, x2, x3).shape) for _ in range(6)]
+    for kind, wgt in ((1, 1.0), (2, 2.0), (3, 3.0)):
+        m = _mode(kind, 1, 1, x1, x2, x3, t)
+        for i in range(6):
+            out[i] = out[i] + GAMMA * wgt * m[i]
+    return out
+
+
+@lru_cache(maxsize=16)
+def _quad_grid(n, p, extra):
+    return _build_grid(n, p, extra)
+
+
+def quad_grid(n, p, extra=3):
+    return _quad_grid(tuple(n), p, extra)
+
+
+def _build_grid(n, p, extra):
+    """Tensor Gauss grid with p+extra points per element: per-axis (x, w, B, B')."""
+    ax = []
+    for ne in n:
+        x, w, e = bspline.gauss_points(ne, p + extra)
+        v, d = bspline.eval_basis(ne, p, x, e)
+        ax.append((x, w, v, d))
+    return ax  # order x, y, z
+
+
+def evaluate(u, grid, deriv=(0, 0, 0)):
+    """Field with coefficients u (Nz, Ny, Nx) at the quadrature grid (qz, qy, qx)."""
+    gx, gy, gz = grid
+    Bx = gx[3] if deriv[0] else gx[2]
+    By = gy[3] if deriv[1] else gy[2]
+    Bz = gz[3] if deriv[2] else gz[2]
+    return apply_1d(Bx, apply_1d(By, apply_1d(Bz, u, "z"), "y"), "x")
+
+
+def project(funcs, n, p, mats):
+    """L2 projection of the 6 component functions f(x1, x2, x3) onto the
+    B-spline space with the boundary constraints of each component."""
+    grid = quad_grid(n, p)
+    gx, gy, gz = grid
+    X3, X2, X1 = np.meshgrid(gz[0], gy[0], gx[0], indexing="ij")
+    W = np.einsum("k,j,i->kji", gz[1], gy[1], gx[1])
+    vals = funcs(X1, X2, X3)
+    out = []
+    for i in range(6):
+        f = vals[i] * W
+        rhs = apply_1d(gx[2].T, apply_1d(gy[2].T, apply_1d(gz[2].T, f, "z"), "y"), "x")
+        dirs = E_DIRICHLET[i] if i < 3 else H_DIRICHLET[i - 3]
+        u = rhs
+        for ax in ("x", "y", "z"):
+            u = solve_lines(mats[ax][0], u, ax, p, ax in dirs)
+        out.append(u)
+    return out
+
+
+def errors(state, n, p, t, exact=u_A):
+    """(L2 error of E, L2 error of H, H(curl) error of E, H(curl) error of H)."""
+    grid = quad_grid(n, p)
+    gx, gy, gz = grid
+    X3, X2, X1 = np.meshgrid(gz[0], gy[0], gx[0], indexing="ij")
+    W = np.einsum("k,j,i->kji", gz[1], gy[1], gx[1])
+    ex = exact(X1, X2, X3, t)
+    # exact curls by centred differences would add error; use the analytic
+    # identity curl E = -dH/dt and curl H = dE/dt (eps = mu = 1), both exact
+    # for u_A, evaluated by a tiny symmetric difference in time.
+    dt = 1e-6
+    ex_p = exact(X1, X2, X3, t + dt)
+    ex_m = exact(X1, X2, X3, t - dt)
+    dexdt = [(a - b) / (2 * dt) for a, b in zip(ex_p, ex_m)]
+    res = []
+    for f0 in (0, 3):
+        uh = [evaluate(state[f0 + i], grid) for i in range(3)]
+        l2 = sum(np.sum(W * (uh[i] - ex[f0 + i]) ** 2) for i in range(3))
+        d = lambda i, ax: evaluate(state[f0 + i], grid, tuple(int(ax == k) for k in range(3)))
+        curl_h = (d(2, 1) - d(1, 2), d(0, 2) - d(2, 0), d(1, 0) - d(0, 1))
+        if f0 == 0:   # curl E = -dH/dt
+            curl_ex = [-dexdt[3 + i] for i in range(3)]
+        else:         # curl H = dE/dt
+            curl_ex = [dexdt[i] for i in range(3)]
+        cl = sum(np.sum(W * (curl_h[i] - curl_ex[i]) ** 2) for i in range(3))
+        res.append((np.sqrt(l2), np.sqrt(l2 + cl)))
+    return res[0][0], res[1][0], res[0][1], res[1][1]
+
+
+def l2_norm(state, n, p, comps=range(6)):
+    grid = quad_grid(n, p)
+    gx, gy, gz = grid
+    W = np.einsum("k,j,i->kji", gz[1], gy[1], gx[1])
+    return np.sqrt(sum(np.sum(W * evaluate(state[i], grid) ** 2) for i in comps))

@@ -1,0 +1,225 @@
+"""One ADI time step of the IGA-FEM Maxwell scheme (FP64 reference).
+
+Test infrastructure only (see ``oracle/__init__.py``).
+
+The time scheme is eqs. (scheme1a)-(scheme1d): two half steps, each implicit in
+one part of the split curl C1 - C2.  After discretisation with B-splines each
+E half step is eq. (discrete1) / (discrete3) and each H half step eq.
+(discrete2) / (discrete4), with the block matrices M, K1, K2, R1, R2, C1, C2
+written out after eq. (discrete4).  Row-wise material follows section
+"Incorporating non-regular material data": every row rst uses the row's
+coefficients a, b, c, d (``oracle.material``).  Readings of the paper taken here:
+
+* C2's third row is M(x)A(x)M (the d/dx2 of the curl split), not M(x)M(x)A.
+* In eq. (discrete4) the C1 term carries a minus sign, as in eq. (scheme1d)
+  and eq. (strong4).
+* The left-hand side of each E component is row-scaled M + c S in one direction
+  (its "stiffness" direction) and M in the other two.  As in the Appendix
+  (eqs. split1, split2) the direction that carries the material is solved first,
+  then the two mass directions.
+* Boundary conditions E x n = 0, H . n = 0: E_i has zero first and last
+  B-spline coefficients in the two directions other than i, H_i in direction i.
+* The current source -J enters the E rows as -b (J, B_rst) at the midpoint
+  time of each half step, t_n + tau/4 and t_n + 3 tau/4.
+
+Components are ordered (E1, E2, E3, H1, H2, H3), each an array (Nz, Ny, Nx).
+
+Pins: tests/test_oracle_bruteforce.py (one sub-step equals a dense solve of the
+full system assembled by 3D quadrature from the weak form, uniform and
+heterogeneous material), tests/test_oracle_manufactured.py (the paper's L2 and
+H(curl) error bounds for u_A and second order in tau), tests/test_oracle_
+stability.py (bounded energy at tau far above the explicit limit).
+"""
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import bspline
+from .banded import kron3, solve_lines
+from . import material
+
+# direction of the stiffness (material) solve of E_i in half step 1 and 2
+STIFF_DIR = {1: ("y", "z", "x"), 2: ("z", "x", "y")}
+# Dirichlet directions: E_i is tangential-constrained in the two directions != i
+E_DIRICHLET = ({"y", "z"}, {"x", "z"}, {"x", "y"})
+H_DIRICHLET = ({"x"}, {"y"}, {"z"})
+
+
+@dataclass
+class Problem:
+    n: tuple                # (nx, ny, nz) elements
+    p: int                  # B-spline degree
+    tau: float              # time step
+    a: np.ndarray           # row coefficients, shape (Nz, Ny, Nx)
+    b: np.ndarray
+    c: np.ndarray
+    d: np.ndarray
+    mats: dict = field(default_factory=dict)   # axis -> (M, S, A, B)
+    source: dict = None     # point source (see set_source)
+
+    @property
+    def shape(self):
+        nx, ny, nz = self.n
+        p = self.p
+        return (nz + p, ny + p, nx + p)
+
+
+def make_problem(n, p, tau, eps=None, mu=None, sigma=None):
+    """Build the 1D matrices and the per-row coefficients.
+
+    eps, mu, sigma: per-element arrays (nz, ny, nx) or None for 1, 1, 0.
+    """
+    nx, ny, nz = n
+    shp_e = (nz, ny, nx)
+    eps = np.ones(shp_e) if eps is None else np.asarray(eps, dtype=np.float64)
+    mu = np.ones(shp_e) if mu is None else np.asarray(mu, dtype=np.float64)
+    sigma = np.zeros(shp_e) if sigma is None else np.asarray(sigma, dtype=np.float64)
+    eh = material.row_hats(eps, n, p)
+    mh = material.row_hats(mu, n, p)
+    sh = material.row_hats(sigma, n, p)
+    a, b, c, d = material.coefficients(eh, mh, sh, tau)
+    mats = {"x": bspline.matrices_1d(nx, p), "y": bspline.matrices_1d(ny, p),
+            "z": bspline.matrices_1d(nz, p)}
+    return Problem(n=tuple(n), p=p, tau=tau, a=a, b=b, c=c, d=d, mats=mats)
+
+
+def set_source(prob, x0, comp, amp, f0, t0, s):
+    """Point dipole J = amp g(t) delta(x - x0) e_comp, comp in {0, 1, 2}.
+
+    (J_comp, B_rst) = amp g(t) B_r(x0) B_s(y0) B_t(z0),
+    g(t) = sin(2 pi f0 (t - t0)) exp(-((t - t0) / s)^2).
+    """
+    nx, ny, nz = prob.n
+    wx = bspline.point_values(nx, prob.p, x0[0])
+    wy = bspline.point_values(ny, prob.p, x0[1])
+    wz = bspline.point_values(nz, prob.p, x0[2])
+    prob.source = dict(w=np.einsum("k,j,i->kji", wz, wy, wx), comp=comp, amp=amp,
+                       f0=f0, t0=t0, s=s)
+
+
+def source_profile(src, t):
+    return np.sin(2 * np.pi * src["f0"] * (t - src["t0"])) * np.exp(-((t - src["t0"]) / src["s"]) ** 2)
+
+
+def _K(prob, ops, u):
+    """Kronecker term: ops = (X, Y, Z) names among 'M', 'S', 'A', 'B'."""
+    idx = {"M": 0, "S": 1, "A": 2, "B": 3}
+    X = prob.mats["x"][idx[ops[0]]]
+    Y = prob.mats["y"][idx[ops[1]]]
+    Z = prob.mats["z"][idx[ops[2]]]
+    return kron3(X, Y, Z, u)
+
+
+def rhs_E(prob, half, E, H, t_mid):
+    """Right-hand sides of the E rows, eq. (dupa1ab) for half step 1 (R1) and
+    the analogous rows of eq. (discrete3) for half step 2 (R2), row-scaled."""
+    E1, E2, E3 = E
+    H1, H2, H3 = H
+    a, b, c = prob.a, prob.b, prob.c
+    curl = (
+        -_K(prob, "MMA", H2) + _K(prob, "MAM", H3),
+        _K(prob, "MMA", H1) - _K(prob, "AMM", H3),
+        -_K(prob, "MAM", H1) + _K(prob, "AMM", H2),
+    )
+    if half == 1:   # R1 = [[0, A(x)B(x)M, 0], [0, 0, M(x)A(x)B], [B(x)M(x)A, 0, 0]]
+        cross = (_K(prob, "ABM", E2), _K(prob, "MAB", E3), _K(prob, "BMA", E1))
+    else:           # R2 = [[0, 0, A(x)M(x)B], [B(x)A(x)M, 0, 0], [0, M(x)B(x)A, 0]]
+        cross = (_K(prob, "AMB", E3), _K(prob, "BAM", E1), _K(prob, "MBA", E2))
+    out = []
+    for i, Ei in enumerate(E):
+        r = a * _K(prob, "MMM", Ei) + b * curl[i] + c * cross[i]
+        if prob.source is not None and prob.source["comp"] == i:
+            src = prob.source
+            r = r - b * src["amp"] * source_profile(src, t_mid) * src["w"]
+        out.append(r)
+    return out
+
+
+def solve_E(prob, half, rhs):
+    """Stiffness direction first (row-scaled M + c S), then the two mass
+    directions (Appendix, eqs. split1 and split2)."""
+    out = []
+    for i in range(3):
+        sd = STIFF_DIR[half][i]
+        dirs = [sd] + [ax for ax in ("x", "y", "z") if ax != sd]
+        u = rhs[i]
+        for k, ax in enumerate(dirs):
+            M, S, _, _ = prob.mats[ax]
+            dch = ax in E_DIRICHLET[i]
+            if k == 0:
+                u = solve_lines(M, u, ax, prob.p, dch, stiff=S, coef=prob.c)
+            else:
+                u = solve_lines(M, u, ax, prob.p, dch)
+        out.append(u)
+    return out
+
+
+def rhs_H(prob, H, E_alpha, E_beta):
+    """RHS of M H_new = M H_old - d C1 E_alpha + d C2 E_beta.
+
+    Half step 1 (eq. discrete2): alpha = E^n, beta = E^{n+1/2}.
+    Half step 2 (eq. discrete4, minus sign on C1): alpha = E^{n+1}, beta = E^{n+1/2}.
+    C1 = [[0,0,MAM],[MMA,0,0],[0,AMM,0]], C2 = [[0,MMA,0],[0,0,AMM],[MAM,0,0]].
+    """
+    H1, H2, H3 = H
+    Ea1, Ea2, Ea3 = E_alpha
+    Eb1, Eb2, Eb3 = E_beta
+    d = prob.d
+    C1 = (_K(prob, "MAM", Ea3), _K(prob, "MMA", Ea1), _K(prob, "AMM", Ea2))
+    C2 = (_K(prob, "MMA", Eb2), _K(prob, "AMM", Eb3), _K(prob, "MAM", Eb1))
+    return [_K(prob, "MMM", H[i]) + d * (-C1[i] + C2[i]) for i in range(3)]
+
+
+def solve_H(prob, rhs):
+    out = []
+    for i in range(3):
+        u = rhs[i]
+        for ax in ("x", "y", "z"):
+            M = prob.mats[ax][0]
+            u = solve_lines(M, u, ax, prob.p, ax in H_DIRICHLET[i])
+        out.append(u)
+    return out
+
+
+def step(prob, state, t):
+    """One full step: (E^n, H^n) at time t -> (E^{n+1}, H^{n+1})."""
+    E = state[:3]
+    H = state[3:]
+    tau = prob.tau
+    E_half = solve_E(prob, 1, rhs_E(prob, 1, E, H, t + 0.25 * tau))
+    H_half = solve_H(prob, rhs_H(prob, H, E, E_half))
+    E_new = solve_E(prob, 2, rhs_E(prob, 2, E_half, H_half, t + 0.75 * tau))
+    H_new = solve_H(prob, rhs_H(prob, H_half, E_new, E_half))
+    return E_new + H_new
+
+
+def run(prob, state, t0, nsteps):
+    state = [np.array(u, dtype=np.float64) for u in state]
+    t = t0
+    for _ in range(nsteps):
+        state = step(prob, state, t)
+        t += prob.tau
+    return state, t
+
+
+def zero_state(prob):
+    return [np.zeros(prob.shape) for _ in range(6)]
+
+
+def apply_dirichlet(state):
+    """Zero the constrained boundary coefficients (E_i tangential, H_i normal)."""
+    out = []
+    for i, u in enumerate(state):
+        u = np.array(u, dtype=np.float64)
+        dirs = E_DIRICHLET[i] if i < 3 else H_DIRICHLET[i - 3]
+        if "x" in dirs:
+            u[:, :, 0] = 0.0
+            u[:, :, -1] = 0.0
+        if "y" in dirs:
+            u[:, 0, :] = 0.0
+            u[:, -1, :] = 0.0
+        if "z" in dirs:
+            u[0, :, :] = 0.0
+            u[-1, :, :] = 0.0
+        out.append(u)
+    return out

@@ -1,0 +1,153 @@
+"""Dense brute-force assembly of one ADI sub-step on tiny meshes (test helper).
+
+Independent of the oracle's code: the basis comes from scipy.interpolate.BSpline,
+every integral is a sum over a full 3D Gauss grid (no Kronecker factorisation),
+and the rows are written straight from the weak forms (weak1)-(weak4) of the
+paper with per-row coefficients a, b, c, d:
+
+  E rows, half step 1:
+    (E1,V1) + c (d2 E1, d2 V1) = a (E1o,V1) + b (-d3 H2 + d2 H3, V1) + c (d1 E2o, d2 V1) - b (J1,V1)
+    (E2,V2) + c (d3 E2, d3 V2) = a (E2o,V2) + b ( d3 H1 - d1 H3, V2) + c (d2 E3o, d3 V2) - b (J2,V2)
+    (E3,V3) + c (d1 E3, d1 V3) = a (E3o,V3) + b (-d2 H1 + d1 H2, V3) + c (d3 E1o, d1 V3) - b (J3,V3)
+  E rows, half step 2: stiffness derivative d3, d1, d2 and cross terms
+    (d1 E3o, d3 V1), (d2 E1o, d1 V2), (d3 E2o, d2 V3).
+  H rows: (H_new, V) = (H_old, V) - d (C1 E_alpha, V) + d (C2 E_beta, V),
+    C1 E = (d2 E3, d3 E1, d1 E2), C2 E = (d3 E2, d1 E3, d2 E1).
+
+The full system is solved with numpy.linalg.solve on the unconstrained DOFs.
+"""
+import numpy as np
+from scipy.interpolate import BSpline
+
+
+def _basis_1d(n, p, x):
+    t = np.concatenate([np.zeros(p), np.linspace(0, 1, n + 1), np.ones(p)])
+    N = n + p
+    v = np.zeros((len(x), N))
+    d = np.zeros((len(x), N))
+    for i in range(N):
+        c = np.zeros(N)
+        c[i] = 1.0
+        s = BSpline(t, c, p, extrapolate=False)
+        v[:, i] = np.nan_to_num(s(x))
+        d[:, i] = np.nan_to_num(s.derivative()(x))
+    return v, d
+
+
+def _gauss(n, q):
+    g, w = np.polynomial.legendre.leggauss(q)
+    h = 1.0 / n
+    x = np.concatenate([(e + 0.5) * h + 0.5 * h * g for e in range(n)])
+    ww = np.concatenate([0.5 * h * w] * n)
+    return x, ww
+
+
+class Dense3D:
+    """Dense 3D operators on the tensor B-spline space of (nx, ny, nz), p."""
+
+    def __init__(self, n, p):
+        self.n, self.p = n, p
+        nx, ny, nz = n
+        self.N = (nx + p, ny + p, nz + p)
+        q = p + 2
+        (x, wx), (y, wy), (z, wz) = _gauss(nx, q), _gauss(ny, q), _gauss(nz, q)
+        vx, dx = _basis_1d(nx, p, x)
+        vy, dy = _basis_1d(ny, p, y)
+        vz, dz = _basis_1d(nz, p, z)
+        # index order (k, j, i) with i (x) fastest, points (qz, qy, qx)
+        self.W = np.kron(np.kron(wz, wy), wx)
+        self.phi = np.kron(np.kron(vz, vy), vx)
+        self.grad = (np.kron(np.kron(vz, vy), dx),   # d/dx1
+                     np.kron(np.kron(vz, dy), vx),   # d/dx2
+                     np.kron(np.kron(dz, vy), vx))   # d/dx3
+        self.pts = (x, y, z)
+        self.vals1d = (vx, vy, vz)
+
+    def inner(self, test_deriv, trial_deriv):
+        """G[row, col] = int D_test B_row D_trial B_col (None = no derivative)."""
+        T = self.phi if test_deriv is None else self.grad[test_deriv]
+        U = self.phi if trial_deriv is None else self.grad[trial_deriv]
+        return T.T @ (self.W[:, None] * U)
+
+    def free(self, dirs):
+        """Mask of unconstrained DOFs for Dirichlet directions ``dirs`` (0,1,2)."""
+        Nx, Ny, Nz = self.N
+        k, j, i = np.meshgrid(np.arange(Nz), np.arange(Ny), np.arange(Nx), indexing="ij")
+        m = np.ones((Nz, Ny, Nx), dtype=bool)
+        for d, idx, Nd in ((0, i, Nx), (1, j, Ny), (2, k, Nz)):
+            if d in dirs:
+                m &= (idx > 0) & (idx < Nd - 1)
+        return m.ravel()
+
+    def point_row(self, x0):
+        """B_rst(x0) for all rst (flattened)."""
+        out = []
+        for d in range(3):
+            v, _ = _basis_1d(self.n[d], self.p, np.array([x0[d]]))
+            out.append(v[0])
+        return np.kron(np.kron(out[2], out[1]), out[0])
+
+    def hat(self, elem_field):
+        """int f B_rst / int B_rst for a per-element field (nz, ny, nx)."""
+        nx, ny, nz = self.n
+        q = self.p + 2
+        ex = np.repeat(np.arange(nx), q)
+        ey = np.repeat(np.arange(ny), q)
+        ez = np.repeat(np.arange(nz), q)
+        fq = elem_field[ez[:, None, None], ey[None, :, None], ex[None, None, :]].ravel()
+        num = self.phi.T @ (self.W * fq)
+        den = self.phi.T @ self.W
+        return (num / den).reshape(self.N[2], self.N[1], self.N[0])
+
+
+E_DIR = ((1, 2), (0, 2), (0, 1))
+H_DIR = ((0,), (1,), (2,))
+
+
+def e_substep(D, half, E, H, a, b, c, J=None):
+    """Dense solve of the E rows of half step ``half``; returns (E1, E2, E3)."""
+    f = lambda u: np.asarray(u).ravel()
+    a, b, c = f(a), f(b), f(c)
+    mass = D.inner(None, None)
+    E = [f(u) for u in E]
+    H = [f(u) for u in H]
+    if half == 1:
+        stiff = (1, 2, 0)
+        cross = ((1, 0, E[1]), (2, 1, E[2]), (0, 2, E[0]))   # (test deriv, trial deriv, field)
+    else:
+        stiff = (2, 0, 1)
+        cross = ((2, 0, E[2]), (0, 1, E[0]), (1, 2, E[1]))
+    curl = (-D.inner(None, 2) @ H[1] + D.inner(None, 1) @ H[2],
+            D.inner(None, 2) @ H[0] - D.inner(None, 0) @ H[2],
+            -D.inner(None, 1) @ H[0] + D.inner(None, 0) @ H[1])
+    out = []
+    for i in range(3):
+        s = stiff[i]
+        lhs = mass + c[:, None] * D.inner(s, s)
+        td, ud, fld = cross[i]
+        rhs = a * (mass @ E[i]) + b * curl[i] + c * (D.inner(td, ud) @ fld)
+        if J is not None:
+            rhs = rhs - b * J[i]
+        m = D.free(E_DIR[i])
+        x = np.zeros_like(rhs)
+        x[m] = np.linalg.solve(lhs[np.ix_(m, m)], rhs[m])
+        out.append(x.reshape(D.N[2], D.N[1], D.N[0]))
+    return out
+
+
+def h_substep(D, H, E_alpha, E_beta, d):
+    f = lambda u: np.asarray(u).ravel()
+    d = f(d)
+    mass = D.inner(None, None)
+    Ea = [f(u) for u in E_alpha]
+    Eb = [f(u) for u in E_beta]
+    C1 = (D.inner(None, 1) @ Ea[2], D.inner(None, 2) @ Ea[0], D.inner(None, 0) @ Ea[1])
+    C2 = (D.inner(None, 2) @ Eb[1], D.inner(None, 0) @ Eb[2], D.inner(None, 1) @ Eb[0])
+    out = []
+    for i in range(3):
+        rhs = mass @ f(H[i]) + d * (-C1[i] + C2[i])
+        m = D.free(H_DIR[i])
+        x = np.zeros_like(rhs)
+        x[m] = np.linalg.solve(mass[np.ix_(m, m)], rhs[m])
+        out.append(x.reshape(D.N[2], D.N[1], D.N[0]))
+    return out
