@@ -1,0 +1,313 @@
+"""Benchmark: field DOF-steps/s of the ADI isogeometric Maxwell step on GB300.
+
+Workload: 256^3 elements, p = 2 (258^3 coefficients x 6 components), seeded
+head-like 3-phase material map (seed 2103), z-directed point dipole, tau = 4x
+the explicit CFL limit, FP32 arithmetic.  One bench "step" is one full ADI time
+step (four sub-solves).  The working set (fields + row coefficients, ~0.7 GB)
+is far larger than the 129 MB L2, so no explicit flush is needed between
+steps.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle instead (the only reference that exists for this method).  With
+``--gpus N`` under torchrun every rank steps its own independent replica
+(the single-instance path does not shard without an exchange step).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "field DOF-steps/s at 256^3 p=2 (mixed/learned vs FP32 GPU), % HBM roofline"
+UNIT = "DOF-steps/s"
+N_ELEM = 256
+P = 2
+SEED = 2103
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=N_ELEM, help="elements per axis (default 256)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+def workload(n):
+    from paper_2103_06998_gb300 import inputs
+    eps, mu, sigma, _ = inputs.head_map((n, n, n), SEED)
+    src = inputs.dipole(SEED)
+    return eps, mu, sigma, src
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("adi_kernels.cu", "adi_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_2103_06998_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def ncu_traffic(kernel, n):
+    """Per-launch DRAM bytes of ``kernel`` from the committed ncu summary, or
+    None when the summary was taken on a different kernel source."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = kernel_source_hash()
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 4 and not line.startswith("#") and parts[0] == kernel and parts[1] == str(n) and parts[3] == src:
+            return float(parts[2])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(n, eps, mu, sigma, src, tau):
+    """The FP64 oracle on the host cores, on a bounded sample: the E and H
+    sub-solves of half step 1 of one time step at the full size (half of a
+    time step), scaled to DOF-steps/s."""
+    from oracle import maxwell_adi as ma
+    from paper_2103_06998_gb300 import inputs
+    prob = ma.make_problem((n, n, n), P, tau, eps, mu, sigma)
+    ma.set_source(prob, src["x0"], src["comp"], src["amp"], src["f0"], src["t0"], src["s"])
+    st = ma.apply_dirichlet(list(inputs.random_fields(prob.shape, 3)))
+    t0 = time.perf_counter()
+    E_half = ma.solve_E(prob, 1, ma.rhs_E(prob, 1, st[:3], st[3:], 1.5 + 0.25 * tau))
+    ma.solve_H(prob, ma.rhs_H(prob, st[3:], st[:3], E_half))
+    dt = time.perf_counter() - t0
+    Nc = (n + P) ** 3
+    return {"value": 6 * Nc * 0.5 / dt, "unit": UNIT, "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+            "sample": "E and H sub-solves of half step 1 (half a time step) at %d^3, p=2, FP64 numpy "
+                      "(BLAS threads = all cores); %.1f s" % (n, dt)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    n = args.n
+    eps, mu, sigma, src = workload(n)
+    from oracle import material
+    from oracle import maxwell_adi as ma
+    from paper_2103_06998_gb300 import inputs
+    eh = material.row_hats(eps, (n, n, n), P)
+    tau = 4.0 * material.cfl_dt((n, n, n), P, eh, material.row_hats(mu, (n, n, n), P))
+    prob = ma.make_problem((n, n, n), P, tau, eps, mu, sigma)
+    ma.set_source(prob, src["x0"], src["comp"], src["amp"], src["f0"], src["t0"], src["s"])
+    st = ma.apply_dirichlet(list(inputs.random_fields(prob.shape, 3)))
+    Nc = (n + P) ** 3
+
+    def one():  # bounded sample: the H sub-solve of half step 1 (a quarter step)
+        ma.solve_H(prob, ma.rhs_H(prob, st[3:], st[:3], st[:3]))
+
+    for _ in range(args.warmup):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    dt = time.perf_counter() - t0
+    value = 6 * Nc * 0.25 * args.steps / dt
+    cores = len(os.sched_getaffinity(0))
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "ADI IGA Maxwell step, %d^3 elements, p=2, head-like 3-phase map seed %d, "
+                                   "dipole, tau=4 dt_CFL" % (n, SEED), "n": n, "p": P, "tau": tau},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "each step: the H sub-solve of half step 1 (RHS + 9 line solves, counted "
+                                       "as a quarter time step) at full size, FP64 numpy"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2103_06998_gb300 import adi, inputs
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    n = args.n
+    eps, mu, sigma, src = workload(n)
+    # tau = 4 x explicit limit (the library computes the limit for these data)
+    s = adi.Solver((n, n, n), P, 1.0, eps, mu, sigma, precision=args.precision)
+    tau = 4.0 * s.cfl_dt()
+    s.set_dt(tau)
+    s.factor()
+    s.set_source(src["x0"], src["comp"], src["amp"], src["f0"], src["t0"], src["s"])
+    stream = torch.cuda.current_stream()
+    s.set_stream(stream.cuda_stream)
+    Nc = (n + P) ** 3
+    state = inputs.random_fields((n + P,) * 3, 3) * 0.0
+    s.set_fields(state, 1.0)
+    dof_steps = 6 * Nc
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- warm-up, then the timed region (device events on the launch stream)
+    for _ in range(args.warmup):
+        s.step(1)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            s.step(1)
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * dof_steps * args.steps / (ms_max * 1e-3)
+
+    # ---- per-kernel device times over the same number of steps (events around
+    # every launch on the same stream, graph off), for the roofline
+    s.set_profiling(True)
+    for _ in range(args.steps):
+        s.step(1)
+    stats = s.kernel_stats()
+    s.set_profiling(False)
+    tot = sum(k["total_ms"] for k in stats)
+    dom = max(stats, key=lambda k: k["total_ms"])
+    launches_per_step = sum(k["launches"] for k in stats) / args.steps
+    avg_ms = dom["total_ms"] / dom["launches"]
+    hbm, peak_kind = peaks()
+    achieved = dom["bytes_per_launch"] / (avg_ms * 1e-3) / 1e9
+    traffic = ncu_traffic(dom["name"], n)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": traffic, "kernel": dom["name"], "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"
+                if peak_kind == "measured" else "fallback 6.8 TB/s",
+                "step_frac": (50 * Nc * (4 if args.precision == "fp32" else 8)) / (ms_max * 1e-3 / args.steps) / 1e9 / hbm,
+                "kernels": {k["name"]: {"launches_per_step": k["launches"] / args.steps,
+                                        "ms_per_launch": k["total_ms"] / k["launches"],
+                                        "share": k["total_ms"] / tot,
+                                        "GBps": k["bytes_per_launch"] / (k["total_ms"] / k["launches"] * 1e-3) / 1e9}
+                            for k in stats}}
+
+    # ---- end to end through the C-ABI with pinned host buffers
+    host_in = torch.empty(6 * Nc, dtype=torch.float64, pin_memory=True)
+    host_out = torch.empty(6 * Nc, dtype=torch.float64, pin_memory=True)
+    host_in.numpy()[:] = inputs.random_fields((n + P,) * 3, 5).ravel() * 1e-3
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        s.set_fields_ptr(host_in.data_ptr(), 1.0)
+        s.step(1)
+        s.fields_ptr(host_out.data_ptr())
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    te = torch.tensor([e2e_s], device="cuda")
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e = {"value": world * dof_steps / float(te.item()), "unit": UNIT,
+           "h2d_bytes_per_step": 6 * Nc * 8, "d2h_bytes_per_step": 6 * Nc * 8}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(n, eps, mu, sigma, src, tau)
+    s.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+                "data": "synthetic",
+                "config": {"workload": "ADI IGA Maxwell step, %d^3 elements, p=2, head-like 3-phase map seed %d, "
+                                       "dipole, tau=4 dt_CFL" % (n, SEED), "n": n, "p": P, "tau": tau,
+                           "l2": "working set 0.7 GB >> 129 MB L2 (no flush needed)",
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(round(launches_per_step * args.steps)),
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

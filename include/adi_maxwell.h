@@ -1,0 +1,169 @@
+/*
+ * adi_maxwell.h -- C-ABI of the GB300 (sm_103a) ADI isogeometric Maxwell stepper.
+ *
+ * The method is the alternating-direction-implicit (ADI) time scheme with
+ * B-spline (IGA) discretisation of Paszynski, Los and Munoz-Matute,
+ * "Alternating directions implicit higher-order finite element method for
+ * simulations of time-dependent electromagnetic wave propagation in
+ * non-regular biological tissues" (arXiv 2103.06998):
+ *
+ *   dE/dt = eps^-1 curl H,  dH/dt = -mu^-1 curl E  on (0,1)^3 with
+ *   E x n = 0 and H . n = 0 on the boundary        (section "Alternating
+ *   directions splitting for Maxwell equations", first system of equations),
+ *
+ * split as curl = C1 - C2 and advanced in two half steps (eqs. scheme1a-1d),
+ * discretised as eqs. discrete1-discrete4 with 1D mass, stiffness and
+ * advection matrices on a regular patch of n_x x n_y x n_z elements of degree
+ * p, and solved by three banded 1D systems per E component (section
+ * "Incorporating non-regular material data", Appendix eqs. split1/split2).
+ * Material data are attached to the test functions (rows).
+ *
+ * Conventions shared by all calls:
+ *  - Coefficient arrays are [component][z][y][x], x fastest, N_d = n_d + p
+ *    coefficients per axis, N_c = N_x N_y N_z per component.  The six
+ *    components are ordered E1, E2, E3, H1, H2, H3.
+ *  - Per-element material arrays are [z][y][x] with n_x n_y n_z entries.
+ *  - The caller owns every host pointer; the library copies what it needs and
+ *    keeps no caller pointer after a call returns.
+ *  - A handle owns all device memory it allocates; adi_destroy frees it.
+ *  - No call aborts or throws.  Failures return a status other than ADI_OK and
+ *    set a message readable with adi_last_error(h).
+ *  - Work is issued on the handle's CUDA stream (adi_set_stream; default: the
+ *    library's own non-blocking stream).  Calls that return host data
+ *    synchronise that stream.
+ *  - A handle is used by one host thread at a time.
+ */
+#ifndef ADI_MAXWELL_H
+#define ADI_MAXWELL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct adi_ctx* adi_handle;
+
+typedef enum {
+  ADI_OK = 0,
+  ADI_EINVAL = 1,   /* invalid argument (sizes, p, dt, material <= 0, null pointer) */
+  ADI_ENOMEM = 2,   /* device or host allocation failed */
+  ADI_ECUDA = 3,    /* a CUDA call failed (message has the CUDA error string) */
+  ADI_ESTATE = 4,   /* call out of order (e.g. adi_step before adi_factor) */
+  ADI_ENUMERIC = 5, /* NaN or Inf found in an input or an output */
+  ADI_ETIMEOUT = 6  /* a bounded device wait gave up */
+} adi_status;
+
+/* Arithmetic of the time step. */
+enum { ADI_PREC_FP64 = 0, ADI_PREC_FP32 = 1 };
+
+typedef struct {
+  int precision;   /* ADI_PREC_FP32 (default) or ADI_PREC_FP64 */
+  int use_graph;   /* 1 (default): adi_step replays a captured CUDA graph of one step */
+  int reserved[6]; /* must be 0 */
+} adi_options;
+
+/* Create a problem on the unit cube.
+ *  nx, ny, nz >= 1 elements per axis; 1 <= p <= 3 (B-spline degree, C^{p-1});
+ *  dt > 0 is the full time step tau (each half step advances tau/2);
+ *  eps, mu, sigma: per-element relative permittivity, permeability and
+ *  conductivity ([z][y][x], n_x n_y n_z doubles each); NULL means 1, 1, 0.
+ *  eps and mu must be > 0 (first system of equations: eps, mu >= delta > 0)
+ *  and sigma >= 0, else ADI_EINVAL.  opt may be NULL (defaults).
+ *  Per-element values become per-test-function values by the support-weighted
+ *  mean  v_rst = sum_e v_e W_e / sum_e W_e,  W_e = prod_d int_{e_d} B_{r_d}
+ *  (the paper attaches material to test functions but does not say how voxel
+ *  data map to them; this is the reading used).  Conductivity enters as
+ *  eps dE/dt + sigma E = curl H - J, trapezoidal over each half step.
+ *  On success *out is a new handle with all fields zero at t = 0. */
+adi_status adi_create(int nx, int ny, int nz, int p, double dt,
+                      const double* eps, const double* mu, const double* sigma,
+                      const adi_options* opt, adi_handle* out);
+
+/* Build the 1D matrices M, S, A (B = A^T) of every axis by Gauss-Legendre
+ * quadrature in FP64 (definitions after eq. discrete4), factor the mass
+ * matrices (full and Dirichlet-reduced) without pivoting, and upload the
+ * factors in the working precision.  Must precede adi_step (else ADI_ESTATE). */
+adi_status adi_factor(adi_handle h);
+
+/* Change the time step; the row coefficients are rebuilt and adi_factor must
+ * be called again before the next adi_step. */
+adi_status adi_set_dt(adi_handle h, double dt);
+
+/* Use the given cudaStream_t (NULL = legacy default stream) for all later work. */
+adi_status adi_set_stream(adi_handle h, void* cuda_stream);
+
+/* Copy 6 N_c doubles (host) into the state and set the time to t.  The
+ * coefficients that the boundary conditions fix to zero (E_i in the two
+ * directions other than i, H_i in direction i: first and last B-spline) are
+ * set to zero.  NaN/Inf in EH gives ADI_ENUMERIC. */
+adi_status adi_set_fields(adi_handle h, const double* EH, double t);
+
+/* Point dipole J = amp g(t) delta(x - x0) e_comp (comp 0, 1, 2 = E1, E2, E3),
+ * g(t) = sin(2 pi f0 (t - t0)) exp(-((t - t0)/s)^2).  Enters the E rows as
+ * -b (J, B_rst) at the mid time of each half step.  Not part of the paper's
+ * equations.  amp = 0 removes the source.  x0 must lie in [0,1]^3. */
+adi_status adi_set_source(adi_handle h, double x0, double y0, double z0, int comp,
+                          double amp, double f0, double t0, double s);
+
+/* Advance n >= 1 full time steps (eqs. scheme1a-1d: E half step 1, H half step
+ * 1, E half step 2, H half step 2).  Asynchronous on the handle's stream. */
+adi_status adi_step(adi_handle h, int n);
+
+/* Run one sub-solve only: which = 0 (E, half step 1), 1 (H, half step 1),
+ * 2 (E, half step 2), 3 (H, half step 2, also advances the time by tau).
+ * Four calls in order equal one adi_step.  For testing. */
+adi_status adi_substep(adi_handle h, int which);
+
+/* Copy the state to 6 N_c host doubles (working precision widened) and the
+ * current time to *t (t may be NULL).  Synchronises the stream.  Returns
+ * ADI_ENUMERIC if any value is NaN/Inf (the data are still copied). */
+adi_status adi_fields(adi_handle h, double* EH, double* t);
+
+/* Copy the state, in the working precision (float or double as created), to
+ * 6 N_c elements of device memory at dev_ptr, on cuda_stream (NULL = the
+ * handle's stream).  Asynchronous. */
+adi_status adi_fields_device(adi_handle h, void* dev_ptr, void* cuda_stream);
+
+/* Explicit-scheme stability limit used to choose dt (not in the paper):
+ * 2 / (c_max sqrt(lambda_x + lambda_y + lambda_z)), lambda_d the largest
+ * eigenvalue of M^-1 S on axis d (Dirichlet-reduced), c_max =
+ * 1/sqrt(min_rows eps^ mu^).  Returns a negative value on error. */
+double adi_cfl_dt(adi_handle h);
+
+/* Block until all work on the handle's stream is done. */
+adi_status adi_sync(adi_handle h);
+
+/* Per-kernel timing.  With profiling on, every kernel launch of adi_step /
+ * adi_substep is bracketed by CUDA events on the handle's stream (graphs are
+ * not used while it is on).  adi_kernel_stats fills up to max entries with
+ * the kernel family name (static string), launch count, and summed device
+ * milliseconds since profiling was switched on, and sets *count; it
+ * synchronises the stream. */
+typedef struct {
+  const char* name;
+  long long launches;
+  double total_ms;
+  double bytes_per_launch; /* algorithmic bytes moved by one launch */
+} adi_kernel_stat;
+adi_status adi_set_profiling(adi_handle h, int on);
+adi_status adi_kernel_stats(adi_handle h, adi_kernel_stat* out, int max, int* count);
+
+/* Sizes: N_x, N_y, N_z, and bytes of one working-precision element. */
+adi_status adi_dims(adi_handle h, int* Nx, int* Ny, int* Nz, int* elem_bytes);
+
+/* Release everything owned by h.  NULL is ignored. */
+void adi_destroy(adi_handle h);
+
+/* Message of the last failure on h (or of the last failed adi_create when h
+ * is NULL).  Never NULL. */
+const char* adi_last_error(adi_handle h);
+
+/* Static name of a status code. */
+const char* adi_status_string(adi_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ADI_MAXWELL_H */

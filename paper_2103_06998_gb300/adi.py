@@ -1,0 +1,191 @@
+"""Python binding of the C-ABI in include/adi_maxwell.h (ctypes, marshalling only).
+
+Every step of the method runs in the CUDA kernels of ``libadi_maxwell.so``;
+this module only converts arguments.  Loading fails loudly when the library is
+missing -- there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libadi_maxwell.so")
+
+ADI_OK, ADI_EINVAL, ADI_ENOMEM, ADI_ECUDA, ADI_ESTATE, ADI_ENUMERIC, ADI_ETIMEOUT = range(7)
+PREC_FP64, PREC_FP32 = 0, 1
+
+# every symbol declared in include/adi_maxwell.h
+EXPORTS = ("adi_create", "adi_factor", "adi_set_dt", "adi_set_stream", "adi_set_fields",
+           "adi_set_source", "adi_step", "adi_substep", "adi_fields", "adi_fields_device",
+           "adi_cfl_dt", "adi_sync", "adi_set_profiling", "adi_kernel_stats", "adi_dims",
+           "adi_destroy", "adi_last_error", "adi_status_string")
+
+
+class AdiOptions(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("use_graph", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+
+
+class AdiKernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_longlong),
+                ("total_ms", ctypes.c_double), ("bytes_per_launch", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libadi_maxwell.so once; raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libadi_maxwell.so not built (run paper_2103_06998_gb300.build.build())")
+    lib = ctypes.CDLL(path)
+    H = ctypes.c_void_p
+    D = ctypes.c_double
+    I = ctypes.c_int
+    P = ctypes.POINTER
+    sig = {
+        "adi_create": (I, [I, I, I, I, D, P(D), P(D), P(D), P(AdiOptions), P(H)]),
+        "adi_factor": (I, [H]),
+        "adi_set_dt": (I, [H, D]),
+        "adi_set_stream": (I, [H, ctypes.c_void_p]),
+        "adi_set_fields": (I, [H, P(D), D]),
+        "adi_set_source": (I, [H, D, D, D, I, D, D, D, D]),
+        "adi_step": (I, [H, I]),
+        "adi_substep": (I, [H, I]),
+        "adi_fields": (I, [H, P(D), P(D)]),
+        "adi_fields_device": (I, [H, ctypes.c_void_p, ctypes.c_void_p]),
+        "adi_cfl_dt": (D, [H]),
+        "adi_sync": (I, [H]),
+        "adi_set_profiling": (I, [H, I]),
+        "adi_kernel_stats": (I, [H, P(AdiKernelStat), I, P(I)]),
+        "adi_dims": (I, [H, P(I), P(I), P(I), P(I)]),
+        "adi_destroy": (None, [H]),
+        "adi_last_error": (ctypes.c_char_p, [H]),
+        "adi_status_string": (ctypes.c_char_p, [I]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+class AdiError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (status, msg))
+        self.status = status
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class Solver:
+    """One ADI Maxwell problem on the GPU (owns an adi_handle)."""
+
+    def __init__(self, n, p, dt, eps=None, mu=None, sigma=None, precision="fp32", use_graph=True):
+        lib = load_library()
+        self._lib = lib
+        self.n = tuple(int(v) for v in n)
+        self.p = int(p)
+        opt = AdiOptions()
+        opt.precision = PREC_FP64 if precision == "fp64" else PREC_FP32
+        opt.use_graph = 1 if use_graph else 0
+        self.dtype = np.float64 if precision == "fp64" else np.float32
+        keep = []
+
+        def arr(a):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            keep.append(a)
+            return _dptr(a)
+
+        h = ctypes.c_void_p()
+        st = lib.adi_create(self.n[0], self.n[1], self.n[2], self.p, float(dt), arr(eps), arr(mu), arr(sigma),
+                            ctypes.byref(opt), ctypes.byref(h))
+        if st != ADI_OK:
+            raise AdiError(st, lib.adi_last_error(None).decode())
+        self.h = h
+        self.shape = (self.n[2] + p, self.n[1] + p, self.n[0] + p)
+        self.dt = float(dt)
+
+    def _check(self, st):
+        if st != ADI_OK:
+            raise AdiError(st, self._lib.adi_last_error(self.h).decode())
+
+    def factor(self):
+        self._check(self._lib.adi_factor(self.h))
+
+    def set_dt(self, dt):
+        self._check(self._lib.adi_set_dt(self.h, float(dt)))
+        self.dt = float(dt)
+
+    def set_stream(self, stream_ptr):
+        self._check(self._lib.adi_set_stream(self.h, ctypes.c_void_p(int(stream_ptr))))
+
+    def set_fields(self, EH, t=0.0):
+        a = np.ascontiguousarray(EH, dtype=np.float64)
+        assert a.size == 6 * int(np.prod(self.shape))
+        self._check(self._lib.adi_set_fields(self.h, _dptr(a), float(t)))
+
+    def set_fields_ptr(self, host_ptr, t=0.0):
+        """Set fields from a raw host pointer to 6 N_c doubles (e.g. pinned memory)."""
+        self._check(self._lib.adi_set_fields(self.h, ctypes.cast(ctypes.c_void_p(int(host_ptr)),
+                                                                 ctypes.POINTER(ctypes.c_double)), float(t)))
+
+    def set_source(self, x0, comp, amp, f0, t0, s):
+        self._check(self._lib.adi_set_source(self.h, float(x0[0]), float(x0[1]), float(x0[2]), int(comp),
+                                             float(amp), float(f0), float(t0), float(s)))
+
+    def step(self, n=1):
+        self._check(self._lib.adi_step(self.h, int(n)))
+
+    def substep(self, which):
+        self._check(self._lib.adi_substep(self.h, int(which)))
+
+    def fields(self):
+        out = np.empty((6,) + self.shape, dtype=np.float64)
+        t = ctypes.c_double()
+        self._check(self._lib.adi_fields(self.h, _dptr(out), ctypes.byref(t)))
+        return out, t.value
+
+    def fields_ptr(self, host_ptr):
+        t = ctypes.c_double()
+        self._check(self._lib.adi_fields(self.h, ctypes.cast(ctypes.c_void_p(int(host_ptr)),
+                                                             ctypes.POINTER(ctypes.c_double)), ctypes.byref(t)))
+        return t.value
+
+    def fields_device(self, dev_ptr, stream_ptr=0):
+        self._check(self._lib.adi_fields_device(self.h, ctypes.c_void_p(int(dev_ptr)), ctypes.c_void_p(int(stream_ptr))))
+
+    def cfl_dt(self):
+        return self._lib.adi_cfl_dt(self.h)
+
+    def sync(self):
+        self._check(self._lib.adi_sync(self.h))
+
+    def set_profiling(self, on):
+        self._check(self._lib.adi_set_profiling(self.h, 1 if on else 0))
+
+    def kernel_stats(self):
+        buf = (AdiKernelStat * 64)()
+        cnt = ctypes.c_int()
+        self._check(self._lib.adi_kernel_stats(self.h, buf, 64, ctypes.byref(cnt)))
+        return [dict(name=buf[i].name.decode(), launches=buf[i].launches, total_ms=buf[i].total_ms,
+                     bytes_per_launch=buf[i].bytes_per_launch) for i in range(min(cnt.value, 64))]
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.adi_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

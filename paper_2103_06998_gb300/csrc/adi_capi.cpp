@@ -1,0 +1,445 @@
+// C-ABI of the ADI isogeometric Maxwell stepper (see include/adi_maxwell.h).
+// Host-side validation, ownership of device memory, CUDA-graph capture of one
+// time step, and per-kernel event timing.  All arithmetic of the step runs in
+// the kernels of adi_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "adi_internal.h"
+
+using adi::Ctx;
+
+namespace {
+
+thread_local std::string g_create_error = "no error";
+
+adi_status fail(Ctx* c, adi_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  else g_create_error = msg;
+  return s;
+}
+
+adi_status cuda_fail(Ctx* c, cudaError_t e, const char* where) {
+  return fail(c, e == cudaErrorMemoryAllocation ? ADI_ENOMEM : ADI_ECUDA,
+              std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+void free_ctx(Ctx* c0) {
+  if (!c0) return;
+  adi_ctx* c = static_cast<adi_ctx*>(c0);
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  for (auto* l : c->pending) delete l;
+  void* ptrs[] = {c->d_eps, c->d_mu, c->d_sigma, c->stage, c->tab, c->d_clock_t0, c->d_clock_step};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (int i = 0; i < 6; ++i) {
+    if (c->cur[i]) cudaFree(c->cur[i]);
+    if (c->half[i]) cudaFree(c->half[i]);
+  }
+  for (int i = 0; i < 3; ++i)
+    if (c->rhs[i]) cudaFree(c->rhs[i]);
+  for (int i = 0; i < 4; ++i)
+    if (c->coef[i]) cudaFree(c->coef[i]);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+bool finite_all(const double* v, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(v[i])) return false;
+  return true;
+}
+
+void drop_graph(Ctx* c) {
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- profiling
+namespace adi {
+
+void prof_begin(Ctx& c, const char* name, double bytes) {
+  if (!c.profiling) return;
+  Launch* l = new (std::nothrow) Launch{name, bytes, nullptr, nullptr};
+  if (!l) return;
+  cudaEventCreate(&l->a);
+  cudaEventCreate(&l->b);
+  cudaEventRecord(l->a, c.stream);
+  c.pending.push_back(l);
+}
+
+void prof_end(Ctx& c) {
+  if (!c.profiling || c.pending.empty()) return;
+  cudaEventRecord(c.pending.back()->b, c.stream);
+}
+
+static void prof_collect(Ctx& c) {
+  cudaStreamSynchronize(c.stream);
+  for (Launch* l : c.pending) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, l->a, l->b);
+    bool found = false;
+    for (auto& s : c.stats)
+      if (std::strcmp(s.name, l->name) == 0) {
+        s.launches += 1;
+        s.total_ms += ms;
+        found = true;
+        break;
+      }
+    if (!found) c.stats.push_back(adi_kernel_stat{l->name, 1, (double)ms, l->bytes});
+    cudaEventDestroy(l->a);
+    cudaEventDestroy(l->b);
+    delete l;
+  }
+  c.pending.clear();
+}
+
+}  // namespace adi
+
+// ------------------------------------------------------------------- API
+extern "C" {
+
+const char* adi_status_string(adi_status s) {
+  switch (s) {
+    case ADI_OK: return "ADI_OK";
+    case ADI_EINVAL: return "ADI_EINVAL";
+    case ADI_ENOMEM: return "ADI_ENOMEM";
+    case ADI_ECUDA: return "ADI_ECUDA";
+    case ADI_ESTATE: return "ADI_ESTATE";
+    case ADI_ENUMERIC: return "ADI_ENUMERIC";
+    case ADI_ETIMEOUT: return "ADI_ETIMEOUT";
+  }
+  return "ADI_UNKNOWN";
+}
+
+const char* adi_last_error(adi_handle h) {
+  if (!h) return g_create_error.c_str();
+  return h->err.c_str();
+}
+
+adi_status adi_create(int nx, int ny, int nz, int p, double dt, const double* eps, const double* mu,
+                      const double* sigma, const adi_options* opt, adi_handle* out) {
+  if (!out) return fail(nullptr, ADI_EINVAL, "adi_create: out is NULL");
+  *out = nullptr;
+  if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, ADI_EINVAL, "adi_create: element counts must be >= 1");
+  if (p < 1 || p > adi::kMaxP) return fail(nullptr, ADI_EINVAL, "adi_create: p must be in 1..3");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(nullptr, ADI_EINVAL, "adi_create: dt must be finite and > 0");
+  int prec = ADI_PREC_FP32, use_graph = 1;
+  if (opt) {
+    if (opt->precision != ADI_PREC_FP32 && opt->precision != ADI_PREC_FP64)
+      return fail(nullptr, ADI_EINVAL, "adi_create: precision must be ADI_PREC_FP32 or ADI_PREC_FP64");
+    for (int i = 0; i < 6; ++i)
+      if (opt->reserved[i] != 0) return fail(nullptr, ADI_EINVAL, "adi_create: reserved option fields must be 0");
+    prec = opt->precision;
+    use_graph = opt->use_graph ? 1 : 0;
+  }
+  const size_t ne = (size_t)nx * ny * nz;
+  for (const double* arr : {eps, mu}) {
+    if (!arr) continue;
+    for (size_t i = 0; i < ne; ++i)
+      if (!(arr[i] > 0.0) || !std::isfinite(arr[i]))
+        return fail(nullptr, ADI_EINVAL, "adi_create: eps and mu must be finite and > 0");
+  }
+  if (sigma)
+    for (size_t i = 0; i < ne; ++i)
+      if (!(sigma[i] >= 0.0) || !std::isfinite(sigma[i]))
+        return fail(nullptr, ADI_EINVAL, "adi_create: sigma must be finite and >= 0");
+
+  adi_ctx* c = new (std::nothrow) adi_ctx();
+  if (!c) return fail(nullptr, ADI_ENOMEM, "adi_create: host allocation failed");
+  c->n[0] = nx;
+  c->n[1] = ny;
+  c->n[2] = nz;
+  c->p = p;
+  for (int d = 0; d < 3; ++d) c->N[d] = c->n[d] + p;
+  c->Nc = (size_t)c->N[0] * c->N[1] * c->N[2];
+  c->precision = prec;
+  c->use_graph = use_graph;
+  c->esize = prec == ADI_PREC_FP64 ? 8 : 4;
+  c->dt = dt;
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) {
+    free_ctx(c);
+    return cuda_fail(nullptr, e, "adi_create: cudaGetDevice");
+  }
+  e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    free_ctx(c);
+    return cuda_fail(nullptr, e, "adi_create: cudaStreamCreate");
+  }
+  c->own_stream = true;
+  const size_t fb = c->Nc * c->esize;
+  bool ok = true;
+  auto alloc = [&](void** p, size_t bytes) {
+    if (!ok) return;
+    if (cudaMalloc(p, bytes) != cudaSuccess) ok = false;
+  };
+  for (int i = 0; i < 6; ++i) {
+    alloc(&c->cur[i], fb);
+    alloc(&c->half[i], fb);
+  }
+  for (int i = 0; i < 3; ++i) alloc(&c->rhs[i], fb);
+  for (int i = 0; i < 4; ++i) alloc(&c->coef[i], fb);
+  alloc(&c->stage, c->Nc * 6 * sizeof(double));
+  alloc((void**)&c->d_eps, ne * sizeof(double));
+  alloc((void**)&c->d_mu, ne * sizeof(double));
+  alloc((void**)&c->d_sigma, ne * sizeof(double));
+  alloc((void**)&c->d_clock_t0, sizeof(double));
+  alloc((void**)&c->d_clock_step, sizeof(long long));
+  if (!ok) {
+    cudaGetLastError();
+    free_ctx(c);
+    return fail(nullptr, ADI_ENOMEM, "adi_create: device allocation failed");
+  }
+  // material: NULL -> 1, 1, 0
+  std::vector<double> tmp(ne);
+  const double* srcs[3] = {eps, mu, sigma};
+  double* dsts[3] = {c->d_eps, c->d_mu, c->d_sigma};
+  const double defaults[3] = {1.0, 1.0, 0.0};
+  for (int k = 0; k < 3; ++k) {
+    const double* s = srcs[k];
+    if (!s) {
+      std::fill(tmp.begin(), tmp.end(), defaults[k]);
+      s = tmp.data();
+    }
+    e = cudaMemcpy(dsts[k], s, ne * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      free_ctx(c);
+      return cuda_fail(nullptr, e, "adi_create: upload material");
+    }
+  }
+  for (int d = 0; d < 3; ++d) adi::build_axis(c->n[d], p, c->axes[d]);
+  e = adi::compute_coefficients(*c);
+  if (e == cudaSuccess) {
+    for (int i = 0; i < 6 && e == cudaSuccess; ++i) {
+      e = cudaMemsetAsync(c->cur[i], 0, fb, c->stream);
+      if (e == cudaSuccess) e = cudaMemsetAsync(c->half[i], 0, fb, c->stream);
+    }
+  }
+  if (e == cudaSuccess) e = adi::set_clock(*c, 0.0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    free_ctx(c);
+    return cuda_fail(nullptr, e, "adi_create: setup kernels");
+  }
+  c->err = "no error";
+  *out = c;
+  return ADI_OK;
+}
+
+adi_status adi_factor(adi_handle h) {
+  if (!h) return fail(nullptr, ADI_EINVAL, "adi_factor: NULL handle");
+  cudaError_t e = adi::upload_tables(*h);
+  if (e != cudaSuccess) return cuda_fail(h, e, "adi_factor");
+  drop_graph(h);
+  h->factored = true;
+  return ADI_OK;
+}
+
+adi_status adi_set_dt(adi_handle h, double dt) {
+  if (!h) return fail(nullptr, ADI_EINVAL, "adi_set_dt: NULL handle");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(h, ADI_EINVAL, "adi_set_dt: dt must be finite and > 0");
+  h->dt = dt;
+  cudaError_t e = adi::compute_coefficients(*h);
+  if (e != cudaSuccess) return cuda_fail(h, e, "adi_set_dt");
+  drop_graph(h);
+  h->factored = false;
+  return ADI_OK;
+}
+
+adi_status adi_set_stream(adi_handle h, void* s) {
+  if (!h) return fail(nullptr, ADI_EINVAL, "adi_set_stream: NULL handle");
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "adi_set_stream");
+  if (h->own_stream) cudaStreamDestroy(h->stream);
+  h->own_stream = false;
+  h->stream = (cudaStream_t)s;
+  drop_graph(h);
+  return ADI_OK;
+}
+
+adi_status adi_set_fields(adi_handle h, const double* EH, double t) {
+  if (!h) return fail(nullptr, ADI_EINVAL, "adi_set_fields: NULL handle");
+  if (!EH) return fail(h, ADI_EINVAL, "adi_set_fields: EH is NULL");
+  if (!std::isfinite(t)) return fail(h, ADI_EINVAL, "adi_set_fields: t must be finite");
+  if (!finite_all(EH, 6 * h->Nc)) return fail(h, ADI_ENUMERIC, "adi_set_fields: NaN or Inf in EH");
+  cudaError_t e = cudaMemcpyAsync(h->stage, EH, 6 * h->Nc * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = adi::set_fields_dev(*h, (const double*)h->stage);
+  if (e == cudaSuccess) e = adi::set_clock(*h, t);
+  if (e != cudaSuccess) return cuda_fail(h, e, "adi_set_fields");
+  h->t_host = t;
+  h->steps_host = 0;
+  return ADI_OK;
+}
+
+adi_status adi_set_source(adi_handle h, double x0, double y0, double z0, int comp, double amp, double f0,
+                          double t0, double s) {
+  if (!h) return fail(nullptr, ADI_EINVAL, "adi_set_source: NULL handle");
+  const double xs[3] = {x0, y0, z0};
+  for (double v : xs)
+    if (!(v >= 0.0 && v <= 1.0)) return fail(h, ADI_EINVAL, "adi_set_source: position must lie in [0,1]^3");
+  if (comp < 0 || comp > 2) return fail(h, ADI_EINVAL, "adi_set_source: comp must be 0, 1 or 2");
+  if (!std::isfinite(amp) || !std::isfinite(f0) || !std::isfinite(t0) || !(s > 0.0) || !std::isfinite(s))
+    return fail(h, ADI_EINVAL, "adi_set_source: amp, f0, t0 must be finite and s > 0");
+  for (int d = 0; d < 3; ++d) {
+    double v[adi::kMaxP + 1] = {};
+    h->src_i0[d] = adi::point_basis(h->n[d], h->p, xs[d], v);
+    for (int q = 0; q <= adi::kMaxP; ++q) h->src_w[d][q] = q <= h->p ? v[q] : 0.0;
+  }
+  h->src_comp = comp;
+  h->src_amp = amp;
+  h->src_f0 = f0;
+  h->src_t0 = t0;
+  h->src_s = s;
+  drop_graph(h);
+  return ADI_OK;
+}
+
+static adi_status capture_graph(adi_handle h) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(h, e, "adi_step: begin capture");
+  cudaError_t ek = cudaSuccess;
+  for (int w = 0; w < 4 && ek == cudaSuccess; ++w) ek = adi::run_substep(*h, w);
+  e = cudaStreamEndCapture(h->stream, &g);
+  if (ek != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(h, ek, "adi_step: kernel launch during capture");
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "adi_step: end capture");
+  e = cudaGraphInstantiate(&h->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    h->graph = nullptr;
+    return cuda_fail(h, e, "adi_step: instantiate");
+  }
+  return ADI_OK;
+}
+
+adi_status adi_step(adi_handle h, int n) {
+  if (!h) return fail(nullptr, ADI_EINVAL, "adi_step: NULL handle");
+  if (n < 1) return fail(h, ADI_EINVAL, "adi_step: n must be >= 1");
+  if (!h->factored) return fail(h, ADI_ESTATE, "adi_step: call adi_factor first");
+  const bool graph = h->use_graph && !h->profiling && h->stream != nullptr;
+  if (graph && !h->graph) {
+    adi_status s = capture_graph(h);
+    if (s != ADI_OK) return s;
+  }
+  for (int k = 0; k < n; ++k) {
+    cudaError_t e = cudaSuccess;
+    if (graph) {
+      e = cudaGraphLaunch(h->graph, h->stream);
+    } else {
+      for (int w = 0; w < 4 && e == cudaSuccess; ++w) e = adi::run_substep(*h, w);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "adi_step");
+    h->steps_host += 1;
+  }
+  return ADI_OK;
+}
+
+adi_status adi_substep(adi_handle h, int which) {
+  if (!h) return fail(nullptr, ADI_EINVAL, "adi_substep: NULL handle");
+  if (which < 0 || which > 3) return fail(h, ADI_EINVAL, "adi_substep: which must be 0..3");
+  if (!h->factored) return fail(h, ADI_ESTATE, "adi_substep: call adi_factor first");
+  cudaError_t e = adi::run_substep(*h, which);
+  if (e != cudaSuccess) return cuda_fail(h, e, "adi_substep");
+  if (which == 3) h->steps_host += 1;
+  return ADI_OK;
+}
+
+adi_status adi_fields(adi_handle h, double* EH, double* t) {
+  if (!h) return fail(nullptr, ADI_EINVAL, "adi_fields: NULL handle");
+  if (!EH) return fail(h, ADI_EINVAL, "adi_fields: EH is NULL");
+  int* d_bad = nullptr;
+  cudaError_t e = cudaMalloc(&d_bad, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, sizeof(int), h->stream);
+  if (e == cudaSuccess) e = adi::get_fields_dev(*h, (double*)h->stage, d_bad);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(EH, h->stage, 6 * h->Nc * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  int bad = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (d_bad) cudaFree(d_bad);
+  if (e != cudaSuccess) return cuda_fail(h, e, "adi_fields");
+  if (t) *t = h->t_host + (double)h->steps_host * h->dt;
+  if (bad) return fail(h, ADI_ENUMERIC, "adi_fields: NaN or Inf in the state");
+  return ADI_OK;
+}
+
+adi_status adi_fields_device(adi_handle h, void* dev_ptr, void* stream) {
+  if (!h) return fail(nullptr, ADI_EINVAL, "adi_fields_device: NULL handle");
+  if (!dev_ptr) return fail(h, ADI_EINVAL, "adi_fields_device: dev_ptr is NULL");
+  cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
+  const size_t fb = h->Nc * h->esize;
+  if (s != h->stream) {
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "adi_fields_device");
+  }
+  for (int i = 0; i < 6; ++i) {
+    cudaError_t e = cudaMemcpyAsync((char*)dev_ptr + i * fb, h->cur[i], fb, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "adi_fields_device");
+  }
+  return ADI_OK;
+}
+
+double adi_cfl_dt(adi_handle h) {
+  if (!h) return -1.0;
+  double lam = 0.0;
+  for (int d = 0; d < 3; ++d) lam += adi::lambda_max(h->axes[d]);
+  if (!(lam > 0.0) || !(h->min_eps_mu > 0.0)) return -1.0;
+  double cmax = 1.0 / std::sqrt(h->min_eps_mu);
+  return 2.0 / (cmax * std::sqrt(lam));
+}
+
+adi_status adi_sync(adi_handle h) {
+  if (!h) return fail(nullptr, ADI_EINVAL, "adi_sync: NULL handle");
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "adi_sync");
+  return ADI_OK;
+}
+
+adi_status adi_set_profiling(adi_handle h, int on) {
+  if (!h) return fail(nullptr, ADI_EINVAL, "adi_set_profiling: NULL handle");
+  adi::prof_collect(*h);
+  h->profiling = on != 0;
+  h->stats.clear();
+  return ADI_OK;
+}
+
+adi_status adi_kernel_stats(adi_handle h, adi_kernel_stat* out, int max, int* count) {
+  if (!h) return fail(nullptr, ADI_EINVAL, "adi_kernel_stats: NULL handle");
+  if (!count || (max > 0 && !out)) return fail(h, ADI_EINVAL, "adi_kernel_stats: NULL output");
+  adi::prof_collect(*h);
+  int n = (int)h->stats.size();
+  for (int i = 0; i < n && i < max; ++i) out[i] = h->stats[i];
+  *count = n;
+  return ADI_OK;
+}
+
+adi_status adi_dims(adi_handle h, int* Nx, int* Ny, int* Nz, int* elem_bytes) {
+  if (!h) return fail(nullptr, ADI_EINVAL, "adi_dims: NULL handle");
+  if (Nx) *Nx = h->N[0];
+  if (Ny) *Ny = h->N[1];
+  if (Nz) *Nz = h->N[2];
+  if (elem_bytes) *elem_bytes = (int)h->esize;
+  return ADI_OK;
+}
+
+void adi_destroy(adi_handle h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  free_ctx(h);
+}
+
+}  // extern "C"

@@ -1,0 +1,162 @@
+// Internal declarations shared by the C-ABI (adi_capi.cpp), the host setup
+// (setup_host.cpp) and the CUDA kernels (adi_kernels.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/adi_maxwell.h"
+
+namespace adi {
+
+constexpr int kMaxP = 3;
+constexpr int kMaxTerms = 12;
+
+// ---------------------------------------------------------------- host setup
+struct Axis1D {
+  int n = 0, p = 0, N = 0;
+  std::vector<double> M, S, A, B;  // bands, row k: [k*(2p+1) + d] = X[k][k+d-p]
+  std::vector<double> G;           // G[r*(p+1) + a] = int over element r-p+a of B_r
+};
+struct BandLU {
+  int N = 0, p = 0, lo = 0, hi = 0;
+  std::vector<double> L, inv_d, U;  // L[k*p+q-1], U[k*p+q-1] for q = 1..p
+};
+void build_axis(int n, int p, Axis1D& ax);
+void band_lu(const std::vector<double>& base, const std::vector<double>* stiff, int N, int p,
+             int lo, int hi, BandLU& out);
+double lambda_max(const Axis1D& ax);
+int point_basis(int n, int p, double x0, double* vals);
+
+// ---------------------------------------------------------- device structures
+// Operator codes of one Kronecker factor.
+enum Op : int { OP_M = 0, OP_S = 1, OP_A = 2, OP_B = 3 };
+// Row coefficient selecting a, b, c, d or 1.
+enum Coef : int { CF_ONE = 0, CF_A = 1, CF_B = 2, CF_C = 3, CF_D = 4 };
+
+template <typename T>
+struct AxisDev {
+  const T* band[4];     // M, S, A, B bands (N x (2p+1))
+  const T* luL[2];      // mass LU, [0] full, [1] Dirichlet-reduced
+  const T* luInv[2];
+  const T* luU[2];
+  int N;
+};
+
+struct Term {
+  int field;   // index into RhsParams::fields
+  int out;     // output component 0..2
+  int op[3];   // Op for x, y, z
+  int coef;    // Coef
+  float sign;  // +1 or -1
+};
+
+template <typename T>
+struct RhsParams {
+  const T* fields[9];
+  const T* coef[5];  // [CF_A], [CF_B], [CF_C], [CF_D] (index 0 unused)
+  T* out[3];
+  AxisDev<T> ax[3];
+  Term terms[kMaxTerms];
+  int nterms;
+  int nfields;
+  int Nx, Ny, Nz;
+  // point source (E rows only): comp < 0 disables
+  int src_comp;
+  int src_i0[3];
+  T src_w[3][kMaxP + 1];
+  double src_amp, src_f0, src_t0, src_s;
+  double tau, t_frac;  // mid time = clock.t0 + (clock.step + t_frac) * tau
+  const double* clock_t0;
+  long long* clock_step;
+  int advance_clock;   // 1: block 0 thread 0 increments the step counter
+};
+
+struct LineParams {
+  int dir;        // 0 x, 1 y, 2 z
+  int N;          // line length
+  long long nlines;
+  int Nx, Ny, Nz;
+  int lo, hi;     // solved rows (Dirichlet: 1 .. N-2)
+  int dirichlet;
+};
+
+// ----------------------------------------------------------- the handle
+struct Launch {  // profiling record of one kernel launch
+  const char* name;
+  double bytes;
+  cudaEvent_t a, b;
+};
+
+struct Ctx {
+  int n[3] = {0, 0, 0};  // elements x, y, z
+  int N[3] = {0, 0, 0};  // coefficients per axis
+  int p = 2;
+  int precision = ADI_PREC_FP32;
+  int use_graph = 1;
+  double dt = 0.0;
+  size_t Nc = 0;
+  size_t esize = 4;
+  bool factored = false;
+  std::string err;
+
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  int smem_optin = 48 * 1024;  // per-block opt-in shared memory (set by adi_factor)
+
+  // per-element material (device, double), kept for set_dt
+  double* d_eps = nullptr;
+  double* d_mu = nullptr;
+  double* d_sigma = nullptr;
+  double min_eps_mu = 1.0;
+
+  // state and work (element type T = float or double), each Nc elements
+  void* cur[6] = {};
+  void* half[6] = {};
+  void* rhs[3] = {};
+  void* coef[4] = {};   // a, b, c, d
+  void* stage = nullptr;  // Nc doubles for host transfers (FP32 mode)
+
+  // 1D tables on device (element type T)
+  void* tab = nullptr;
+  size_t tab_bytes = 0;
+  Axis1D axes[3];
+  double* d_clock_t0 = nullptr;
+  long long* d_clock_step = nullptr;
+  double t_host = 0.0;
+  long long steps_host = 0;
+
+  // source
+  int src_comp = -1;
+  int src_i0[3] = {0, 0, 0};
+  double src_w[3][kMaxP + 1] = {};
+  double src_amp = 0, src_f0 = 0, src_t0 = 0, src_s = 1;
+
+  // graph of one step
+  cudaGraphExec_t graph = nullptr;
+
+  // profiling
+  bool profiling = false;
+  std::vector<Launch*> pending;
+  std::vector<adi_kernel_stat> stats;
+};
+
+// Kernel-side entry points (adi_kernels.cu), all asynchronous on ctx.stream.
+cudaError_t upload_tables(Ctx& c);
+cudaError_t compute_coefficients(Ctx& c);
+cudaError_t run_substep(Ctx& c, int which);
+cudaError_t set_fields_dev(Ctx& c, const double* d_src);
+cudaError_t get_fields_dev(Ctx& c, double* d_dst, int* d_bad);
+cudaError_t set_clock(Ctx& c, double t0);
+
+// profiling hooks used by the launchers
+void prof_begin(Ctx& c, const char* name, double bytes);
+void prof_end(Ctx& c);
+
+}  // namespace adi
+
+// The opaque handle type of the C-ABI is the context itself.
+struct adi_ctx : public adi::Ctx {};

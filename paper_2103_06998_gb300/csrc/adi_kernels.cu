@@ -1,0 +1,883 @@
+// CUDA kernels of the ADI isogeometric Maxwell step (sm_103a).
+//
+// One time step is four sub-solves (eqs. scheme1a-1d of the paper, discretised
+// as eqs. discrete1-discrete4):
+//   E half step 1: RHS (eq. dupa1ab, rows scaled by a, b, c) -> stiffness
+//                  direction line solve (row-scaled M + c S) -> two mass
+//                  direction line solves (Appendix, eqs. split1/split2);
+//   H half step 1: RHS (eq. discrete2, rows scaled by d) -> three mass solves;
+//   E half step 2: as half step 1 with K2 / R2 (eq. discrete3);
+//   H half step 2: eq. discrete4 with the minus sign of eq. scheme1d on C1.
+//
+// Kernels:
+//   rhs_kernel   sum-factorised Kronecker contractions on a 3D tile held in
+//                shared memory (z pass, y pass, x pass per term), all terms of
+//                one sub-step in one launch, each input tile loaded once.
+//   line_kernel  banded Gaussian elimination without pivoting along x, y or z,
+//                one thread per line; a tile of lines is staged in shared
+//                memory (coalesced, transposed to line-major for x), solved in
+//                place and written back.  STIFF=true factors the row-scaled
+//                M + c S on the fly; otherwise the precomputed mass LU is used.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+
+#include "adi_internal.h"
+
+namespace adi {
+
+namespace {
+
+// ------------------------------------------------------------------ RHS
+template <typename T, int P, int TX, int TY, int TZ>
+__global__ void __launch_bounds__(TX* TY) rhs_kernel(const RhsParams<T> prm) {
+  constexpr int W = 2 * P + 1;
+  constexpr int HX = TX + 2 * P, HY = TY + 2 * P, HZ = TZ + 2 * P;
+  constexpr int NT = TX * TY;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* s_in = reinterpret_cast<T*>(smem_raw);
+  T* s_z = s_in + HZ * HY * HX;
+  T* s_y = s_z + TZ * HY * HX;
+  __shared__ T s_bx[TX][W], s_by[TY][W], s_bz[TZ][W];
+
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
+  const int Nx = prm.Nx, Ny = prm.Ny, Nz = prm.Nz;
+  const long long sxy = (long long)Nx * Ny;
+  const int gx = x0 + tx, gy = y0 + ty;
+  const bool col_in = gx < Nx && gy < Ny;
+
+  // row coefficients of this thread's outputs
+  T cf[5][TZ];
+#pragma unroll
+  for (int k = 0; k < 5; ++k)
+#pragma unroll
+    for (int zz = 0; zz < TZ; ++zz) cf[k][zz] = T(k == 0 ? 1 : 0);
+#pragma unroll
+  for (int k = 1; k < 5; ++k) {
+    if (prm.coef[k] != nullptr && col_in) {
+#pragma unroll
+      for (int zz = 0; zz < TZ; ++zz) {
+        int gz = z0 + zz;
+        if (gz < Nz) cf[k][zz] = prm.coef[k][gz * sxy + (long long)gy * Nx + gx];
+      }
+    }
+  }
+
+  T acc[3][TZ];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int zz = 0; zz < TZ; ++zz) acc[c][zz] = T(0);
+
+  int cur_field = -1;
+  for (int t = 0; t < prm.nterms; ++t) {
+    const Term tm = prm.terms[t];
+    __syncthreads();  // previous x pass done with s_y / band rows
+    if (tm.field != cur_field) {
+      const T* __restrict__ f = prm.fields[tm.field];
+      for (int i = tid; i < HZ * HY * HX; i += NT) {
+        int xx = i % HX, r = i / HX, yy = r % HY, zz = r / HY;
+        int X = x0 - P + xx, Y = y0 - P + yy, Z = z0 - P + zz;
+        T v = T(0);
+        if (X >= 0 && X < Nx && Y >= 0 && Y < Ny && Z >= 0 && Z < Nz) v = f[Z * sxy + (long long)Y * Nx + X];
+        s_in[i] = v;
+      }
+      cur_field = tm.field;
+    }
+    {
+      const T* bx = prm.ax[0].band[tm.op[0]];
+      const T* by = prm.ax[1].band[tm.op[1]];
+      const T* bz = prm.ax[2].band[tm.op[2]];
+      for (int i = tid; i < (TX + TY + TZ) * W; i += NT) {
+        int row = i / W, q = i % W;
+        if (row < TX) {
+          int g = x0 + row;
+          s_bx[row][q] = g < Nx ? bx[g * W + q] : T(0);
+        } else if (row < TX + TY) {
+          int g = y0 + row - TX;
+          s_by[row - TX][q] = g < Ny ? by[g * W + q] : T(0);
+        } else {
+          int g = z0 + row - TX - TY;
+          s_bz[row - TX - TY][q] = g < Nz ? bz[g * W + q] : T(0);
+        }
+      }
+    }
+    __syncthreads();
+    // z pass: s_z[zz][yy][xx] = sum_q Z[z0+zz][q] s_in[zz+q][yy][xx]
+    for (int i = tid; i < TZ * HY * HX; i += NT) {
+      int rem = i % (HY * HX), zz = i / (HY * HX);
+      T s = T(0);
+#pragma unroll
+      for (int q = 0; q < W; ++q) s += s_bz[zz][q] * s_in[(zz + q) * HY * HX + rem];
+      s_z[i] = s;
+    }
+    __syncthreads();
+    // y pass: s_y[zz][yy][xx] = sum_q Y[y0+yy][q] s_z[zz][yy+q][xx]
+    for (int i = tid; i < TZ * TY * HX; i += NT) {
+      int xx = i % HX, r = i / HX, yy = r % TY, zz = r / TY;
+      T s = T(0);
+#pragma unroll
+      for (int q = 0; q < W; ++q) s += s_by[yy][q] * s_z[(zz * HY + yy + q) * HX + xx];
+      s_y[i] = s;
+    }
+    __syncthreads();
+    // x pass and accumulation into this thread's outputs
+    const T sg = T(tm.sign);
+#pragma unroll
+    for (int zz = 0; zz < TZ; ++zz) {
+      T s = T(0);
+#pragma unroll
+      for (int q = 0; q < W; ++q) s += s_bx[tx][q] * s_y[(zz * TY + ty) * HX + tx + q];
+      T w = sg;
+      switch (tm.coef) {
+        case CF_A: w *= cf[1][zz]; break;
+        case CF_B: w *= cf[2][zz]; break;
+        case CF_C: w *= cf[3][zz]; break;
+        case CF_D: w *= cf[4][zz]; break;
+        default: break;
+      }
+      if (tm.out == 0) acc[0][zz] += w * s;
+      else if (tm.out == 1) acc[1][zz] += w * s;
+      else acc[2][zz] += w * s;
+    }
+  }
+
+  // point source: -b amp g(t_mid) B_r(x0) B_s(y0) B_t(z0) on its component
+  double g = 0.0;
+  if (prm.src_comp >= 0) {
+    double tm = *prm.clock_t0 + ((double)*prm.clock_step + prm.t_frac) * prm.tau;
+    double u = tm - prm.src_t0;
+    g = prm.src_amp * sin(2.0 * 3.14159265358979323846 * prm.src_f0 * u) * exp(-(u / prm.src_s) * (u / prm.src_s));
+  }
+  if (col_in) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+#pragma unroll
+      for (int zz = 0; zz < TZ; ++zz) {
+        int gz = z0 + zz;
+        if (gz >= Nz) continue;
+        T v = acc[c][zz];
+        if (c == prm.src_comp) {
+          int ix = gx - prm.src_i0[0], iy = gy - prm.src_i0[1], iz = gz - prm.src_i0[2];
+          if (ix >= 0 && ix <= P && iy >= 0 && iy <= P && iz >= 0 && iz <= P)
+            v -= cf[2][zz] * T(g) * prm.src_w[0][ix] * prm.src_w[1][iy] * prm.src_w[2][iz];
+        }
+        prm.out[c][gz * sxy + (long long)gy * Nx + gx] = v;
+      }
+    }
+  }
+  if (prm.advance_clock && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && tid == 0)
+    *prm.clock_step += 1;
+}
+
+// ----------------------------------------------------------- line solves
+__device__ __forceinline__ long long line_offset(const LineParams& lp, long long L) {
+  // first element of line L; lines along y are indexed z*Nx + x, along z y*Nx + x
+  if (lp.dir == 0) return L * lp.N;
+  if (lp.dir == 1) return (L / lp.Nx) * (long long)lp.Nx * lp.Ny + (L % lp.Nx);
+  return L;
+}
+
+__device__ __forceinline__ long long line_stride(const LineParams& lp) {
+  if (lp.dir == 0) return 1;
+  if (lp.dir == 1) return lp.Nx;
+  return (long long)lp.Nx * lp.Ny;
+}
+
+template <typename T, int P, bool STIFF>
+__global__ void line_kernel(const T* src, T* dst, const LineParams lp, const AxisDev<T> ax,
+                            const T* __restrict__ cvec) {
+  constexpr int W = 2 * P + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int LINES = blockDim.x, LP = LINES + 1, N = lp.N;
+  T* sr = reinterpret_cast<T*>(smem_raw);  // [k][line], row pitch LP
+  T* su = sr + (size_t)N * LP;             // STIFF: P planes [q][k][line]
+  const int t = threadIdx.x;
+  const long long L0 = (long long)blockIdx.x * LINES;
+  const int cnt = (int)min((long long)LINES, lp.nlines - L0);
+  const long long stride = line_stride(lp);
+
+  // ---- stage the tile (coalesced), transposing x lines to [k][line]
+  if (lp.dir == 0) {
+    const T* base = src + L0 * N;
+    const T* cbase = STIFF ? cvec + L0 * N : nullptr;
+    for (int line = 0; line < cnt; ++line) {
+      for (int k = t; k < N; k += LINES) {
+        sr[k * LP + line] = base[(long long)line * N + k];
+        if (STIFF) su[k * LP + line] = cbase[(long long)line * N + k];
+      }
+    }
+  } else if (t < cnt) {
+    const long long off = line_offset(lp, L0 + t);
+#pragma unroll 8
+    for (int k = 0; k < N; ++k) {
+      sr[k * LP + t] = src[off + k * stride];
+      if (STIFF) su[k * LP + t] = cvec[off + k * stride];
+    }
+  }
+  __syncthreads();
+
+  if (t < cnt) {
+    const int lo = lp.lo, hi = lp.hi;
+    if (STIFF) {
+      const T* __restrict__ Mb = ax.band[OP_M];
+      const T* __restrict__ Sb = ax.band[OP_S];
+      T Uq[P][P + 1], invq[P], yq[P];
+#pragma unroll
+      for (int m = 0; m < P; ++m) {
+        invq[m] = T(0);
+        yq[m] = T(0);
+#pragma unroll
+        for (int e = 0; e <= P; ++e) Uq[m][e] = T(0);
+      }
+      for (int k = lo; k <= hi; ++k) {
+        const T ck = su[k * LP + t];
+        T a[W];
+#pragma unroll
+        for (int d = 0; d < W; ++d) {
+          int j = k + d - P;
+          a[d] = (j >= lo && j <= hi) ? Mb[k * W + d] + ck * Sb[k * W + d] : T(0);
+        }
+        T l[P + 1];
+        l[0] = T(0);
+#pragma unroll
+        for (int q = P; q >= 1; --q) {  // column k - q
+          T s = a[P - q];
+#pragma unroll
+          for (int m = q + 1; m <= P; ++m) s -= l[m] * Uq[m - 1][m - q];
+          l[q] = s * invq[q - 1];
+        }
+        T Un[P + 1];
+#pragma unroll
+        for (int e = 0; e <= P; ++e) {
+          T s = a[P + e];
+#pragma unroll
+          for (int m = 1; m <= P; ++m)
+            if (e + m <= P) s -= l[m] * Uq[m - 1][e + m];
+          Un[e] = s;
+        }
+        const T inv = T(1) / Un[0];
+        T y = sr[k * LP + t];
+#pragma unroll
+        for (int m = 1; m <= P; ++m) y -= l[m] * yq[m - 1];
+        sr[k * LP + t] = y * inv;
+#pragma unroll
+        for (int e = 1; e <= P; ++e) su[((size_t)(e - 1) * N + k) * LP + t] = Un[e] * inv;
+#pragma unroll
+        for (int m = P - 1; m >= 1; --m) {
+          invq[m] = invq[m - 1];
+          yq[m] = yq[m - 1];
+#pragma unroll
+          for (int e = 0; e <= P; ++e) Uq[m][e] = Uq[m - 1][e];
+        }
+        invq[0] = inv;
+        yq[0] = y;
+#pragma unroll
+        for (int e = 0; e <= P; ++e) Uq[0][e] = Un[e];
+      }
+      T xq[P];
+#pragma unroll
+      for (int m = 0; m < P; ++m) xq[m] = T(0);
+      for (int k = hi; k >= lo; --k) {
+        T x = sr[k * LP + t];
+#pragma unroll
+        for (int e = 1; e <= P; ++e) x -= su[((size_t)(e - 1) * N + k) * LP + t] * xq[e - 1];
+        sr[k * LP + t] = x;
+#pragma unroll
+        for (int m = P - 1; m >= 1; --m) xq[m] = xq[m - 1];
+        xq[0] = x;
+      }
+    } else {
+      const int dch = lp.dirichlet;
+      const T* __restrict__ Lt = ax.luL[dch];
+      const T* __restrict__ It = ax.luInv[dch];
+      const T* __restrict__ Ut = ax.luU[dch];
+      T yq[P];
+#pragma unroll
+      for (int m = 0; m < P; ++m) yq[m] = T(0);
+      for (int k = lo; k <= hi; ++k) {
+        T y = sr[k * LP + t];
+#pragma unroll
+        for (int m = 1; m <= P; ++m) y -= Lt[k * P + m - 1] * yq[m - 1];
+        sr[k * LP + t] = y;
+#pragma unroll
+        for (int m = P - 1; m >= 1; --m) yq[m] = yq[m - 1];
+        yq[0] = y;
+      }
+      T xq[P];
+#pragma unroll
+      for (int m = 0; m < P; ++m) xq[m] = T(0);
+      for (int k = hi; k >= lo; --k) {
+        T x = It[k] * sr[k * LP + t];
+#pragma unroll
+        for (int e = 1; e <= P; ++e) x -= Ut[k * P + e - 1] * xq[e - 1];
+        sr[k * LP + t] = x;
+#pragma unroll
+        for (int m = P - 1; m >= 1; --m) xq[m] = xq[m - 1];
+        xq[0] = x;
+      }
+    }
+    for (int k = 0; k < lo; ++k) sr[k * LP + t] = T(0);
+    for (int k = hi + 1; k < N; ++k) sr[k * LP + t] = T(0);
+  }
+  __syncthreads();
+
+  // ---- write back
+  if (lp.dir == 0) {
+    T* base = dst + L0 * N;
+    for (int line = 0; line < cnt; ++line)
+      for (int k = t; k < N; k += LINES) base[(long long)line * N + k] = sr[k * LP + line];
+  } else if (t < cnt) {
+    const long long off = line_offset(lp, L0 + t);
+#pragma unroll 8
+    for (int k = 0; k < N; ++k) dst[off + k * stride] = sr[k * LP + t];
+  }
+}
+
+// ------------------------------------------------------------ conversions
+__device__ __forceinline__ bool constrained(int comp, int i, int j, int k, int Nx, int Ny, int Nz) {
+  // E_i (comp 0..2): zero ends in the two directions != i; H_i: in direction i
+  bool bx = (i == 0 || i == Nx - 1), by = (j == 0 || j == Ny - 1), bz = (k == 0 || k == Nz - 1);
+  switch (comp) {
+    case 0: return by || bz;
+    case 1: return bx || bz;
+    case 2: return bx || by;
+    case 3: return bx;
+    case 4: return by;
+    default: return bz;
+  }
+}
+
+template <typename T>
+__global__ void set_fields_kernel(const double* __restrict__ src, T* d0, T* d1, T* d2, T* d3, T* d4, T* d5,
+                                  int Nx, int Ny, int Nz) {
+  const long long Nc = (long long)Nx * Ny * Nz;
+  T* dst[6] = {d0, d1, d2, d3, d4, d5};
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < 6 * Nc;
+       g += (long long)gridDim.x * blockDim.x) {
+    int comp = (int)(g / Nc);
+    long long r = g % Nc;
+    int i = (int)(r % Nx), j = (int)((r / Nx) % Ny), k = (int)(r / ((long long)Nx * Ny));
+    double v = src[g];
+    dst[comp][r] = constrained(comp, i, j, k, Nx, Ny, Nz) ? T(0) : T(v);
+  }
+}
+
+template <typename T>
+__global__ void get_fields_kernel(double* __restrict__ dst, const T* s0, const T* s1, const T* s2, const T* s3,
+                                  const T* s4, const T* s5, long long Nc, int* bad) {
+  const T* src[6] = {s0, s1, s2, s3, s4, s5};
+  int local_bad = 0;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < 6 * Nc;
+       g += (long long)gridDim.x * blockDim.x) {
+    double v = (double)src[g / Nc][g % Nc];
+    if (!isfinite(v)) local_bad = 1;
+    dst[g] = v;
+  }
+  if (local_bad) atomicOr(bad, 1);
+}
+
+__global__ void clock_kernel(double* t0, long long* step, double t) {
+  *t0 = t;
+  *step = 0;
+}
+
+// Per-row material (support-weighted mean of per-element data) and the row
+// coefficients a, b, c, d; also the running minimum of eps^ mu^.
+template <typename T>
+__global__ void coef_kernel(const double* __restrict__ eps, const double* __restrict__ mu,
+                            const double* __restrict__ sig, const double* __restrict__ Gx,
+                            const double* __restrict__ Gy, const double* __restrict__ Gz, int nx, int ny,
+                            int nz, int p, double tau, T* ca, T* cb, T* cc, T* cd,
+                            unsigned long long* min_bits) {
+  const int Nx = nx + p, Ny = ny + p, Nz = nz + p;
+  const long long Nc = (long long)Nx * Ny * Nz;
+  double local_min = 1e300;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < Nc;
+       g += (long long)gridDim.x * blockDim.x) {
+    int r = (int)(g % Nx), s = (int)((g / Nx) % Ny), t = (int)(g / ((long long)Nx * Ny));
+    double ne = 0, nm = 0, ns = 0, den = 0;
+    for (int c = 0; c <= p; ++c) {
+      int ez = t - p + c;
+      if (ez < 0 || ez >= nz) continue;
+      double wz = Gz[t * (p + 1) + c];
+      for (int b = 0; b <= p; ++b) {
+        int ey = s - p + b;
+        if (ey < 0 || ey >= ny) continue;
+        double wyz = wz * Gy[s * (p + 1) + b];
+        for (int a = 0; a <= p; ++a) {
+          int ex = r - p + a;
+          if (ex < 0 || ex >= nx) continue;
+          double w = wyz * Gx[r * (p + 1) + a];
+          long long e = ((long long)ez * ny + ey) * nx + ex;
+          ne += w * eps[e];
+          nm += w * mu[e];
+          ns += w * sig[e];
+          den += w;
+        }
+      }
+    }
+    double eh = ne / den, mh = nm / den, sh = ns / den;
+    double alpha = sh * tau / (4.0 * eh);
+    ca[g] = T((1.0 - alpha) / (1.0 + alpha));
+    cb[g] = T(tau / (2.0 * eh * (1.0 + alpha)));
+    cc[g] = T(tau * tau / (4.0 * eh * mh * (1.0 + alpha)));
+    cd[g] = T(tau / (2.0 * mh));
+    local_min = fmin(local_min, eh * mh);
+  }
+  // positive doubles order like their bit patterns
+  atomicMin(min_bits, (unsigned long long)__double_as_longlong(local_min));
+}
+
+// ---------------------------------------------------------------- helpers
+template <typename T>
+struct Layout {
+  // offsets (elements of T) of the 1D tables of axis d inside c.tab
+  size_t band[3][4];
+  size_t lu[3][2][3];
+  size_t total;
+};
+
+template <typename T>
+Layout<T> table_layout(const Ctx& c) {
+  Layout<T> L{};
+  size_t off = 0;
+  const int p = c.p, W = 2 * p + 1;
+  for (int d = 0; d < 3; ++d) {
+    int N = c.N[d];
+    for (int o = 0; o < 4; ++o) {
+      L.band[d][o] = off;
+      off += (size_t)N * W;
+    }
+    for (int f = 0; f < 2; ++f) {
+      L.lu[d][f][0] = off;
+      off += (size_t)N * p;
+      L.lu[d][f][1] = off;
+      off += (size_t)N;
+      L.lu[d][f][2] = off;
+      off += (size_t)N * p;
+    }
+  }
+  L.total = off;
+  return L;
+}
+
+template <typename T>
+AxisDev<T> axis_dev(const Ctx& c, int d) {
+  Layout<T> L = table_layout<T>(c);
+  const T* base = reinterpret_cast<const T*>(c.tab);
+  AxisDev<T> a;
+  for (int o = 0; o < 4; ++o) a.band[o] = base + L.band[d][o];
+  for (int f = 0; f < 2; ++f) {
+    a.luL[f] = base + L.lu[d][f][0];
+    a.luInv[f] = base + L.lu[d][f][1];
+    a.luU[f] = base + L.lu[d][f][2];
+  }
+  a.N = c.N[d];
+  return a;
+}
+
+template <typename T>
+cudaError_t upload_tables_t(Ctx& c) {
+  Layout<T> L = table_layout<T>(c);
+  std::vector<T> h(L.total, T(0));
+  const int p = c.p;
+  for (int d = 0; d < 3; ++d) {
+    const Axis1D& ax = c.axes[d];
+    const std::vector<double>* src[4] = {&ax.M, &ax.S, &ax.A, &ax.B};
+    for (int o = 0; o < 4; ++o)
+      for (size_t i = 0; i < src[o]->size(); ++i) h[L.band[d][o] + i] = T((*src[o])[i]);
+    for (int f = 0; f < 2; ++f) {
+      BandLU lu;
+      int N = ax.N;
+      band_lu(ax.M, nullptr, N, p, f ? 1 : 0, f ? N - 2 : N - 1, lu);
+      for (int k = 0; k < N; ++k) {
+        h[L.lu[d][f][1] + k] = T(lu.inv_d[k]);
+        for (int q = 0; q < p; ++q) {
+          h[L.lu[d][f][0] + (size_t)k * p + q] = T(lu.L[(size_t)k * p + q]);
+          h[L.lu[d][f][2] + (size_t)k * p + q] = T(lu.U[(size_t)k * p + q]);
+        }
+      }
+    }
+  }
+  if (c.tab && c.tab_bytes != L.total * sizeof(T)) {
+    cudaFree(c.tab);
+    c.tab = nullptr;
+  }
+  if (!c.tab) {
+    cudaError_t e = cudaMalloc(&c.tab, L.total * sizeof(T));
+    if (e != cudaSuccess) return e;
+    c.tab_bytes = L.total * sizeof(T);
+  }
+  cudaError_t e = cudaMemcpyAsync(c.tab, h.data(), L.total * sizeof(T), cudaMemcpyHostToDevice, c.stream);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(c.stream);
+}
+
+// Terms of the E right-hand side (eq. dupa1ab and its half step 2 analogue).
+// fields: 0..2 = E1..E3, 3..5 = H1..H3 (old level).
+int e_terms(int half, Term* t) {
+  auto T_ = [](int f, int out, int ox, int oy, int oz, int cf, float s) {
+    Term x;
+    x.field = f;
+    x.out = out;
+    x.op[0] = ox;
+    x.op[1] = oy;
+    x.op[2] = oz;
+    x.coef = cf;
+    x.sign = s;
+    return x;
+  };
+  int n = 0;
+  // E fields: a M(x)M(x)M E_i, and the R cross terms scaled by c
+  if (half == 1) {
+    t[n++] = T_(0, 0, OP_M, OP_M, OP_M, CF_A, 1.f);
+    t[n++] = T_(0, 2, OP_B, OP_M, OP_A, CF_C, 1.f);  // R1[3][1] = B(x)M(x)A
+    t[n++] = T_(1, 1, OP_M, OP_M, OP_M, CF_A, 1.f);
+    t[n++] = T_(1, 0, OP_A, OP_B, OP_M, CF_C, 1.f);  // R1[1][2] = A(x)B(x)M
+    t[n++] = T_(2, 2, OP_M, OP_M, OP_M, CF_A, 1.f);
+    t[n++] = T_(2, 1, OP_M, OP_A, OP_B, CF_C, 1.f);  // R1[2][3] = M(x)A(x)B
+  } else {
+    t[n++] = T_(0, 0, OP_M, OP_M, OP_M, CF_A, 1.f);
+    t[n++] = T_(0, 1, OP_B, OP_A, OP_M, CF_C, 1.f);  // R2[2][1] = B(x)A(x)M
+    t[n++] = T_(1, 1, OP_M, OP_M, OP_M, CF_A, 1.f);
+    t[n++] = T_(1, 2, OP_M, OP_B, OP_A, CF_C, 1.f);  // R2[3][2] = M(x)B(x)A
+    t[n++] = T_(2, 2, OP_M, OP_M, OP_M, CF_A, 1.f);
+    t[n++] = T_(2, 0, OP_A, OP_M, OP_B, CF_C, 1.f);  // R2[1][3] = A(x)M(x)B
+  }
+  // curl H = (C1 - C2) H, scaled by b
+  t[n++] = T_(3, 1, OP_M, OP_M, OP_A, CF_B, 1.f);   // + d3 H1 -> E2
+  t[n++] = T_(3, 2, OP_M, OP_A, OP_M, CF_B, -1.f);  // - d2 H1 -> E3
+  t[n++] = T_(4, 0, OP_M, OP_M, OP_A, CF_B, -1.f);  // - d3 H2 -> E1
+  t[n++] = T_(4, 2, OP_A, OP_M, OP_M, CF_B, 1.f);   // + d1 H2 -> E3
+  t[n++] = T_(5, 0, OP_M, OP_A, OP_M, CF_B, 1.f);   // + d2 H3 -> E1
+  t[n++] = T_(5, 1, OP_A, OP_M, OP_M, CF_B, -1.f);  // - d1 H3 -> E2
+  return n;
+}
+
+// Terms of the H right-hand side: M H_old - d C1 E_alpha + d C2 E_beta.
+// fields: 0..2 = H_old, 3..5 = E_alpha, 6..8 = E_beta.
+int h_terms(Term* t) {
+  auto T_ = [](int f, int out, int ox, int oy, int oz, int cf, float s) {
+    Term x;
+    x.field = f;
+    x.out = out;
+    x.op[0] = ox;
+    x.op[1] = oy;
+    x.op[2] = oz;
+    x.coef = cf;
+    x.sign = s;
+    return x;
+  };
+  int n = 0;
+  t[n++] = T_(0, 0, OP_M, OP_M, OP_M, CF_ONE, 1.f);
+  t[n++] = T_(1, 1, OP_M, OP_M, OP_M, CF_ONE, 1.f);
+  t[n++] = T_(2, 2, OP_M, OP_M, OP_M, CF_ONE, 1.f);
+  t[n++] = T_(3, 1, OP_M, OP_M, OP_A, CF_D, -1.f);  // (C1 E)2 = d3 E1
+  t[n++] = T_(4, 2, OP_A, OP_M, OP_M, CF_D, -1.f);  // (C1 E)3 = d1 E2
+  t[n++] = T_(5, 0, OP_M, OP_A, OP_M, CF_D, -1.f);  // (C1 E)1 = d2 E3
+  t[n++] = T_(6, 2, OP_M, OP_A, OP_M, CF_D, 1.f);   // (C2 E)3 = d2 E1
+  t[n++] = T_(7, 0, OP_M, OP_M, OP_A, CF_D, 1.f);   // (C2 E)1 = d3 E2
+  t[n++] = T_(8, 1, OP_A, OP_M, OP_M, CF_D, 1.f);   // (C2 E)2 = d1 E3
+  return n;
+}
+
+template <typename T, int P>
+constexpr int rhs_tz() { return 8; }
+
+template <typename T, int P>
+size_t rhs_smem() {
+  constexpr int TX = 32, TY = 8, TZ = 8;
+  return sizeof(T) * ((size_t)(TZ + 2 * P) * (TY + 2 * P) * (TX + 2 * P) + (size_t)TZ * (TY + 2 * P) * (TX + 2 * P) +
+                      (size_t)TZ * TY * (TX + 2 * P));
+}
+
+template <typename T, int P>
+cudaError_t launch_rhs(Ctx& c, RhsParams<T>& prm, const char* name, double bytes) {
+  constexpr int TX = 32, TY = 8, TZ = 8;
+  size_t smem = rhs_smem<T, P>();
+  auto kern = rhs_kernel<T, P, TX, TY, TZ>;
+  dim3 grid((c.N[0] + TX - 1) / TX, (c.N[1] + TY - 1) / TY, (c.N[2] + TZ - 1) / TZ);
+  prof_begin(c, name, bytes);
+  kern<<<grid, dim3(TX, TY), smem, c.stream>>>(prm);
+  prof_end(c);
+  return cudaGetLastError();
+}
+
+template <typename T, int P>
+cudaError_t launch_line(Ctx& c, const T* src, T* dst, int dir, bool stiff, int dirichlet, const T* cvec,
+                        const char* name) {
+  LineParams lp;
+  lp.dir = dir;
+  lp.N = c.N[dir];
+  lp.Nx = c.N[0];
+  lp.Ny = c.N[1];
+  lp.Nz = c.N[2];
+  lp.nlines = (long long)c.N[0] * c.N[1] * c.N[2] / c.N[dir];
+  lp.dirichlet = dirichlet;
+  lp.lo = dirichlet ? 1 : 0;
+  lp.hi = dirichlet ? lp.N - 2 : lp.N - 1;
+  const int planes = stiff ? 1 + P : 1;
+  int lines = 64;
+  const size_t limit = (size_t)c.smem_optin;
+  while (lines > 8 && (size_t)planes * lp.N * (lines + 1) * sizeof(T) > limit) lines /= 2;
+  size_t smem = (size_t)planes * lp.N * (lines + 1) * sizeof(T);
+  if (smem > limit) return cudaErrorInvalidValue;
+  auto kern = stiff ? line_kernel<T, P, true> : line_kernel<T, P, false>;
+  long long blocks = (lp.nlines + lines - 1) / lines;
+  double bytes = (double)c.Nc * sizeof(T) * (stiff ? 3.0 : 2.0);
+  prof_begin(c, name, bytes);
+  kern<<<(unsigned)blocks, lines, smem, c.stream>>>(src, dst, lp, axis_dev<T>(c, dir), cvec);
+  prof_end(c);
+  return cudaGetLastError();
+}
+
+// E half step: RHS, then per component stiffness direction first, then the two
+// mass directions (order of the Appendix, eqs. split1/split2).
+template <typename T, int P>
+cudaError_t e_substep(Ctx& c, int half) {
+  T** cur = reinterpret_cast<T**>(c.cur);
+  T** hlf = reinterpret_cast<T**>(c.half);
+  T** R = reinterpret_cast<T**>(c.rhs);
+  T** cf = reinterpret_cast<T**>(c.coef);
+  T* const* Ein = half == 1 ? cur : hlf;
+  T* const* Hin = half == 1 ? cur : hlf;
+  T* const* Eout = half == 1 ? hlf : cur;
+  RhsParams<T> prm{};
+  for (int i = 0; i < 3; ++i) {
+    prm.fields[i] = Ein[i];
+    prm.fields[3 + i] = Hin[3 + i];
+    prm.out[i] = R[i];
+  }
+  prm.nfields = 6;
+  prm.coef[CF_A] = cf[0];
+  prm.coef[CF_B] = cf[1];
+  prm.coef[CF_C] = cf[2];
+  prm.coef[CF_D] = nullptr;
+  for (int d = 0; d < 3; ++d) prm.ax[d] = axis_dev<T>(c, d);
+  prm.nterms = e_terms(half, prm.terms);
+  prm.Nx = c.N[0];
+  prm.Ny = c.N[1];
+  prm.Nz = c.N[2];
+  prm.src_comp = (c.src_comp >= 0 && c.src_amp != 0.0) ? c.src_comp : -1;
+  for (int d = 0; d < 3; ++d) {
+    prm.src_i0[d] = c.src_i0[d];
+    for (int q = 0; q <= kMaxP; ++q) prm.src_w[d][q] = T(c.src_w[d][q]);
+  }
+  prm.src_amp = c.src_amp;
+  prm.src_f0 = c.src_f0;
+  prm.src_t0 = c.src_t0;
+  prm.src_s = c.src_s;
+  prm.tau = c.dt;
+  prm.t_frac = half == 1 ? 0.25 : 0.75;
+  prm.clock_t0 = c.d_clock_t0;
+  prm.clock_step = c.d_clock_step;
+  prm.advance_clock = 0;
+  double bytes = (double)c.Nc * sizeof(T) * 12.0;
+  cudaError_t e = launch_rhs<T, P>(c, prm, "rhs_E", bytes);
+  if (e != cudaSuccess) return e;
+  // stiffness direction of E_i: half 1 (y, z, x), half 2 (z, x, y)
+  static const int stiff_dir[2][3] = {{1, 2, 0}, {2, 0, 1}};
+  static const char* stiff_name[3] = {"line_x_stiff", "line_y_stiff", "line_z_stiff"};
+  static const char* mass_name[3] = {"line_x_mass", "line_y_mass", "line_z_mass"};
+  for (int i = 0; i < 3; ++i) {
+    int sd = stiff_dir[half - 1][i];
+    e = launch_line<T, P>(c, R[i], R[i], sd, true, 1, cf[2], stiff_name[sd]);
+    if (e != cudaSuccess) return e;
+    int md[2], m = 0;
+    for (int d = 0; d < 3; ++d)
+      if (d != sd) md[m++] = d;
+    e = launch_line<T, P>(c, R[i], R[i], md[0], false, md[0] != i, nullptr, mass_name[md[0]]);
+    if (e != cudaSuccess) return e;
+    e = launch_line<T, P>(c, R[i], Eout[i], md[1], false, md[1] != i, nullptr, mass_name[md[1]]);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// H half step: M H_new = M H_old - d C1 E_alpha + d C2 E_beta, then three
+// mass solves per component (H_i constrained in direction i).
+template <typename T, int P>
+cudaError_t h_substep(Ctx& c, int half) {
+  T** cur = reinterpret_cast<T**>(c.cur);
+  T** hlf = reinterpret_cast<T**>(c.half);
+  T** R = reinterpret_cast<T**>(c.rhs);
+  T** cf = reinterpret_cast<T**>(c.coef);
+  RhsParams<T> prm{};
+  // half 1: H_old = H^n (cur), alpha = E^n (cur), beta = E^{n+1/2} (half), out -> half
+  // half 2: H_old = H^{n+1/2} (half), alpha = E^{n+1} (cur), beta = E^{n+1/2} (half), out -> cur
+  T* const* Hold = half == 1 ? cur : hlf;
+  T* const* Hout = half == 1 ? hlf : cur;
+  for (int i = 0; i < 3; ++i) {
+    prm.fields[i] = Hold[3 + i];
+    prm.fields[3 + i] = cur[i];
+    prm.fields[6 + i] = hlf[i];
+    prm.out[i] = R[i];
+  }
+  prm.nfields = 9;
+  prm.coef[CF_D] = cf[3];
+  for (int d = 0; d < 3; ++d) prm.ax[d] = axis_dev<T>(c, d);
+  prm.nterms = h_terms(prm.terms);
+  prm.Nx = c.N[0];
+  prm.Ny = c.N[1];
+  prm.Nz = c.N[2];
+  prm.src_comp = -1;
+  prm.clock_t0 = c.d_clock_t0;
+  prm.clock_step = c.d_clock_step;
+  prm.advance_clock = half == 2 ? 1 : 0;
+  double bytes = (double)c.Nc * sizeof(T) * 13.0;
+  cudaError_t e = launch_rhs<T, P>(c, prm, "rhs_H", bytes);
+  if (e != cudaSuccess) return e;
+  static const char* mass_name[3] = {"line_x_mass", "line_y_mass", "line_z_mass"};
+  for (int i = 0; i < 3; ++i) {
+    for (int d = 0; d < 3; ++d) {
+      T* dst = d == 2 ? Hout[3 + i] : R[i];
+      e = launch_line<T, P>(c, R[i], dst, d, false, d == i, nullptr, mass_name[d]);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+template <typename T, int P>
+cudaError_t substep_tp(Ctx& c, int which) {
+  switch (which) {
+    case 0: return e_substep<T, P>(c, 1);
+    case 1: return h_substep<T, P>(c, 1);
+    case 2: return e_substep<T, P>(c, 2);
+    default: return h_substep<T, P>(c, 2);
+  }
+}
+
+template <typename T>
+cudaError_t substep_t(Ctx& c, int which) {
+  switch (c.p) {
+    case 1: return substep_tp<T, 1>(c, which);
+    case 2: return substep_tp<T, 2>(c, which);
+    default: return substep_tp<T, 3>(c, which);
+  }
+}
+
+// Opt in to large dynamic shared memory once, outside any stream capture:
+// the per-block opt-in limit minus the kernel's static shared memory.
+template <typename K>
+cudaError_t opt_in(K kern, int optin) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+
+template <typename T, int P>
+cudaError_t prepare_tp(int optin) {
+  cudaError_t e = opt_in(rhs_kernel<T, P, 32, 8, 8>, optin);
+  if (e == cudaSuccess) e = opt_in(line_kernel<T, P, true>, optin);
+  if (e == cudaSuccess) e = opt_in(line_kernel<T, P, false>, optin);
+  return e;
+}
+
+template <typename T>
+cudaError_t prepare_t(int p, int optin) {
+  switch (p) {
+    case 1: return prepare_tp<T, 1>(optin);
+    case 2: return prepare_tp<T, 2>(optin);
+    default: return prepare_tp<T, 3>(optin);
+  }
+}
+
+unsigned grid_for(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  if (b > 152LL * 64) b = 152LL * 64;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+}  // namespace
+
+cudaError_t upload_tables(Ctx& c) {
+  int optin = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c.device);
+  if (e != cudaSuccess) return e;
+  c.smem_optin = optin;
+  e = c.precision == ADI_PREC_FP64 ? prepare_t<double>(c.p, optin) : prepare_t<float>(c.p, optin);
+  if (e != cudaSuccess) return e;
+  return c.precision == ADI_PREC_FP64 ? upload_tables_t<double>(c) : upload_tables_t<float>(c);
+}
+
+cudaError_t run_substep(Ctx& c, int which) {
+  return c.precision == ADI_PREC_FP64 ? substep_t<double>(c, which) : substep_t<float>(c, which);
+}
+
+cudaError_t set_fields_dev(Ctx& c, const double* d_src) {
+  unsigned g = grid_for(6LL * (long long)c.Nc, 256);
+  if (c.precision == ADI_PREC_FP64) {
+    double** d = reinterpret_cast<double**>(c.cur);
+    set_fields_kernel<double><<<g, 256, 0, c.stream>>>(d_src, d[0], d[1], d[2], d[3], d[4], d[5], c.N[0], c.N[1], c.N[2]);
+  } else {
+    float** d = reinterpret_cast<float**>(c.cur);
+    set_fields_kernel<float><<<g, 256, 0, c.stream>>>(d_src, d[0], d[1], d[2], d[3], d[4], d[5], c.N[0], c.N[1], c.N[2]);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t get_fields_dev(Ctx& c, double* d_dst, int* d_bad) {
+  unsigned g = grid_for(6LL * (long long)c.Nc, 256);
+  if (c.precision == ADI_PREC_FP64) {
+    double** s = reinterpret_cast<double**>(c.cur);
+    get_fields_kernel<double><<<g, 256, 0, c.stream>>>(d_dst, s[0], s[1], s[2], s[3], s[4], s[5], (long long)c.Nc, d_bad);
+  } else {
+    float** s = reinterpret_cast<float**>(c.cur);
+    get_fields_kernel<float><<<g, 256, 0, c.stream>>>(d_dst, s[0], s[1], s[2], s[3], s[4], s[5], (long long)c.Nc, d_bad);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t set_clock(Ctx& c, double t0) {
+  clock_kernel<<<1, 1, 0, c.stream>>>(c.d_clock_t0, c.d_clock_step, t0);
+  return cudaGetLastError();
+}
+
+cudaError_t compute_coefficients(Ctx& c) {
+  const int p = c.p;
+  std::vector<double> G;
+  size_t offs[4] = {0, 0, 0, 0};
+  for (int d = 0; d < 3; ++d) {
+    offs[d] = G.size();
+    G.insert(G.end(), c.axes[d].G.begin(), c.axes[d].G.end());
+  }
+  double* dG = nullptr;
+  unsigned long long* dmin = nullptr;
+  cudaError_t e = cudaMalloc(&dG, G.size() * sizeof(double));
+  if (e != cudaSuccess) return e;
+  e = cudaMalloc(&dmin, sizeof(unsigned long long));
+  if (e != cudaSuccess) { cudaFree(dG); return e; }
+  unsigned long long init = 0x7FEFFFFFFFFFFFFFULL;  // largest finite double
+  cudaMemcpyAsync(dG, G.data(), G.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream);
+  cudaMemcpyAsync(dmin, &init, sizeof(init), cudaMemcpyHostToDevice, c.stream);
+  unsigned g = grid_for((long long)c.Nc, 256);
+  if (c.precision == ADI_PREC_FP64) {
+    double** cf = reinterpret_cast<double**>(c.coef);
+    coef_kernel<double><<<g, 256, 0, c.stream>>>(c.d_eps, c.d_mu, c.d_sigma, dG + offs[0], dG + offs[1], dG + offs[2],
+                                                c.n[0], c.n[1], c.n[2], p, c.dt, cf[0], cf[1], cf[2], cf[3], dmin);
+  } else {
+    float** cf = reinterpret_cast<float**>(c.coef);
+    coef_kernel<float><<<g, 256, 0, c.stream>>>(c.d_eps, c.d_mu, c.d_sigma, dG + offs[0], dG + offs[1], dG + offs[2],
+                                               c.n[0], c.n[1], c.n[2], p, c.dt, cf[0], cf[1], cf[2], cf[3], dmin);
+  }
+  e = cudaGetLastError();
+  unsigned long long bits = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, dmin, sizeof(bits), cudaMemcpyDeviceToHost, c.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  cudaFree(dG);
+  cudaFree(dmin);
+  if (e == cudaSuccess) {
+    double m;
+    memcpy(&m, &bits, sizeof(m));
+    c.min_eps_mu = m;
+  }
+  return e;
+}
+
+}  // namespace adi

@@ -1,0 +1,59 @@
+"""The C-ABI library builds, loads and exports every function of the header
+(no compute call: runs without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "adi_maxwell.h")
+
+
+def _declared():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(adi_[a-z_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2103_06998_gb300 import adi, build
+    if not os.path.exists(adi.LIB_PATH):
+        build.build()
+    return ctypes.CDLL(adi.LIB_PATH)
+
+
+def test_header_declares_the_binding_exports():
+    from paper_2103_06998_gb300 import adi
+    assert set(_declared()) == set(adi.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [s for s in _declared() if not hasattr(lib, s)]
+    assert not missing, missing
+
+
+def test_status_strings_without_gpu(lib):
+    f = lib.adi_status_string
+    f.restype = ctypes.c_char_p
+    f.argtypes = [ctypes.c_int]
+    assert f(0) == b"ADI_OK" and f(4) == b"ADI_ESTATE" and f(99) == b"ADI_UNKNOWN"
+    g = lib.adi_last_error
+    g.restype = ctypes.c_char_p
+    g.argtypes = [ctypes.c_void_p]
+    assert g(None)  # never NULL
+
+
+def test_invalid_arguments_rejected_before_any_cuda_call(lib):
+    from paper_2103_06998_gb300 import adi
+    L = adi.load_library()
+    h = ctypes.c_void_p()
+    assert L.adi_create(0, 4, 4, 2, 0.1, None, None, None, None, ctypes.byref(h)) == adi.ADI_EINVAL
+    assert L.adi_create(4, 4, 4, 7, 0.1, None, None, None, None, ctypes.byref(h)) == adi.ADI_EINVAL
+    assert L.adi_create(4, 4, 4, 2, -1.0, None, None, None, None, ctypes.byref(h)) == adi.ADI_EINVAL
+    import numpy as np
+    bad = np.full(64, -1.0)
+    assert L.adi_create(4, 4, 4, 2, 0.1, adi._dptr(bad), None, None, None, ctypes.byref(h)) == adi.ADI_EINVAL
+    assert b"eps and mu" in L.adi_last_error(None)
+    assert L.adi_step(None, 1) == adi.ADI_EINVAL

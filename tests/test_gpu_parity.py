@@ -1,0 +1,204 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the FP64 CPU oracle.
+
+Tolerances: the FP64 GPU path must agree with the oracle to 1e-11 relative L2
+(only the summation order differs); the FP32 path to 1e-5 relative L2 per step
+from an identical state (coefficient l2 norm over all six components) for
+p <= 2.  FP32 rounding after the line solves grows with the condition number
+of the 3D mass matrix, kappa_1D^3; for p = 3 the bound is scaled by
+(kappa_1D(3) / kappa_1D(2))^3 (about 16), computed below.
+"""
+import numpy as np
+import pytest
+
+from oracle import maxwell_adi as ma
+from oracle import manufactured as mf
+from oracle import material
+from paper_2103_06998_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-11, "fp32": 1e-5}
+
+
+def tol(prec, p):
+    if prec == "fp64" or p <= 2:
+        return TOL[prec]
+    from oracle import bspline
+    k = lambda q: np.linalg.cond(bspline.matrices_1d(32, q)[0])
+    return TOL[prec] * (k(p) / k(2)) ** 3
+
+
+def _adi():
+    from paper_2103_06998_gb300 import adi
+    return adi
+
+
+def rel(a, b):
+    num = sum(np.sum((np.asarray(x, np.float64) - y) ** 2) for x, y in zip(a, b))
+    den = sum(np.sum(np.asarray(y) ** 2) for y in b)
+    return float(np.sqrt(num / den))
+
+
+def _setup(n, p, tau, mat, prec, src=None, seed=3, t0=0.0):
+    if mat == "uniform":
+        eps = mu = sigma = None
+    elif mat == "head":
+        eps, mu, sigma, _ = inputs.head_map(n, 2103)
+    else:
+        eps, mu, sigma = inputs.random_material(n, 7, mu_range=(1.0, 2.0))
+    prob = ma.make_problem(n, p, tau, eps, mu, sigma)
+    s = _adi().Solver(n, p, tau, eps, mu, sigma, precision=prec)
+    s.factor()
+    if src is not None:
+        ma.set_source(prob, src["x0"], src["comp"], src["amp"], src["f0"], src["t0"], src["s"])
+        s.set_source(src["x0"], src["comp"], src["amp"], src["f0"], src["t0"], src["s"])
+    state = ma.apply_dirichlet(list(inputs.random_fields(prob.shape, seed)))
+    s.set_fields(np.array(state), t0)
+    return prob, s, state
+
+
+# ragged multi-tile sizes: RHS tiles are 32 x 8 x 8, line tiles 64 lines
+SMALL = [((37, 19, 11), 2, "head"), ((13, 30, 9), 1, "random"), ((11, 9, 21), 3, "random"),
+         ((5, 4, 3), 2, "uniform")]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n,p,mat", SMALL)
+def test_each_substep_matches_oracle(n, p, mat, prec):
+    tau = 0.03
+    src = inputs.dipole(2103)
+    prob, s, st = _setup(n, p, tau, mat, prec, src=src, t0=1.37)
+    E, H = st[:3], st[3:]
+    t = 1.37
+    E_half = ma.solve_E(prob, 1, ma.rhs_E(prob, 1, E, H, t + 0.25 * tau))
+    H_half = ma.solve_H(prob, ma.rhs_H(prob, H, E, E_half))
+    E_new = ma.solve_E(prob, 2, ma.rhs_E(prob, 2, E_half, H_half, t + 0.75 * tau))
+    H_new = ma.solve_H(prob, ma.rhs_H(prob, H_half, E_new, E_half))
+    # the state buffers after each sub-solve: 0 writes E_half, 2 writes E_new
+    s.substep(0)
+    s.substep(1)
+    s.substep(2)
+    s.substep(3)
+    got, tt = s.fields()
+    s.close()
+    assert abs(tt - (t + tau)) < 1e-12
+    err = rel(got, E_new + H_new)
+    assert err < tol(prec, p), err
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_graph_step_equals_substeps(prec):
+    n, p, tau = (20, 17, 12), 2, 0.02
+    src = inputs.dipole(2103)
+    prob, s, st = _setup(n, p, tau, "head", prec, src=src, t0=1.2)
+    ref, _ = ma.run(prob, st, 1.2, 3)
+    s.step(3)
+    got, t = s.fields()
+    assert abs(t - (1.2 + 3 * tau)) < 1e-12
+    assert rel(got, ref) < 3 * TOL[prec]
+    # the same three steps through sub-solves give the same bits
+    s2 = _adi().Solver(n, p, tau, *inputs.head_map(n, 2103)[:3], precision=prec, use_graph=False)
+    s2.factor()
+    s2.set_source(src["x0"], src["comp"], src["amp"], src["f0"], src["t0"], src["s"])
+    s2.set_fields(np.array(st), 1.2)
+    for _ in range(3):
+        for w in range(4):
+            s2.substep(w)
+    got2, _ = s2.fields()
+    s.close()
+    s2.close()
+    assert np.array_equal(got, got2)
+
+
+def test_config1_manufactured_fp64_against_oracle_and_exact():
+    # 16^3, p = 2, FP64, u_A with eps = mu = 1, sigma = 0, tau = 1e-2, 10 steps
+    n, p, tau, steps = (16, 16, 16), 2, 1e-2, 10
+    prob = ma.make_problem(n, p, tau)
+    st = mf.project(lambda a, b, c: mf.u_A(a, b, c, 0.0), n, p, prob.mats)
+    ref, t = ma.run(prob, st, 0.0, steps)
+    s = _adi().Solver(n, p, tau, precision="fp64")
+    s.factor()
+    s.set_fields(np.array(st), 0.0)
+    s.step(steps)
+    got, tg = s.fields()
+    s.close()
+    assert abs(tg - t) < 1e-12
+    assert rel(got, ref) < 1e-11
+    eL2E, eL2H, _, _ = mf.errors(list(got), n, p, t)
+    assert eL2E < 2e-4 and eL2H < 2e-4
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_config2_head_dipole_64(prec):
+    # 64^3, p = 2, head map, dipole, tau = 4 dt_CFL: one step from an identical
+    # state (per-step error) and a 5-step trajectory
+    n, p = (64, 64, 64), 2
+    eps, mu, sigma, _ = inputs.head_map(n, 2103)
+    tau = 4.0 * material.cfl_dt(n, p, material.row_hats(eps, n, p), material.row_hats(mu, n, p))
+    src = inputs.dipole(2103)
+    prob, s, st = _setup(n, p, tau, "head", prec, src=src, t0=1.5)
+    assert abs(s.cfl_dt() - tau / 4.0) < 1e-9 * tau
+    ref1, _ = ma.run(prob, st, 1.5, 1)
+    s.step(1)
+    got1, _ = s.fields()
+    assert rel(got1, ref1) < TOL[prec]
+    ref5, _ = ma.run(prob, ref1, 1.5 + tau, 4)
+    s.step(4)
+    got5, _ = s.fields()
+    s.close()
+    assert rel(got5, ref5) < 5 * TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp32"])
+def test_full_size_256_one_step(prec):
+    # the benchmark's workload: 256^3, p = 2, head map, dipole, tau = 4 dt_CFL,
+    # one step compared element by element with the oracle
+    n, p = (256, 256, 256), 2
+    eps, mu, sigma, _ = inputs.head_map(n, 2103)
+    prob = ma.make_problem(n, p, 1.0, eps, mu, sigma)
+    tau = 4.0 * material.cfl_dt(n, p, material.row_hats(eps, n, p), material.row_hats(mu, n, p))
+    prob = ma.make_problem(n, p, tau, eps, mu, sigma)
+    src = inputs.dipole(2103)
+    ma.set_source(prob, src["x0"], src["comp"], src["amp"], src["f0"], src["t0"], src["s"])
+    st = ma.apply_dirichlet(list(inputs.random_fields(prob.shape, 3)))
+    ref, _ = ma.run(prob, st, 1.5, 1)
+    s = _adi().Solver(n, p, tau, eps, mu, sigma, precision=prec)
+    s.factor()
+    s.set_source(src["x0"], src["comp"], src["amp"], src["f0"], src["t0"], src["s"])
+    s.set_fields(np.array(st), 1.5)
+    s.step(1)
+    got, _ = s.fields()
+    s.close()
+    assert rel(got, ref) < TOL[prec]
+
+
+def test_error_paths():
+    adi = _adi()
+    s = adi.Solver((4, 4, 4), 2, 0.1)
+    with pytest.raises(adi.AdiError) as e:
+        s.step(1)
+    assert e.value.status == adi.ADI_ESTATE
+    s.factor()
+    bad = np.zeros((6, 6, 6, 6))
+    bad[0, 2, 2, 2] = np.nan
+    with pytest.raises(adi.AdiError) as e:
+        s.set_fields(bad)
+    assert e.value.status == adi.ADI_ENUMERIC
+    with pytest.raises(adi.AdiError) as e:
+        s.set_source((1.5, 0.5, 0.5), 2, 1.0, 2.0, 1.5, 0.5)
+    assert e.value.status == adi.ADI_EINVAL
+    with pytest.raises(adi.AdiError) as e:
+        s.step(0)
+    assert e.value.status == adi.ADI_EINVAL
+    s.close()
+
+
+def test_set_fields_enforces_boundary_constraints():
+    adi = _adi()
+    n, p = (6, 5, 4), 2
+    s = adi.Solver(n, p, 0.1, precision="fp64")
+    raw = inputs.random_fields((n[2] + p, n[1] + p, n[0] + p), 9)
+    s.set_fields(raw)
+    got, _ = s.fields()
+    s.close()
+    np.testing.assert_array_equal(got, np.array(ma.apply_dirichlet(list(raw))))
