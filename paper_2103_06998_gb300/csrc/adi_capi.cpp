@@ -218,6 +218,15 @@ adi_status adi_create(int nx, int ny, int nz, int p, double dt, const double* ep
       return cuda_fail(nullptr, e, "adi_create: upload material");
     }
   }
+  c->mu_uniform = true;
+  c->mu_value = mu ? mu[0] : 1.0;
+  if (mu)
+    for (size_t i = 1; i < ne; ++i)
+      if (mu[i] != mu[0]) {
+        c->mu_uniform = false;
+        break;
+      }
+  c->d_uniform = dt / (2.0 * c->mu_value);
   for (int d = 0; d < 3; ++d) adi::build_axis(c->n[d], p, c->axes[d]);
   e = adi::compute_coefficients(*c);
   if (e == cudaSuccess) {
@@ -250,6 +259,7 @@ adi_status adi_set_dt(adi_handle h, double dt) {
   if (!h) return fail(nullptr, ADI_EINVAL, "adi_set_dt: NULL handle");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(h, ADI_EINVAL, "adi_set_dt: dt must be finite and > 0");
   h->dt = dt;
+  h->d_uniform = dt / (2.0 * h->mu_value);
   cudaError_t e = adi::compute_coefficients(*h);
   if (e != cudaSuccess) return cuda_fail(h, e, "adi_set_dt");
   drop_graph(h);

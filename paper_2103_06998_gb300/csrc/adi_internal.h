@@ -43,6 +43,9 @@ struct AxisDev {
   const T* luInv[2];
   const T* luU[2];
   int N;
+  // rows inner_lo .. inner_hi of M, S, A, B equal the interior stencil inner[op]
+  T inner[4][2 * kMaxP + 1];
+  int inner_lo, inner_hi;
 };
 
 struct Term {
@@ -51,6 +54,14 @@ struct Term {
   int op[3];   // Op for x, y, z
   int coef;    // Coef
   float sign;  // +1 or -1
+};
+
+// Interior (translation-invariant) stencils of M, A, B on one axis: rows
+// 2p .. N-1-2p of the band tables are all equal for open uniform knots.
+template <typename T>
+struct Stencils {
+  T w[3][2 * kMaxP + 1];  // [M, A, B][tap]
+  int lo, hi;             // interior rows: lo <= row <= hi (lo > hi: none)
 };
 
 template <typename T>
@@ -72,6 +83,7 @@ struct RhsParams {
   const double* clock_t0;
   long long* clock_step;
   int advance_clock;   // 1: block 0 thread 0 increments the step counter
+  Stencils<T> st[3];   // interior stencils per axis (E kernel)
 };
 
 struct LineParams {
@@ -79,8 +91,22 @@ struct LineParams {
   int N;          // line length
   long long nlines;
   int Nx, Ny, Nz;
-  int lo, hi;     // solved rows (Dirichlet: 1 .. N-2)
-  int dirichlet;
+};
+
+enum LineMode : int { LM_MASS = 0, LM_STIFF = 1, LM_DERIV = 2 };
+
+// One array's line solve inside a launch (blockIdx.y selects the job).
+template <typename T>
+struct LineJob {
+  const T* src;   // right-hand side (MASS, STIFF) or the differentiated field (DERIV)
+  T* dst;         // result (may alias src or aux)
+  const T* aux;   // c (STIFF) or the field the derivative is added to (DERIV)
+  T scale;        // DERIV: dst = aux + scale * M^-1 A src
+  int dirichlet;  // 1: first and last coefficient are fixed to zero
+};
+template <typename T>
+struct LineJobs {
+  LineJob<T> job[3];
 };
 
 // ----------------------------------------------------------- the handle
@@ -112,6 +138,9 @@ struct Ctx {
   double* d_mu = nullptr;
   double* d_sigma = nullptr;
   double min_eps_mu = 1.0;
+  bool mu_uniform = false;  // all per-element mu equal: H half steps use 1D derivatives
+  double mu_value = 1.0;
+  double d_uniform = 0.0;   // tau / (2 mu) when mu_uniform
 
   // state and work (element type T = float or double), each Nc elements
   void* cur[6] = {};

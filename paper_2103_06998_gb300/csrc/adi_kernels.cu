@@ -186,42 +186,68 @@ __device__ __forceinline__ long long line_stride(const LineParams& lp) {
   return (long long)lp.Nx * lp.Ny;
 }
 
-template <typename T, int P, bool STIFF>
-__global__ void line_kernel(const T* src, T* dst, const LineParams lp, const AxisDev<T> ax,
-                            const T* __restrict__ cvec) {
+// Asynchronous global -> shared copy of one element (cp.async, no register
+// round trip); all copies of a tile are in flight together.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem) {
+  unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  if (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+__device__ __forceinline__ float fast_rcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
+
+// Stage one tile of lines (transposed to [k][line], pitch LP) with cp.async.
+template <typename T>
+__device__ __forceinline__ void stage_tile(T* s, const T* g, const LineParams& lp, long long L0, int cnt,
+                                           int LP) {
+  const int t = threadIdx.x, LINES = blockDim.x, N = lp.N;
+  if (lp.dir == 0) {
+    const T* base = g + L0 * N;
+    for (int line = 0; line < cnt; ++line)
+      for (int k = t; k < N; k += LINES) cp_async_elem(&s[k * LP + line], &base[(long long)line * N + k]);
+  } else if (t < cnt) {
+    const long long off = line_offset(lp, L0 + t), stride = line_stride(lp);
+    for (int k = 0; k < N; ++k) cp_async_elem(&s[k * LP + t], &g[off + k * stride]);
+  }
+}
+
+// Banded solves along one axis, one thread per line (Gaussian elimination
+// without pivoting restricted to the band; Appendix, eqs. split1/split2).
+//   LM_MASS : x = M^-1 r with the precomputed (full or Dirichlet) mass LU.
+//   LM_STIFF: x = (M + diag(c) S)^-1 r; the LU of each line is formed row by
+//             row from c (per-test-function material) and its normalised upper
+//             factors are kept in shared memory for the back substitution.
+//   LM_DERIV: out = base + scale * M^-1 (A u): the 1D derivative in the L2
+//             sense, used by the H half steps when mu is uniform.
+// blockIdx.y selects one of up to three independent jobs of the same axis.
+template <typename T, int P, int MODE>
+__global__ void __launch_bounds__(64) line_kernel(const LineJobs<T> jobs, const LineParams lp, const AxisDev<T> ax) {
   constexpr int W = 2 * P + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const LineJob<T> job = jobs.job[blockIdx.y];
   const int LINES = blockDim.x, LP = LINES + 1, N = lp.N;
-  T* sr = reinterpret_cast<T*>(smem_raw);  // [k][line], row pitch LP
-  T* su = sr + (size_t)N * LP;             // STIFF: P planes [q][k][line]
+  T* sr = reinterpret_cast<T*>(smem_raw);  // [k][line]
+  T* su = sr + (size_t)N * LP;             // LM_STIFF: c, then P planes of upper factors
   const int t = threadIdx.x;
   const long long L0 = (long long)blockIdx.x * LINES;
   const int cnt = (int)min((long long)LINES, lp.nlines - L0);
-  const long long stride = line_stride(lp);
 
-  // ---- stage the tile (coalesced), transposing x lines to [k][line]
-  if (lp.dir == 0) {
-    const T* base = src + L0 * N;
-    const T* cbase = STIFF ? cvec + L0 * N : nullptr;
-    for (int line = 0; line < cnt; ++line) {
-      for (int k = t; k < N; k += LINES) {
-        sr[k * LP + line] = base[(long long)line * N + k];
-        if (STIFF) su[k * LP + line] = cbase[(long long)line * N + k];
-      }
-    }
-  } else if (t < cnt) {
-    const long long off = line_offset(lp, L0 + t);
-#pragma unroll 8
-    for (int k = 0; k < N; ++k) {
-      sr[k * LP + t] = src[off + k * stride];
-      if (STIFF) su[k * LP + t] = cvec[off + k * stride];
-    }
-  }
+  stage_tile(sr, job.src, lp, L0, cnt, LP);
+  if (MODE == LM_STIFF) stage_tile(su, job.aux, lp, L0, cnt, LP);
+  cp_async_wait_all();
   __syncthreads();
 
   if (t < cnt) {
-    const int lo = lp.lo, hi = lp.hi;
-    if (STIFF) {
+    const int lo = job.dirichlet ? 1 : 0, hi = job.dirichlet ? N - 2 : N - 1;
+    const int ilo = ax.inner_lo, ihi = ax.inner_hi;
+    if (MODE == LM_STIFF) {
       const T* __restrict__ Mb = ax.band[OP_M];
       const T* __restrict__ Sb = ax.band[OP_S];
       T Uq[P][P + 1], invq[P], yq[P];
@@ -232,18 +258,20 @@ __global__ void line_kernel(const T* src, T* dst, const LineParams lp, const Axi
 #pragma unroll
         for (int e = 0; e <= P; ++e) Uq[m][e] = T(0);
       }
-      for (int k = lo; k <= hi; ++k) {
-        const T ck = su[k * LP + t];
+      // one row of the on-the-fly Doolittle LU of M + c S and the forward step
+      auto row = [&](int k, T ck, T rk, bool inner) {
         T a[W];
 #pragma unroll
         for (int d = 0; d < W; ++d) {
-          int j = k + d - P;
-          a[d] = (j >= lo && j <= hi) ? Mb[k * W + d] + ck * Sb[k * W + d] : T(0);
+          const int j = k + d - P;
+          const T mv = inner ? ax.inner[OP_M][d] : Mb[k * W + d];
+          const T sv = inner ? ax.inner[OP_S][d] : Sb[k * W + d];
+          a[d] = (j >= lo && j <= hi) ? mv + ck * sv : T(0);
         }
         T l[P + 1];
         l[0] = T(0);
 #pragma unroll
-        for (int q = P; q >= 1; --q) {  // column k - q
+        for (int q = P; q >= 1; --q) {  // multiplier of row k - q
           T s = a[P - q];
 #pragma unroll
           for (int m = q + 1; m <= P; ++m) s -= l[m] * Uq[m - 1][m - q];
@@ -258,8 +286,8 @@ __global__ void line_kernel(const T* src, T* dst, const LineParams lp, const Axi
             if (e + m <= P) s -= l[m] * Uq[m - 1][e + m];
           Un[e] = s;
         }
-        const T inv = T(1) / Un[0];
-        T y = sr[k * LP + t];
+        const T inv = fast_rcp(Un[0]);
+        T y = rk;
 #pragma unroll
         for (int m = 1; m <= P; ++m) y -= l[m] * yq[m - 1];
         sr[k * LP + t] = y * inv;
@@ -276,11 +304,44 @@ __global__ void line_kernel(const T* src, T* dst, const LineParams lp, const Axi
         yq[0] = y;
 #pragma unroll
         for (int e = 0; e <= P; ++e) Uq[0][e] = Un[e];
+      };
+      int k = lo;
+      for (; k + 3 <= hi; k += 4) {
+        T cc[4], rr[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          cc[u] = su[(k + u) * LP + t];
+          rr[u] = sr[(k + u) * LP + t];
+        }
+        const bool inner = k - P >= ilo && k + 3 + P <= ihi;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) row(k + u, cc[u], rr[u], inner);
       }
+      for (; k <= hi; ++k) row(k, su[k * LP + t], sr[k * LP + t], false);
       T xq[P];
 #pragma unroll
       for (int m = 0; m < P; ++m) xq[m] = T(0);
-      for (int k = hi; k >= lo; --k) {
+      k = hi;
+      for (; k - 3 >= lo; k -= 4) {
+        T yy[4], uu[4][P];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          yy[u] = sr[(k - u) * LP + t];
+#pragma unroll
+          for (int e = 1; e <= P; ++e) uu[u][e - 1] = su[((size_t)(e - 1) * N + k - u) * LP + t];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          T x = yy[u];
+#pragma unroll
+          for (int e = 1; e <= P; ++e) x -= uu[u][e - 1] * xq[e - 1];
+          sr[(k - u) * LP + t] = x;
+#pragma unroll
+          for (int m = P - 1; m >= 1; --m) xq[m] = xq[m - 1];
+          xq[0] = x;
+        }
+      }
+      for (; k >= lo; --k) {
         T x = sr[k * LP + t];
 #pragma unroll
         for (int e = 1; e <= P; ++e) x -= su[((size_t)(e - 1) * N + k) * LP + t] * xq[e - 1];
@@ -290,26 +351,93 @@ __global__ void line_kernel(const T* src, T* dst, const LineParams lp, const Axi
         xq[0] = x;
       }
     } else {
-      const int dch = lp.dirichlet;
-      const T* __restrict__ Lt = ax.luL[dch];
-      const T* __restrict__ It = ax.luInv[dch];
-      const T* __restrict__ Ut = ax.luU[dch];
+      const int dch = job.dirichlet;
+      const T* __restrict__ Lt = dch ? ax.luL[1] : ax.luL[0];
+      const T* __restrict__ It = dch ? ax.luInv[1] : ax.luInv[0];
+      const T* __restrict__ Ut = dch ? ax.luU[1] : ax.luU[0];
+      const T* __restrict__ Ab = ax.band[OP_A];
+      // LM_DERIV: the right-hand side of row k is (A u)_k; a register window
+      // keeps u[k-P .. k+P] because sr[k] is overwritten by the elimination.
+      T win[W];
+      if (MODE == LM_DERIV) {
+#pragma unroll
+        for (int d = 0; d < W; ++d) {
+          int j = lo + d - P;
+          win[d] = (j >= 0 && j < N) ? sr[j * LP + t] : T(0);
+        }
+      }
       T yq[P];
 #pragma unroll
       for (int m = 0; m < P; ++m) yq[m] = T(0);
-      for (int k = lo; k <= hi; ++k) {
-        T y = sr[k * LP + t];
+      auto fwd = [&](int k, T rk, const T* lk, bool inner) {
+        T y = rk;
+        if (MODE == LM_DERIV) {
+          y = T(0);
 #pragma unroll
-        for (int m = 1; m <= P; ++m) y -= Lt[k * P + m - 1] * yq[m - 1];
+          for (int d = 0; d < W; ++d) y += (inner ? ax.inner[OP_A][d] : Ab[k * W + d]) * win[d];
+#pragma unroll
+          for (int d = 0; d < W - 1; ++d) win[d] = win[d + 1];
+          win[W - 1] = rk;  // u[k + P + 1], loaded by the caller
+        }
+#pragma unroll
+        for (int m = 1; m <= P; ++m) y -= lk[m - 1] * yq[m - 1];
         sr[k * LP + t] = y;
 #pragma unroll
         for (int m = P - 1; m >= 1; --m) yq[m] = yq[m - 1];
         yq[0] = y;
+      };
+      // MASS: rk = r[k]; DERIV: rk = u[k + P + 1] (the next window entry)
+      auto load_rk = [&](int k) -> T {
+        if (MODE == LM_DERIV) {
+          const int j = k + P + 1;
+          return j < N ? sr[j * LP + t] : T(0);
+        }
+        return sr[k * LP + t];
+      };
+      int k = lo;
+      for (; k + 3 <= hi; k += 4) {
+        T rr[4], ll[4][P];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          rr[u] = load_rk(k + u);
+#pragma unroll
+          for (int m = 0; m < P; ++m) ll[u][m] = Lt[(k + u) * P + m];
+        }
+        const bool inner = k - P >= ilo && k + 3 + P <= ihi;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) fwd(k + u, rr[u], ll[u], inner);
+      }
+      for (; k <= hi; ++k) {
+        T lk[P];
+#pragma unroll
+        for (int m = 0; m < P; ++m) lk[m] = Lt[k * P + m];
+        fwd(k, load_rk(k), lk, false);
       }
       T xq[P];
 #pragma unroll
       for (int m = 0; m < P; ++m) xq[m] = T(0);
-      for (int k = hi; k >= lo; --k) {
+      k = hi;
+      for (; k - 3 >= lo; k -= 4) {
+        T yy[4], iv[4], uu[4][P];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          yy[u] = sr[(k - u) * LP + t];
+          iv[u] = It[k - u];
+#pragma unroll
+          for (int e = 0; e < P; ++e) uu[u][e] = Ut[(k - u) * P + e];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          T x = iv[u] * yy[u];
+#pragma unroll
+          for (int e = 1; e <= P; ++e) x -= uu[u][e - 1] * xq[e - 1];
+          sr[(k - u) * LP + t] = x;
+#pragma unroll
+          for (int m = P - 1; m >= 1; --m) xq[m] = xq[m - 1];
+          xq[0] = x;
+        }
+      }
+      for (; k >= lo; --k) {
         T x = It[k] * sr[k * LP + t];
 #pragma unroll
         for (int e = 1; e <= P; ++e) x -= Ut[k * P + e - 1] * xq[e - 1];
@@ -324,15 +452,288 @@ __global__ void line_kernel(const T* src, T* dst, const LineParams lp, const Axi
   }
   __syncthreads();
 
-  // ---- write back
+  // ---- write back (LM_DERIV: out = base + scale * x)
+  const T scale = job.scale;
   if (lp.dir == 0) {
-    T* base = dst + L0 * N;
+    T* base = job.dst + L0 * N;
+    const T* b0 = MODE == LM_DERIV ? job.aux + L0 * N : nullptr;
     for (int line = 0; line < cnt; ++line)
-      for (int k = t; k < N; k += LINES) base[(long long)line * N + k] = sr[k * LP + line];
+      for (int k = t; k < N; k += LINES) {
+        long long g = (long long)line * N + k;
+        T v = sr[k * LP + line];
+        if (MODE == LM_DERIV) v = b0[g] + scale * v;
+        base[g] = v;
+      }
   } else if (t < cnt) {
-    const long long off = line_offset(lp, L0 + t);
-#pragma unroll 8
-    for (int k = 0; k < N; ++k) dst[off + k * stride] = sr[k * LP + t];
+    const long long off = line_offset(lp, L0 + t), stride = line_stride(lp);
+#pragma unroll 4
+    for (int k = 0; k < N; ++k) {
+      T v = sr[k * LP + t];
+      if (MODE == LM_DERIV) v = job.aux[off + k * stride] + scale * v;
+      job.dst[off + k * stride] = v;
+    }
+  }
+}
+
+// ------------------------------------------------- E right-hand side (v2)
+// One CTA per 32 x 8 x 8 output tile (256 threads).  For each of the six input
+// fields a (8+2P) x (8+2P) x (32+2P) tile with halo is staged by cp.async
+// (double buffered across fields) and contracted by sum factorisation: a z pass
+// (thread per haloed (y,x) column, 8 outputs from a register window), a y pass
+// (thread per (z',x) column) and an x pass (thread per two x outputs in four
+// (z',y) rows), accumulating the a-, b- and c-scaled terms into registers.
+// Each field enters exactly two terms of eq. (dupa1ab) (half step 1) or of its
+// half-step-2 analogue (R2 instead of R1); the term plan is a compile-time
+// table, so interior stencils are constant operands.  Rows near the boundary
+// (outside 2p .. N-1-2p) read their band rows from the tables instead.
+namespace rhs2 {
+constexpr int TX = 32, TY = 8, TZ = 8, NT = 256;
+
+// the two terms of field F in half step H: ops per axis, output, coefficient, sign
+template <int H, int F>
+struct Plan;
+#define ADI_PLAN(H, F, X0, Y0, Z0, O0, C0, S0, X1, Y1, Z1, O1, C1, S1)                   \
+  template <>                                                                             \
+  struct Plan<H, F> {                                                                     \
+    static constexpr int x0 = X0, y0 = Y0, z0 = Z0, o0 = O0, c0 = C0;                     \
+    static constexpr int x1 = X1, y1 = Y1, z1 = Z1, o1 = O1, c1 = C1;                     \
+    static constexpr float s0 = S0, s1 = S1;                                              \
+  };
+// E1: a M(x)M(x)M E1 ; R1[3][1] = B(x)M(x)A -> E3 (c) ; R2[2][1] = B(x)A(x)M -> E2 (c)
+ADI_PLAN(1, 0, OP_M, OP_M, OP_M, 0, CF_A, 1.f, OP_B, OP_M, OP_A, 2, CF_C, 1.f)
+ADI_PLAN(2, 0, OP_M, OP_M, OP_M, 0, CF_A, 1.f, OP_B, OP_A, OP_M, 1, CF_C, 1.f)
+// E2: a MMM E2 ; R1[1][2] = A(x)B(x)M -> E1 ; R2[3][2] = M(x)B(x)A -> E3
+ADI_PLAN(1, 1, OP_M, OP_M, OP_M, 1, CF_A, 1.f, OP_A, OP_B, OP_M, 0, CF_C, 1.f)
+ADI_PLAN(2, 1, OP_M, OP_M, OP_M, 1, CF_A, 1.f, OP_M, OP_B, OP_A, 2, CF_C, 1.f)
+// E3: a MMM E3 ; R1[2][3] = M(x)A(x)B -> E2 ; R2[1][3] = A(x)M(x)B -> E1
+ADI_PLAN(1, 2, OP_M, OP_M, OP_M, 2, CF_A, 1.f, OP_M, OP_A, OP_B, 1, CF_C, 1.f)
+ADI_PLAN(2, 2, OP_M, OP_M, OP_M, 2, CF_A, 1.f, OP_A, OP_M, OP_B, 0, CF_C, 1.f)
+// curl H = (C1 - C2) H scaled by b (both half steps):
+// H1: +d3 H1 -> E2, -d2 H1 -> E3 ; H2: -d3 H2 -> E1, +d1 H2 -> E3 ; H3: +d2 H3 -> E1, -d1 H3 -> E2
+ADI_PLAN(1, 3, OP_M, OP_M, OP_A, 1, CF_B, 1.f, OP_M, OP_A, OP_M, 2, CF_B, -1.f)
+ADI_PLAN(2, 3, OP_M, OP_M, OP_A, 1, CF_B, 1.f, OP_M, OP_A, OP_M, 2, CF_B, -1.f)
+ADI_PLAN(1, 4, OP_M, OP_M, OP_A, 0, CF_B, -1.f, OP_A, OP_M, OP_M, 2, CF_B, 1.f)
+ADI_PLAN(2, 4, OP_M, OP_M, OP_A, 0, CF_B, -1.f, OP_A, OP_M, OP_M, 2, CF_B, 1.f)
+ADI_PLAN(1, 5, OP_M, OP_A, OP_M, 0, CF_B, 1.f, OP_A, OP_M, OP_M, 1, CF_B, -1.f)
+ADI_PLAN(2, 5, OP_M, OP_A, OP_M, 0, CF_B, 1.f, OP_A, OP_M, OP_M, 1, CF_B, -1.f)
+#undef ADI_PLAN
+
+__host__ __device__ constexpr int sidx(int op) { return op == OP_M ? 0 : (op == OP_A ? 1 : 2); }
+
+// band value X[r][q] of op on axis D: interior rows use the constant stencil
+template <typename T, int P, int D, int OP, bool INNER>
+__device__ __forceinline__ T bandv(const RhsParams<T>& prm, int r, int q) {
+  if (INNER) return prm.st[D].w[sidx(OP)][q];
+  return prm.ax[D].band[OP][r * (2 * P + 1) + q];
+}
+
+template <typename T, int P>
+struct Smem {
+  static constexpr int HX = TX + 2 * P, HY = TY + 2 * P, HZ = TZ + 2 * P;
+  static constexpr int TILE = HZ * HY * HX, ZR = TZ * HY * HX, YR = TZ * TY * HX;
+};
+
+// z pass: column i of the haloed plane, 8 outputs from a window of HZ values
+template <typename T, int P, int OP, bool INNER>
+__device__ __forceinline__ void zpass(const RhsParams<T>& prm, const T* tl, T* zr, int z0, int i) {
+  using S = Smem<T, P>;
+  constexpr int W = 2 * P + 1;
+  T w[S::HZ];
+#pragma unroll
+  for (int k = 0; k < S::HZ; ++k) w[k] = tl[k * S::HY * S::HX + i];
+#pragma unroll
+  for (int zz = 0; zz < TZ; ++zz) {
+    T s = T(0);
+#pragma unroll
+    for (int q = 0; q < W; ++q) s += bandv<T, P, 2, OP, INNER>(prm, z0 + zz, q) * w[zz + q];
+    zr[zz * S::HY * S::HX + i] = s;
+  }
+}
+
+// y pass: column (zz, xx), 8 outputs from a window of HY values
+template <typename T, int P, int OP, bool INNER>
+__device__ __forceinline__ void ypass(const RhsParams<T>& prm, const T* zr, T* yr, int y0, int zz, int xx) {
+  using S = Smem<T, P>;
+  constexpr int W = 2 * P + 1;
+  T w[S::HY];
+  const T* src = zr + zz * S::HY * S::HX + xx;
+#pragma unroll
+  for (int k = 0; k < S::HY; ++k) w[k] = src[k * S::HX];
+#pragma unroll
+  for (int yy = 0; yy < TY; ++yy) {
+    T s = T(0);
+#pragma unroll
+    for (int q = 0; q < W; ++q) s += bandv<T, P, 1, OP, INNER>(prm, y0 + yy, q) * w[yy + q];
+    yr[(zz * TY + yy) * S::HX + xx] = s;
+  }
+}
+
+// x pass for two consecutive x outputs in four rows; adds coef * sign * value
+template <typename T, int P, int OP, bool INNER, int OUT, int CK>
+__device__ __forceinline__ void xpass(const RhsParams<T>& prm, const T* yr, int gx, int xp, int rg, float sg,
+                                      T (&cf)[3][4][2], T (&acc)[3][4][2]) {
+  using S = Smem<T, P>;
+  constexpr int W = 2 * P + 1;
+  T bx[2][W];
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int q = 0; q < W; ++q) bx[j][q] = bandv<T, P, 0, OP, INNER>(prm, min(gx + j, prm.Nx - 1), q);
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const T* src = yr + (rg * 4 + r) * S::HX + xp;
+    T w[W + 1];
+#pragma unroll
+    for (int q = 0; q < W + 1; ++q) w[q] = src[q];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      T s = T(0);
+#pragma unroll
+      for (int q = 0; q < W; ++q) s += bx[j][q] * w[j + q];
+      acc[OUT][r][j] += (T(sg) * cf[CK][r][j]) * s;
+    }
+  }
+}
+
+template <typename T, int P>
+__device__ __forceinline__ void stage(const RhsParams<T>& prm, int f, T* s, int x0, int y0, int z0) {
+  using S = Smem<T, P>;
+  const T* __restrict__ g = prm.fields[f];
+  const int Nx = prm.Nx, Ny = prm.Ny, Nz = prm.Nz;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int row = warp; row < S::HZ * S::HY; row += NT / 32) {
+    const int yy = row % S::HY, zz = row / S::HY;
+    const int Y = y0 - P + yy, Z = z0 - P + zz;
+    T* srow = s + row * S::HX;
+    const bool rin = Y >= 0 && Y < Ny && Z >= 0 && Z < Nz;
+    const T* grow = g + ((long long)Z * Ny + Y) * Nx;
+    for (int xx = lane; xx < S::HX; xx += 32) {
+      const int X = x0 - P + xx;
+      if (rin && X >= 0 && X < Nx) cp_async_elem(&srow[xx], &grow[X]);
+      else srow[xx] = T(0);
+    }
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+template <typename T, int P, int H, int F>
+__device__ __forceinline__ void do_field(const RhsParams<T>& prm, T* s_tile, T* s_zr, T* s_yr, int x0, int y0,
+                                         int z0, bool inZ, bool inY, bool inX, int xp, int rg,
+                                         T (&cf)[3][4][2], T (&acc)[3][4][2]) {
+  using S = Smem<T, P>;
+  using PL = Plan<H, F>;
+  const int tid = threadIdx.x;
+  if (F + 1 < 6) {
+    stage<T, P>(prm, F + 1, s_tile + ((F + 1) & 1) * S::TILE, x0, y0, z0);
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+  } else {
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  }
+  __syncthreads();
+  const T* tl = s_tile + (F & 1) * S::TILE;
+  constexpr bool zshare = PL::z0 == PL::z1;
+  for (int i = tid; i < S::HY * S::HX; i += NT) {
+    if (inZ) zpass<T, P, PL::z0, true>(prm, tl, s_zr, z0, i);
+    else zpass<T, P, PL::z0, false>(prm, tl, s_zr, z0, i);
+    if (!zshare) {
+      if (inZ) zpass<T, P, PL::z1, true>(prm, tl, s_zr + S::ZR, z0, i);
+      else zpass<T, P, PL::z1, false>(prm, tl, s_zr + S::ZR, z0, i);
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < TZ * S::HX; i += NT) {
+    const int zz = i / S::HX, xx = i % S::HX;
+    if (inY) {
+      ypass<T, P, PL::y0, true>(prm, s_zr, s_yr, y0, zz, xx);
+      ypass<T, P, PL::y1, true>(prm, s_zr + (zshare ? 0 : S::ZR), s_yr + S::YR, y0, zz, xx);
+    } else {
+      ypass<T, P, PL::y0, false>(prm, s_zr, s_yr, y0, zz, xx);
+      ypass<T, P, PL::y1, false>(prm, s_zr + (zshare ? 0 : S::ZR), s_yr + S::YR, y0, zz, xx);
+    }
+  }
+  __syncthreads();
+  const int gx = x0 + xp;  // band rows are clamped per output inside xpass
+  if (inX) {
+    xpass<T, P, PL::x0, true, PL::o0, PL::c0 - CF_A>(prm, s_yr, gx, xp, rg, PL::s0, cf, acc);
+    xpass<T, P, PL::x1, true, PL::o1, PL::c1 - CF_A>(prm, s_yr + S::YR, gx, xp, rg, PL::s1, cf, acc);
+  } else {
+    xpass<T, P, PL::x0, false, PL::o0, PL::c0 - CF_A>(prm, s_yr, gx, xp, rg, PL::s0, cf, acc);
+    xpass<T, P, PL::x1, false, PL::o1, PL::c1 - CF_A>(prm, s_yr + S::YR, gx, xp, rg, PL::s1, cf, acc);
+  }
+  __syncthreads();
+}
+}  // namespace rhs2
+
+template <typename T, int P, int H>
+__global__ void __launch_bounds__(rhs2::NT, sizeof(T) == 4 ? 2 : 1) rhs_e_kernel(const RhsParams<T> prm) {
+  using namespace rhs2;
+  using S = Smem<T, P>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* s_tile = reinterpret_cast<T*>(smem_raw);  // 2 x TILE (double buffer)
+  T* s_zr = s_tile + 2 * S::TILE;               // 2 x ZR
+  T* s_yr = s_zr + 2 * S::ZR;                   // 2 x YR
+  const int tid = threadIdx.x;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
+  const int Nx = prm.Nx, Ny = prm.Ny, Nz = prm.Nz;
+  const long long sxy = (long long)Nx * Ny;
+  // tile-level interior tests (band rows of all outputs of the tile)
+  const bool inZ = z0 >= prm.st[2].lo && z0 + TZ - 1 <= prm.st[2].hi;
+  const bool inY = y0 >= prm.st[1].lo && y0 + TY - 1 <= prm.st[1].hi;
+  // x pass: two consecutive x (xp) in four consecutive (z',y) rows
+  const int xp = (tid % 16) * 2, rg = tid / 16;
+  const bool inX = x0 + xp >= prm.st[0].lo && x0 + xp + 1 <= prm.st[0].hi;
+  T cf[3][4][2], acc[3][4][2];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int row = rg * 4 + r, zz = row / TY, yy = row % TY;
+    const int gz = z0 + zz, gy = y0 + yy;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int gx = x0 + xp + j;
+      const bool in = gx < Nx && gy < Ny && gz < Nz;
+      const long long g = gz * sxy + (long long)gy * Nx + gx;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        cf[c][r][j] = in ? prm.coef[1 + c][g] : T(0);
+        acc[c][r][j] = T(0);
+      }
+    }
+  }
+  stage<T, P>(prm, 0, s_tile, x0, y0, z0);
+  do_field<T, P, H, 0>(prm, s_tile, s_zr, s_yr, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+  do_field<T, P, H, 1>(prm, s_tile, s_zr, s_yr, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+  do_field<T, P, H, 2>(prm, s_tile, s_zr, s_yr, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+  do_field<T, P, H, 3>(prm, s_tile, s_zr, s_yr, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+  do_field<T, P, H, 4>(prm, s_tile, s_zr, s_yr, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+  do_field<T, P, H, 5>(prm, s_tile, s_zr, s_yr, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+
+  // ---- point source and store (two consecutive x per row)
+  double g = 0.0;
+  if (prm.src_comp >= 0) {
+    double tm = *prm.clock_t0 + ((double)*prm.clock_step + prm.t_frac) * prm.tau;
+    double u = tm - prm.src_t0;
+    g = prm.src_amp * sin(2.0 * 3.14159265358979323846 * prm.src_f0 * u) * exp(-(u / prm.src_s) * (u / prm.src_s));
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int row = rg * 4 + r, zz = row / TY, yy = row % TY;
+      const int gz = z0 + zz, gy = y0 + yy;
+      if (gz >= Nz || gy >= Ny) continue;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int gx = x0 + xp + j;
+        if (gx >= Nx) continue;
+        T v = acc[c][r][j];
+        if (c == prm.src_comp) {
+          int ix = gx - prm.src_i0[0], iy = gy - prm.src_i0[1], iz = gz - prm.src_i0[2];
+          if (ix >= 0 && ix <= P && iy >= 0 && iy <= P && iz >= 0 && iz <= P)
+            v -= cf[1][r][j] * T(g) * prm.src_w[0][ix] * prm.src_w[1][iy] * prm.src_w[2][iz];
+        }
+        prm.out[c][gz * sxy + (long long)gy * Nx + gx] = v;
+      }
+    }
   }
 }
 
@@ -383,6 +784,8 @@ __global__ void clock_kernel(double* t0, long long* step, double t) {
   *t0 = t;
   *step = 0;
 }
+
+__global__ void clock_advance_kernel(long long* step) { *step += 1; }
 
 // Per-row material (support-weighted mean of per-element data) and the row
 // coefficients a, b, c, d; also the running minimum of eps^ mu^.
@@ -476,6 +879,17 @@ AxisDev<T> axis_dev(const Ctx& c, int d) {
     a.luU[f] = base + L.lu[d][f][2];
   }
   a.N = c.N[d];
+  const Axis1D& h = c.axes[d];
+  const int p = h.p, W = 2 * p + 1;
+  a.inner_lo = 2 * p;
+  a.inner_hi = h.N - 1 - 2 * p;
+  for (int o = 0; o < 4; ++o)
+    for (int q = 0; q < 2 * kMaxP + 1; ++q) a.inner[o][q] = T(0);
+  if (a.inner_lo <= a.inner_hi) {
+    const std::vector<double>* src[4] = {&h.M, &h.S, &h.A, &h.B};
+    for (int o = 0; o < 4; ++o)
+      for (int q = 0; q < W; ++q) a.inner[o][q] = T((*src[o])[(size_t)a.inner_lo * W + q]);
+  }
   return a;
 }
 
@@ -606,9 +1020,47 @@ cudaError_t launch_rhs(Ctx& c, RhsParams<T>& prm, const char* name, double bytes
   return cudaGetLastError();
 }
 
+cudaError_t advance_clock(Ctx& c) {
+  prof_begin(c, "clock", 0.0);
+  clock_advance_kernel<<<1, 1, 0, c.stream>>>(c.d_clock_step);
+  prof_end(c);
+  return cudaGetLastError();
+}
+
 template <typename T, int P>
-cudaError_t launch_line(Ctx& c, const T* src, T* dst, int dir, bool stiff, int dirichlet, const T* cvec,
-                        const char* name) {
+size_t rhs_e_smem() {
+  using S = rhs2::Smem<T, P>;
+  return sizeof(T) * (2 * (size_t)S::TILE + 2 * (size_t)S::ZR + 2 * (size_t)S::YR);
+}
+
+template <typename T>
+Stencils<T> stencils_of(const Axis1D& ax) {
+  Stencils<T> s{};
+  const int p = ax.p, W = 2 * p + 1;
+  s.lo = 2 * p;
+  s.hi = ax.N - 1 - 2 * p;
+  if (s.lo <= s.hi) {
+    const std::vector<double>* src[3] = {&ax.M, &ax.A, &ax.B};
+    for (int o = 0; o < 3; ++o)
+      for (int q = 0; q < W; ++q) s.w[o][q] = T((*src[o])[(size_t)s.lo * W + q]);
+  }
+  return s;
+}
+
+template <typename T, int P>
+cudaError_t launch_rhs_e(Ctx& c, RhsParams<T>& prm, int half, double bytes) {
+  using namespace rhs2;
+  for (int d = 0; d < 3; ++d) prm.st[d] = stencils_of<T>(c.axes[d]);
+  dim3 grid((c.N[0] + TX - 1) / TX, (c.N[1] + TY - 1) / TY, (c.N[2] + TZ - 1) / TZ);
+  prof_begin(c, "rhs_E", bytes);
+  if (half == 1) rhs_e_kernel<T, P, 1><<<grid, NT, rhs_e_smem<T, P>(), c.stream>>>(prm);
+  else rhs_e_kernel<T, P, 2><<<grid, NT, rhs_e_smem<T, P>(), c.stream>>>(prm);
+  prof_end(c);
+  return cudaGetLastError();
+}
+
+template <typename T, int P>
+cudaError_t launch_line(Ctx& c, int dir, int mode, const LineJobs<T>& jobs, int njobs, const char* name) {
   LineParams lp;
   lp.dir = dir;
   lp.N = c.N[dir];
@@ -616,26 +1068,39 @@ cudaError_t launch_line(Ctx& c, const T* src, T* dst, int dir, bool stiff, int d
   lp.Ny = c.N[1];
   lp.Nz = c.N[2];
   lp.nlines = (long long)c.N[0] * c.N[1] * c.N[2] / c.N[dir];
-  lp.dirichlet = dirichlet;
-  lp.lo = dirichlet ? 1 : 0;
-  lp.hi = dirichlet ? lp.N - 2 : lp.N - 1;
-  const int planes = stiff ? 1 + P : 1;
-  int lines = 64;
+  const int planes = mode == LM_STIFF ? 1 + P : 1;
   const size_t limit = (size_t)c.smem_optin;
-  while (lines > 8 && (size_t)planes * lp.N * (lines + 1) * sizeof(T) > limit) lines /= 2;
-  size_t smem = (size_t)planes * lp.N * (lines + 1) * sizeof(T);
-  if (smem > limit) return cudaErrorInvalidValue;
-  auto kern = stiff ? line_kernel<T, P, true> : line_kernel<T, P, false>;
+  auto smem_for = [&](int lines) { return (size_t)planes * lp.N * (lines + 1) * sizeof(T); };
+  // largest tile (<= 64 lines) that leaves room for two CTAs per SM
+  int lines = 64;
+  while (lines > 8 && smem_for(lines) > limit / 2) lines /= 2;
+  if (smem_for(lines) > limit) return cudaErrorInvalidValue;
+  size_t smem = smem_for(lines);
   long long blocks = (lp.nlines + lines - 1) / lines;
-  double bytes = (double)c.Nc * sizeof(T) * (stiff ? 3.0 : 2.0);
-  prof_begin(c, name, bytes);
-  kern<<<(unsigned)blocks, lines, smem, c.stream>>>(src, dst, lp, axis_dev<T>(c, dir), cvec);
+  double per_job = (double)c.Nc * sizeof(T) * (mode == LM_MASS ? 2.0 : 3.0);
+  prof_begin(c, name, per_job * njobs);
+  dim3 grid((unsigned)blocks, njobs);
+  const AxisDev<T> ax = axis_dev<T>(c, dir);
+  if (mode == LM_STIFF) line_kernel<T, P, LM_STIFF><<<grid, lines, smem, c.stream>>>(jobs, lp, ax);
+  else if (mode == LM_DERIV) line_kernel<T, P, LM_DERIV><<<grid, lines, smem, c.stream>>>(jobs, lp, ax);
+  else line_kernel<T, P, LM_MASS><<<grid, lines, smem, c.stream>>>(jobs, lp, ax);
   prof_end(c);
   return cudaGetLastError();
 }
 
-// E half step: RHS, then per component stiffness direction first, then the two
-// mass directions (order of the Appendix, eqs. split1/split2).
+template <typename T>
+LineJob<T> job_of(const T* src, T* dst, const T* aux, double scale, int dirichlet) {
+  LineJob<T> j;
+  j.src = src;
+  j.dst = dst;
+  j.aux = aux;
+  j.scale = T(scale);
+  j.dirichlet = dirichlet;
+  return j;
+}
+
+// E half step: RHS, then per component the stiffness direction first, then the
+// two mass directions (order of the Appendix, eqs. split1/split2).
 template <typename T, int P>
 cudaError_t e_substep(Ctx& c, int half) {
   T** cur = reinterpret_cast<T**>(c.cur);
@@ -676,7 +1141,7 @@ cudaError_t e_substep(Ctx& c, int half) {
   prm.clock_step = c.d_clock_step;
   prm.advance_clock = 0;
   double bytes = (double)c.Nc * sizeof(T) * 12.0;
-  cudaError_t e = launch_rhs<T, P>(c, prm, "rhs_E", bytes);
+  cudaError_t e = launch_rhs_e<T, P>(c, prm, half, bytes);
   if (e != cudaSuccess) return e;
   // stiffness direction of E_i: half 1 (y, z, x), half 2 (z, x, y)
   static const int stiff_dir[2][3] = {{1, 2, 0}, {2, 0, 1}};
@@ -684,23 +1149,28 @@ cudaError_t e_substep(Ctx& c, int half) {
   static const char* mass_name[3] = {"line_x_mass", "line_y_mass", "line_z_mass"};
   for (int i = 0; i < 3; ++i) {
     int sd = stiff_dir[half - 1][i];
-    e = launch_line<T, P>(c, R[i], R[i], sd, true, 1, cf[2], stiff_name[sd]);
+    LineJobs<T> js{};
+    js.job[0] = job_of<T>(R[i], R[i], cf[2], 0.0, 1);
+    e = launch_line<T, P>(c, sd, LM_STIFF, js, 1, stiff_name[sd]);
     if (e != cudaSuccess) return e;
     int md[2], m = 0;
     for (int d = 0; d < 3; ++d)
       if (d != sd) md[m++] = d;
-    e = launch_line<T, P>(c, R[i], R[i], md[0], false, md[0] != i, nullptr, mass_name[md[0]]);
+    js.job[0] = job_of<T>(R[i], R[i], nullptr, 0.0, md[0] != i);
+    e = launch_line<T, P>(c, md[0], LM_MASS, js, 1, mass_name[md[0]]);
     if (e != cudaSuccess) return e;
-    e = launch_line<T, P>(c, R[i], Eout[i], md[1], false, md[1] != i, nullptr, mass_name[md[1]]);
+    js.job[0] = job_of<T>(R[i], Eout[i], nullptr, 0.0, md[1] != i);
+    e = launch_line<T, P>(c, md[1], LM_MASS, js, 1, mass_name[md[1]]);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
-// H half step: M H_new = M H_old - d C1 E_alpha + d C2 E_beta, then three
-// mass solves per component (H_i constrained in direction i).
+// H half step, general material: M H_new = M H_old - d C1 E_alpha + d C2 E_beta
+// (eqs. discrete2 / discrete4), then three mass solves per component (H_i
+// constrained in direction i).
 template <typename T, int P>
-cudaError_t h_substep(Ctx& c, int half) {
+cudaError_t h_substep_general(Ctx& c, int half) {
   T** cur = reinterpret_cast<T**>(c.cur);
   T** hlf = reinterpret_cast<T**>(c.half);
   T** R = reinterpret_cast<T**>(c.rhs);
@@ -731,14 +1201,53 @@ cudaError_t h_substep(Ctx& c, int half) {
   cudaError_t e = launch_rhs<T, P>(c, prm, "rhs_H", bytes);
   if (e != cudaSuccess) return e;
   static const char* mass_name[3] = {"line_x_mass", "line_y_mass", "line_z_mass"};
-  for (int i = 0; i < 3; ++i) {
-    for (int d = 0; d < 3; ++d) {
-      T* dst = d == 2 ? Hout[3 + i] : R[i];
-      e = launch_line<T, P>(c, R[i], dst, d, false, d == i, nullptr, mass_name[d]);
-      if (e != cudaSuccess) return e;
-    }
+  for (int d = 0; d < 3; ++d) {
+    LineJobs<T> js{};
+    for (int i = 0; i < 3; ++i) js.job[i] = job_of<T>(R[i], d == 2 ? Hout[3 + i] : R[i], nullptr, 0.0, d == i);
+    e = launch_line<T, P>(c, d, LM_MASS, js, 3, mass_name[d]);
+    if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+// H half step when mu is uniform (d constant): since the H system matrix is the
+// 3D mass matrix, H_new = H_old + d M^-1 (-C1 E_alpha + C2 E_beta) exactly, and
+// M^-1 (M (x) A (x) M) reduces to the 1D derivative D = M^-1 A along one axis
+// (the other two factors cancel; the boundary constraints of E and H make the
+// cancelled factors identical).  Componentwise:
+//   H1 += d (-D_y E3_alpha + D_z E2_beta)
+//   H2 += d (-D_z E1_alpha + D_x E3_beta)
+//   H3 += d (-D_x E2_alpha + D_y E1_beta)
+// done as three axis passes (z, x, y), two components each.
+template <typename T, int P>
+cudaError_t h_substep_uniform(Ctx& c, int half) {
+  T** cur = reinterpret_cast<T**>(c.cur);
+  T** hlf = reinterpret_cast<T**>(c.half);
+  T* const* Hold = half == 1 ? cur : hlf;
+  T* const* Hout = half == 1 ? hlf : cur;
+  T* const* Ea = cur;  // alpha: E^n (half 1) or E^{n+1} (half 2)
+  T* const* Eb = hlf;  // beta:  E^{n+1/2}
+  const double d = c.d_uniform;
+  LineJobs<T> js{};
+  js.job[0] = job_of<T>(Eb[1], Hout[3], Hold[3], d, 0);
+  js.job[1] = job_of<T>(Ea[0], Hout[4], Hold[4], -d, 0);
+  cudaError_t e = launch_line<T, P>(c, 2, LM_DERIV, js, 2, "line_z_deriv");
+  if (e != cudaSuccess) return e;
+  js.job[0] = job_of<T>(Eb[2], Hout[4], Hout[4], d, 0);
+  js.job[1] = job_of<T>(Ea[1], Hout[5], Hold[5], -d, 0);
+  e = launch_line<T, P>(c, 0, LM_DERIV, js, 2, "line_x_deriv");
+  if (e != cudaSuccess) return e;
+  js.job[0] = job_of<T>(Ea[2], Hout[3], Hout[3], -d, 0);
+  js.job[1] = job_of<T>(Eb[0], Hout[5], Hout[5], d, 0);
+  e = launch_line<T, P>(c, 1, LM_DERIV, js, 2, "line_y_deriv");
+  if (e != cudaSuccess) return e;
+  if (half == 2) e = advance_clock(c);
+  return e;
+}
+
+template <typename T, int P>
+cudaError_t h_substep(Ctx& c, int half) {
+  return c.mu_uniform ? h_substep_uniform<T, P>(c, half) : h_substep_general<T, P>(c, half);
 }
 
 template <typename T, int P>
@@ -773,8 +1282,11 @@ cudaError_t opt_in(K kern, int optin) {
 template <typename T, int P>
 cudaError_t prepare_tp(int optin) {
   cudaError_t e = opt_in(rhs_kernel<T, P, 32, 8, 8>, optin);
-  if (e == cudaSuccess) e = opt_in(line_kernel<T, P, true>, optin);
-  if (e == cudaSuccess) e = opt_in(line_kernel<T, P, false>, optin);
+  if (e == cudaSuccess) e = opt_in(rhs_e_kernel<T, P, 1>, optin);
+  if (e == cudaSuccess) e = opt_in(rhs_e_kernel<T, P, 2>, optin);
+  if (e == cudaSuccess) e = opt_in(line_kernel<T, P, LM_MASS>, optin);
+  if (e == cudaSuccess) e = opt_in(line_kernel<T, P, LM_STIFF>, optin);
+  if (e == cudaSuccess) e = opt_in(line_kernel<T, P, LM_DERIV>, optin);
   return e;
 }
 
