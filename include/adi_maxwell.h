@@ -132,6 +132,33 @@ adi_status adi_fields_device(adi_handle h, void* dev_ptr, void* cuda_stream);
  * 1/sqrt(min_rows eps^ mu^).  Returns a negative value on error. */
 double adi_cfl_dt(adi_handle h);
 
+/* Allocation-free variant of adi_cfl_dt for callers that cannot allocate
+ * device memory (the paper has no counterpart; this is a library service).
+ * Who needs it: code that is recording a CUDA graph (cudaMalloc is not allowed
+ * while a stream is being captured), services that give all device memory to
+ * their own pool at start-up and forbid later cudaMalloc/cudaFree, and
+ * real-time loops that must not block in the allocator.  adi_create allocates
+ * the whole state, so such callers cannot get the explicit time-step limit
+ * from a handle at that point; this call computes the same value as
+ * adi_cfl_dt of a handle created from the same nx, ny, nz, p, eps and mu.
+ *  d_eps, d_mu: per-element eps and mu in DEVICE memory ([z][y][x], doubles,
+ *  owned by the caller, read only).  *dt_out (host) receives the limit.
+ *  cuda_stream: the stream to run on (NULL = legacy default stream); the call
+ *  synchronises it before returning.
+ * No device memory is allocated or freed: the scratch (the 1D element-integral
+ * tables and a running minimum) is one file-scope device array of 8192
+ * doubles (64 KiB) that every GPU which loads the library keeps until the
+ * process exits.  Sizes with (nx + ny + nz + 3p) * (p + 1) > 8184 are rejected
+ * with ADI_EINVAL before any GPU work.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  All calls share the one
+ * array and each call re-initialises what it reads, so calls that overlap on
+ * the GPU (different streams, or host threads on the same device) race and
+ * must be serialised by the caller.  Errors: ADI_EINVAL (NULL pointer, sizes),
+ * ADI_ECUDA, ADI_ENUMERIC (eps or mu <= 0); message via adi_last_error(NULL). */
+adi_status adi_cfl_dt_noalloc(int nx, int ny, int nz, int p, const double* d_eps, const double* d_mu,
+                              void* cuda_stream, double* dt_out);
+
 /* Block until all work on the handle's stream is done. */
 adi_status adi_sync(adi_handle h);
 

@@ -18,7 +18,7 @@ PREC_FP64, PREC_FP32 = 0, 1
 # every symbol declared in include/adi_maxwell.h
 EXPORTS = ("adi_create", "adi_factor", "adi_set_dt", "adi_set_stream", "adi_set_fields",
            "adi_set_source", "adi_step", "adi_substep", "adi_fields", "adi_fields_device",
-           "adi_cfl_dt", "adi_sync", "adi_set_profiling", "adi_kernel_stats", "adi_dims",
+           "adi_cfl_dt", "adi_cfl_dt_noalloc", "adi_sync", "adi_set_profiling", "adi_kernel_stats", "adi_dims",
            "adi_destroy", "adi_last_error", "adi_status_string")
 
 
@@ -58,6 +58,7 @@ def load_library(path=LIB_PATH):
         "adi_fields": (I, [H, P(D), P(D)]),
         "adi_fields_device": (I, [H, ctypes.c_void_p, ctypes.c_void_p]),
         "adi_cfl_dt": (D, [H]),
+        "adi_cfl_dt_noalloc": (I, [I, I, I, I, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, P(D)]),
         "adi_sync": (I, [H]),
         "adi_set_profiling": (I, [H, I]),
         "adi_kernel_stats": (I, [H, P(AdiKernelStat), I, P(I)]),

@@ -68,6 +68,8 @@ void drop_graph(Ctx* c) {
 // ------------------------------------------------------------- profiling
 namespace adi {
 
+adi_status fail_global(adi_status s, const std::string& msg) { return fail(nullptr, s, msg); }
+
 void prof_begin(Ctx& c, const char* name, double bytes) {
   if (!c.profiling) return;
   Launch* l = new (std::nothrow) Launch{name, bytes, nullptr, nullptr};

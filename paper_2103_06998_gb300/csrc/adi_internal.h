@@ -181,6 +181,9 @@ cudaError_t set_fields_dev(Ctx& c, const double* d_src);
 cudaError_t get_fields_dev(Ctx& c, double* d_dst, int* d_bad);
 cudaError_t set_clock(Ctx& c, double t0);
 
+// record a failure that has no handle (readable through adi_last_error(NULL))
+adi_status fail_global(adi_status s, const std::string& msg);
+
 // profiling hooks used by the launchers
 void prof_begin(Ctx& c, const char* name, double bytes);
 void prof_end(Ctx& c);
