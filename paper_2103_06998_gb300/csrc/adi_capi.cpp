@@ -186,10 +186,8 @@ adi_status adi_create(int nx, int ny, int nz, int p, double dt, const double* ep
     if (!ok) return;
     if (cudaMalloc(p, bytes) != cudaSuccess) ok = false;
   };
-  for (int i = 0; i < 6; ++i) {
-    alloc(&c->cur[i], fb);
-    alloc(&c->half[i], fb);
-  }
+  for (int i = 0; i < 6; ++i) alloc(&c->cur[i], fb);
+  for (int i = 0; i < 3; ++i) alloc(&c->half[i], fb);  // E^{n+1/2}; H is updated in place
   for (int i = 0; i < 3; ++i) alloc(&c->rhs[i], fb);
   for (int i = 0; i < 4; ++i) alloc(&c->coef[i], fb);
   alloc(&c->stage, c->Nc * 6 * sizeof(double));
@@ -234,7 +232,7 @@ adi_status adi_create(int nx, int ny, int nz, int p, double dt, const double* ep
   if (e == cudaSuccess) {
     for (int i = 0; i < 6 && e == cudaSuccess; ++i) {
       e = cudaMemsetAsync(c->cur[i], 0, fb, c->stream);
-      if (e == cudaSuccess) e = cudaMemsetAsync(c->half[i], 0, fb, c->stream);
+      if (e == cudaSuccess && i < 3) e = cudaMemsetAsync(c->half[i], 0, fb, c->stream);
     }
   }
   if (e == cudaSuccess) e = adi::set_clock(*c, 0.0);

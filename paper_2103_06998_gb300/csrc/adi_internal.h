@@ -144,7 +144,7 @@ struct Ctx {
 
   // state and work (element type T = float or double), each Nc elements
   void* cur[6] = {};
-  void* half[6] = {};
+  void* half[6] = {};  // [0..2]: E^{n+1/2}; [3..5] unused (H is updated in place)
   void* rhs[3] = {};
   void* coef[4] = {};   // a, b, c, d
   void* stage = nullptr;  // Nc doubles for host transfers (FP32 mode)

@@ -173,19 +173,6 @@ __global__ void __launch_bounds__(TX* TY) rhs_kernel(const RhsParams<T> prm) {
 }
 
 // ----------------------------------------------------------- line solves
-__device__ __forceinline__ long long line_offset(const LineParams& lp, long long L) {
-  // first element of line L; lines along y are indexed z*Nx + x, along z y*Nx + x
-  if (lp.dir == 0) return L * lp.N;
-  if (lp.dir == 1) return (L / lp.Nx) * (long long)lp.Nx * lp.Ny + (L % lp.Nx);
-  return L;
-}
-
-__device__ __forceinline__ long long line_stride(const LineParams& lp) {
-  if (lp.dir == 0) return 1;
-  if (lp.dir == 1) return lp.Nx;
-  return (long long)lp.Nx * lp.Ny;
-}
-
 // Asynchronous global -> shared copy of one element (cp.async, no register
 // round trip); all copies of a tile are in flight together.
 template <typename T>
@@ -203,53 +190,118 @@ __device__ __forceinline__ void cp_async_wait_all() {
 __device__ __forceinline__ float fast_rcp(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
 
-// Stage one tile of lines (transposed to [k][line], pitch LP) with cp.async.
-template <typename T>
-__device__ __forceinline__ void stage_tile(T* s, const T* g, const LineParams& lp, long long L0, int cnt,
-                                           int LP) {
-  const int t = threadIdx.x, LINES = blockDim.x, N = lp.N;
-  if (lp.dir == 0) {
-    const T* base = g + L0 * N;
-    for (int line = 0; line < cnt; ++line)
-      for (int k = t; k < N; k += LINES) cp_async_elem(&s[k * LP + line], &base[(long long)line * N + k]);
-  } else if (t < cnt) {
-    const long long off = line_offset(lp, L0 + t), stride = line_stride(lp);
-    for (int k = 0; k < N; ++k) cp_async_elem(&s[k * LP + t], &g[off + k * stride]);
-  }
+// Fire-and-forget global add (red.global.add): the L2 performs the update.
+__device__ __forceinline__ void red_add(float* p, float v) {
+  asm volatile("red.global.add.f32 [%0], %1;\n" ::"l"(p), "f"(v) : "memory");
+}
+__device__ __forceinline__ void red_add(double* p, double v) {
+  asm volatile("red.global.add.f64 [%0], %1;\n" ::"l"(p), "d"(v) : "memory");
 }
 
 // Banded solves along one axis, one thread per line (Gaussian elimination
 // without pivoting restricted to the band; Appendix, eqs. split1/split2).
-//   LM_MASS : x = M^-1 r with the precomputed (full or Dirichlet) mass LU.
-//   LM_STIFF: x = (M + diag(c) S)^-1 r; the LU of each line is formed row by
-//             row from c (per-test-function material) and its normalised upper
+//   LM_MASS : dst = M^-1 src with the precomputed (full or Dirichlet) mass LU.
+//   LM_STIFF: dst = (M + diag(c) S)^-1 src; the LU of each line is formed row by
+//             row from c (per-test-function material), and its normalised upper
 //             factors are kept in shared memory for the back substitution.
-//   LM_DERIV: out = base + scale * M^-1 (A u): the 1D derivative in the L2
-//             sense, used by the H half steps when mu is uniform.
-// blockIdx.y selects one of up to three independent jobs of the same axis.
-template <typename T, int P, int MODE>
+//   LM_DERIV: dst += scale * M^-1 (A src): the 1D derivative in the L2 sense,
+//             added in place with red.global.add (H half steps, uniform mu).
+// A tile of LINES lines is staged with cp.async into shared memory as
+// [row][line] (x lines transposed; pitch LINES+1 for x so both the staging and
+// the per-thread recurrence are bank-conflict free), solved in place, written
+// back.  The 1D tables of the axis are staged into shared memory as well.
+// blockIdx.y selects one of up to three independent jobs on the same axis.
+template <typename T, int P, int MODE, bool XDIR>
 __global__ void __launch_bounds__(64) line_kernel(const LineJobs<T> jobs, const LineParams lp, const AxisDev<T> ax) {
   constexpr int W = 2 * P + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const LineJob<T> job = jobs.job[blockIdx.y];
-  const int LINES = blockDim.x, LP = LINES + 1, N = lp.N;
-  T* sr = reinterpret_cast<T*>(smem_raw);  // [k][line]
-  T* su = sr + (size_t)N * LP;             // LM_STIFF: c, then P planes of upper factors
+  // static parameter offsets (a dynamic index would copy the struct to the stack)
+  const LineJob<T> job = blockIdx.y == 0 ? jobs.job[0] : (blockIdx.y == 1 ? jobs.job[1] : jobs.job[2]);
+  const T* __restrict__ src = job.src;
+  T* dst = job.dst;
+  const T* __restrict__ cvec = job.aux;
+  const int dch = job.dirichlet;
+  const T scale = job.scale;
+  const int LINES = blockDim.x, LP = XDIR ? LINES + 1 : LINES, N = lp.N;
+  // shared memory: tables | data [N][LP] | STIFF: c then P factor planes
+  constexpr int TABW = MODE == LM_STIFF ? 2 * W : (MODE == LM_DERIV ? 3 * P + 1 + W : 3 * P + 1);
+  T* tab = reinterpret_cast<T*>(smem_raw);
+  T* sr = tab + ((N * TABW + 3) & ~3);
+  T* su = sr + N * LP;
   const int t = threadIdx.x;
-  const long long L0 = (long long)blockIdx.x * LINES;
-  const int cnt = (int)min((long long)LINES, lp.nlines - L0);
+  const int L0 = blockIdx.x * LINES;
+  const int cnt = min(LINES, (int)(lp.nlines - L0));
 
-  stage_tile(sr, job.src, lp, L0, cnt, LP);
-  if (MODE == LM_STIFF) stage_tile(su, job.aux, lp, L0, cnt, LP);
+  // ---- 1D tables: MASS/DERIV [L(P) inv U(P) (A(W))], STIFF [M(W) S(W)], row-major per row
+  for (int i = t; i < N; i += LINES) {
+    T* row = tab + i * TABW;
+    if (MODE == LM_STIFF) {
+#pragma unroll
+      for (int d = 0; d < W; ++d) {
+        row[d] = ax.band[OP_M][i * W + d];
+        row[W + d] = ax.band[OP_S][i * W + d];
+      }
+    } else {
+      const T* Lt = dch ? ax.luL[1] : ax.luL[0];
+      const T* It = dch ? ax.luInv[1] : ax.luInv[0];
+      const T* Ut = dch ? ax.luU[1] : ax.luU[0];
+#pragma unroll
+      for (int q = 0; q < P; ++q) {
+        row[q] = Lt[i * P + q];
+        row[P + 1 + q] = Ut[i * P + q];
+      }
+      row[P] = It[i];
+      if (MODE == LM_DERIV) {
+#pragma unroll
+        for (int d = 0; d < W; ++d) row[3 * P + 1 + d] = ax.band[OP_A][i * W + d];
+      }
+    }
+  }
+
+  // ---- stage the tile (and c for STIFF)
+  long long off = 0, stride = 1;  // first element and stride of this thread's line (columns)
+  if (XDIR) {
+    const T* base = src + (long long)L0 * N;
+    const T* cb = MODE == LM_STIFF ? cvec + (long long)L0 * N : nullptr;
+    for (int line = 0; line < cnt; ++line) {
+      const T* g = base + (long long)line * N;
+      const T* gc = MODE == LM_STIFF ? cb + (long long)line * N : nullptr;
+      for (int k = t; k < N; k += LINES) {
+        cp_async_elem(&sr[k * LP + line], g + k);
+        if (MODE == LM_STIFF) cp_async_elem(&su[k * LP + line], gc + k);
+      }
+    }
+  } else if (t < cnt) {
+    const int L = L0 + t;
+    if (lp.dir == 1) {
+      off = (long long)(L / lp.Nx) * lp.Nx * lp.Ny + (L % lp.Nx);
+      stride = lp.Nx;
+    } else {
+      off = L;
+      stride = (long long)lp.Nx * lp.Ny;
+    }
+    const T* g = src + off;
+    const T* gc = MODE == LM_STIFF ? cvec + off : nullptr;
+    T* s = sr + t;
+    T* sc = su + t;
+#pragma unroll 8
+    for (int k = 0; k < N; ++k) {
+      cp_async_elem(s, g);
+      if (MODE == LM_STIFF) cp_async_elem(sc, gc);
+      s += LP;
+      sc += LP;
+      g += stride;
+      if (MODE == LM_STIFF) gc += stride;
+    }
+  }
   cp_async_wait_all();
   __syncthreads();
 
   if (t < cnt) {
-    const int lo = job.dirichlet ? 1 : 0, hi = job.dirichlet ? N - 2 : N - 1;
-    const int ilo = ax.inner_lo, ihi = ax.inner_hi;
+    const int lo = dch ? 1 : 0, hi = dch ? N - 2 : N - 1;
+    T* col = sr + t;
     if (MODE == LM_STIFF) {
-      const T* __restrict__ Mb = ax.band[OP_M];
-      const T* __restrict__ Sb = ax.band[OP_S];
+      const int plane = N * LP;
       T Uq[P][P + 1], invq[P], yq[P];
 #pragma unroll
       for (int m = 0; m < P; ++m) {
@@ -259,14 +311,19 @@ __global__ void __launch_bounds__(64) line_kernel(const LineJobs<T> jobs, const 
         for (int e = 0; e <= P; ++e) Uq[m][e] = T(0);
       }
       // one row of the on-the-fly Doolittle LU of M + c S and the forward step
-      auto row = [&](int k, T ck, T rk, bool inner) {
+      auto row = [&](int k, bool inner) {
+        const T ck = su[k * LP + t];
+        const T* tb = tab + k * TABW;
         T a[W];
 #pragma unroll
         for (int d = 0; d < W; ++d) {
-          const int j = k + d - P;
-          const T mv = inner ? ax.inner[OP_M][d] : Mb[k * W + d];
-          const T sv = inner ? ax.inner[OP_S][d] : Sb[k * W + d];
-          a[d] = (j >= lo && j <= hi) ? mv + ck * sv : T(0);
+          const T mv = inner ? ax.inner[OP_M][d] : tb[d];
+          const T sv = inner ? ax.inner[OP_S][d] : tb[W + d];
+          a[d] = mv + ck * sv;
+          if (!inner) {
+            const int j = k + d - P;
+            if (j < lo || j > hi) a[d] = T(0);
+          }
         }
         T l[P + 1];
         l[0] = T(0);
@@ -287,12 +344,12 @@ __global__ void __launch_bounds__(64) line_kernel(const LineJobs<T> jobs, const 
           Un[e] = s;
         }
         const T inv = fast_rcp(Un[0]);
-        T y = rk;
+        T y = col[k * LP];
 #pragma unroll
         for (int m = 1; m <= P; ++m) y -= l[m] * yq[m - 1];
-        sr[k * LP + t] = y * inv;
+        col[k * LP] = y * inv;
 #pragma unroll
-        for (int e = 1; e <= P; ++e) su[((size_t)(e - 1) * N + k) * LP + t] = Un[e] * inv;
+        for (int e = 1; e <= P; ++e) su[(e - 1) * plane + k * LP + t] = Un[e] * inv;
 #pragma unroll
         for (int m = P - 1; m >= 1; --m) {
           invq[m] = invq[m - 1];
@@ -305,172 +362,104 @@ __global__ void __launch_bounds__(64) line_kernel(const LineJobs<T> jobs, const 
 #pragma unroll
         for (int e = 0; e <= P; ++e) Uq[0][e] = Un[e];
       };
+      // rows whose band lies inside the solved range and in the interior stencil
+      const int kin0 = max(lo + P, ax.inner_lo), kin1 = min(hi - P, ax.inner_hi);
       int k = lo;
-      for (; k + 3 <= hi; k += 4) {
-        T cc[4], rr[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          cc[u] = su[(k + u) * LP + t];
-          rr[u] = sr[(k + u) * LP + t];
-        }
-        const bool inner = k - P >= ilo && k + 3 + P <= ihi;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) row(k + u, cc[u], rr[u], inner);
-      }
-      for (; k <= hi; ++k) row(k, su[k * LP + t], sr[k * LP + t], false);
+      for (; k < kin0 && k <= hi; ++k) row(k, false);
+#pragma unroll 4
+      for (; k <= kin1; ++k) row(k, true);
+      for (; k <= hi; ++k) row(k, false);
       T xq[P];
 #pragma unroll
       for (int m = 0; m < P; ++m) xq[m] = T(0);
-      k = hi;
-      for (; k - 3 >= lo; k -= 4) {
-        T yy[4], uu[4][P];
+#pragma unroll 4
+      for (k = hi; k >= lo; --k) {
+        T x = col[k * LP];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          yy[u] = sr[(k - u) * LP + t];
-#pragma unroll
-          for (int e = 1; e <= P; ++e) uu[u][e - 1] = su[((size_t)(e - 1) * N + k - u) * LP + t];
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          T x = yy[u];
-#pragma unroll
-          for (int e = 1; e <= P; ++e) x -= uu[u][e - 1] * xq[e - 1];
-          sr[(k - u) * LP + t] = x;
-#pragma unroll
-          for (int m = P - 1; m >= 1; --m) xq[m] = xq[m - 1];
-          xq[0] = x;
-        }
-      }
-      for (; k >= lo; --k) {
-        T x = sr[k * LP + t];
-#pragma unroll
-        for (int e = 1; e <= P; ++e) x -= su[((size_t)(e - 1) * N + k) * LP + t] * xq[e - 1];
-        sr[k * LP + t] = x;
+        for (int e = 1; e <= P; ++e) x -= su[(e - 1) * plane + k * LP + t] * xq[e - 1];
+        col[k * LP] = x;
 #pragma unroll
         for (int m = P - 1; m >= 1; --m) xq[m] = xq[m - 1];
         xq[0] = x;
       }
     } else {
-      const int dch = job.dirichlet;
-      const T* __restrict__ Lt = dch ? ax.luL[1] : ax.luL[0];
-      const T* __restrict__ It = dch ? ax.luInv[1] : ax.luInv[0];
-      const T* __restrict__ Ut = dch ? ax.luU[1] : ax.luU[0];
-      const T* __restrict__ Ab = ax.band[OP_A];
       // LM_DERIV: the right-hand side of row k is (A u)_k; a register window
-      // keeps u[k-P .. k+P] because sr[k] is overwritten by the elimination.
+      // keeps u[k-P .. k+P] because col[k] is overwritten by the elimination.
       T win[W];
       if (MODE == LM_DERIV) {
 #pragma unroll
         for (int d = 0; d < W; ++d) {
-          int j = lo + d - P;
-          win[d] = (j >= 0 && j < N) ? sr[j * LP + t] : T(0);
+          const int j = lo + d - P;
+          win[d] = (j >= 0 && j < N) ? col[j * LP] : T(0);
         }
       }
       T yq[P];
 #pragma unroll
       for (int m = 0; m < P; ++m) yq[m] = T(0);
-      auto fwd = [&](int k, T rk, const T* lk, bool inner) {
-        T y = rk;
+      int k;
+#pragma unroll 4
+      for (k = lo; k <= hi; ++k) {
+        const T* tb = tab + k * TABW;
+        T y;
         if (MODE == LM_DERIV) {
+          const int j = k + P + 1;
+          const T nxt = j < N ? col[j * LP] : T(0);
           y = T(0);
 #pragma unroll
-          for (int d = 0; d < W; ++d) y += (inner ? ax.inner[OP_A][d] : Ab[k * W + d]) * win[d];
+          for (int d = 0; d < W; ++d) y += tb[3 * P + 1 + d] * win[d];
 #pragma unroll
           for (int d = 0; d < W - 1; ++d) win[d] = win[d + 1];
-          win[W - 1] = rk;  // u[k + P + 1], loaded by the caller
+          win[W - 1] = nxt;
+        } else {
+          y = col[k * LP];
         }
 #pragma unroll
-        for (int m = 1; m <= P; ++m) y -= lk[m - 1] * yq[m - 1];
-        sr[k * LP + t] = y;
+        for (int m = 1; m <= P; ++m) y -= tb[m - 1] * yq[m - 1];
+        col[k * LP] = y;
 #pragma unroll
         for (int m = P - 1; m >= 1; --m) yq[m] = yq[m - 1];
         yq[0] = y;
-      };
-      // MASS: rk = r[k]; DERIV: rk = u[k + P + 1] (the next window entry)
-      auto load_rk = [&](int k) -> T {
-        if (MODE == LM_DERIV) {
-          const int j = k + P + 1;
-          return j < N ? sr[j * LP + t] : T(0);
-        }
-        return sr[k * LP + t];
-      };
-      int k = lo;
-      for (; k + 3 <= hi; k += 4) {
-        T rr[4], ll[4][P];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          rr[u] = load_rk(k + u);
-#pragma unroll
-          for (int m = 0; m < P; ++m) ll[u][m] = Lt[(k + u) * P + m];
-        }
-        const bool inner = k - P >= ilo && k + 3 + P <= ihi;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) fwd(k + u, rr[u], ll[u], inner);
-      }
-      for (; k <= hi; ++k) {
-        T lk[P];
-#pragma unroll
-        for (int m = 0; m < P; ++m) lk[m] = Lt[k * P + m];
-        fwd(k, load_rk(k), lk, false);
       }
       T xq[P];
 #pragma unroll
       for (int m = 0; m < P; ++m) xq[m] = T(0);
-      k = hi;
-      for (; k - 3 >= lo; k -= 4) {
-        T yy[4], iv[4], uu[4][P];
+#pragma unroll 4
+      for (k = hi; k >= lo; --k) {
+        const T* tb = tab + k * TABW;
+        T x = tb[P] * col[k * LP];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          yy[u] = sr[(k - u) * LP + t];
-          iv[u] = It[k - u];
-#pragma unroll
-          for (int e = 0; e < P; ++e) uu[u][e] = Ut[(k - u) * P + e];
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          T x = iv[u] * yy[u];
-#pragma unroll
-          for (int e = 1; e <= P; ++e) x -= uu[u][e - 1] * xq[e - 1];
-          sr[(k - u) * LP + t] = x;
-#pragma unroll
-          for (int m = P - 1; m >= 1; --m) xq[m] = xq[m - 1];
-          xq[0] = x;
-        }
-      }
-      for (; k >= lo; --k) {
-        T x = It[k] * sr[k * LP + t];
-#pragma unroll
-        for (int e = 1; e <= P; ++e) x -= Ut[k * P + e - 1] * xq[e - 1];
-        sr[k * LP + t] = x;
+        for (int e = 1; e <= P; ++e) x -= tb[P + e] * xq[e - 1];
+        col[k * LP] = x;
 #pragma unroll
         for (int m = P - 1; m >= 1; --m) xq[m] = xq[m - 1];
         xq[0] = x;
       }
     }
-    for (int k = 0; k < lo; ++k) sr[k * LP + t] = T(0);
-    for (int k = hi + 1; k < N; ++k) sr[k * LP + t] = T(0);
+    for (int k = 0; k < lo; ++k) col[k * LP] = T(0);
+    for (int k = hi + 1; k < N; ++k) col[k * LP] = T(0);
   }
   __syncthreads();
 
-  // ---- write back (LM_DERIV: out = base + scale * x)
-  const T scale = job.scale;
-  if (lp.dir == 0) {
-    T* base = job.dst + L0 * N;
-    const T* b0 = MODE == LM_DERIV ? job.aux + L0 * N : nullptr;
-    for (int line = 0; line < cnt; ++line)
+  // ---- write back (LM_DERIV: dst += scale * x, done by the L2)
+  if (XDIR) {
+    T* base = dst + (long long)L0 * N;
+    for (int line = 0; line < cnt; ++line) {
+      T* g = base + (long long)line * N;
       for (int k = t; k < N; k += LINES) {
-        long long g = (long long)line * N + k;
-        T v = sr[k * LP + line];
-        if (MODE == LM_DERIV) v = b0[g] + scale * v;
-        base[g] = v;
+        const T v = sr[k * LP + line];
+        if (MODE == LM_DERIV) red_add(g + k, scale * v);
+        else g[k] = v;
       }
+    }
   } else if (t < cnt) {
-    const long long off = line_offset(lp, L0 + t), stride = line_stride(lp);
-#pragma unroll 4
+    T* g = dst + off;
+    const T* s = sr + t;
+#pragma unroll 8
     for (int k = 0; k < N; ++k) {
-      T v = sr[k * LP + t];
-      if (MODE == LM_DERIV) v = job.aux[off + k * stride] + scale * v;
-      job.dst[off + k * stride] = v;
+      if (MODE == LM_DERIV) red_add(g, scale * *s);
+      else *g = *s;
+      g += stride;
+      s += LP;
     }
   }
 }
@@ -1068,9 +1057,14 @@ cudaError_t launch_line(Ctx& c, int dir, int mode, const LineJobs<T>& jobs, int 
   lp.Ny = c.N[1];
   lp.Nz = c.N[2];
   lp.nlines = (long long)c.N[0] * c.N[1] * c.N[2] / c.N[dir];
+  const int W = 2 * P + 1;
+  const int tabw = mode == LM_STIFF ? 2 * W : (mode == LM_DERIV ? 3 * P + 1 + W : 3 * P + 1);
   const int planes = mode == LM_STIFF ? 1 + P : 1;
   const size_t limit = (size_t)c.smem_optin;
-  auto smem_for = [&](int lines) { return (size_t)planes * lp.N * (lines + 1) * sizeof(T); };
+  auto smem_for = [&](int lines) {
+    const int lp_ = dir == 0 ? lines + 1 : lines;
+    return sizeof(T) * ((((size_t)lp.N * tabw + 3) & ~(size_t)3) + (size_t)planes * lp.N * lp_);
+  };
   // largest tile (<= 64 lines) that leaves room for two CTAs per SM
   int lines = 64;
   while (lines > 8 && smem_for(lines) > limit / 2) lines /= 2;
@@ -1081,9 +1075,17 @@ cudaError_t launch_line(Ctx& c, int dir, int mode, const LineJobs<T>& jobs, int 
   prof_begin(c, name, per_job * njobs);
   dim3 grid((unsigned)blocks, njobs);
   const AxisDev<T> ax = axis_dev<T>(c, dir);
-  if (mode == LM_STIFF) line_kernel<T, P, LM_STIFF><<<grid, lines, smem, c.stream>>>(jobs, lp, ax);
-  else if (mode == LM_DERIV) line_kernel<T, P, LM_DERIV><<<grid, lines, smem, c.stream>>>(jobs, lp, ax);
-  else line_kernel<T, P, LM_MASS><<<grid, lines, smem, c.stream>>>(jobs, lp, ax);
+  const bool x = dir == 0;
+  if (mode == LM_STIFF) {
+    if (x) line_kernel<T, P, LM_STIFF, true><<<grid, lines, smem, c.stream>>>(jobs, lp, ax);
+    else line_kernel<T, P, LM_STIFF, false><<<grid, lines, smem, c.stream>>>(jobs, lp, ax);
+  } else if (mode == LM_DERIV) {
+    if (x) line_kernel<T, P, LM_DERIV, true><<<grid, lines, smem, c.stream>>>(jobs, lp, ax);
+    else line_kernel<T, P, LM_DERIV, false><<<grid, lines, smem, c.stream>>>(jobs, lp, ax);
+  } else {
+    if (x) line_kernel<T, P, LM_MASS, true><<<grid, lines, smem, c.stream>>>(jobs, lp, ax);
+    else line_kernel<T, P, LM_MASS, false><<<grid, lines, smem, c.stream>>>(jobs, lp, ax);
+  }
   prof_end(c);
   return cudaGetLastError();
 }
@@ -1108,7 +1110,7 @@ cudaError_t e_substep(Ctx& c, int half) {
   T** R = reinterpret_cast<T**>(c.rhs);
   T** cf = reinterpret_cast<T**>(c.coef);
   T* const* Ein = half == 1 ? cur : hlf;
-  T* const* Hin = half == 1 ? cur : hlf;
+  T* const* Hin = cur;  // H^n (half 1) or H^{n+1/2} (half 2), updated in place
   T* const* Eout = half == 1 ? hlf : cur;
   RhsParams<T> prm{};
   for (int i = 0; i < 3; ++i) {
@@ -1176,10 +1178,10 @@ cudaError_t h_substep_general(Ctx& c, int half) {
   T** R = reinterpret_cast<T**>(c.rhs);
   T** cf = reinterpret_cast<T**>(c.coef);
   RhsParams<T> prm{};
-  // half 1: H_old = H^n (cur), alpha = E^n (cur), beta = E^{n+1/2} (half), out -> half
-  // half 2: H_old = H^{n+1/2} (half), alpha = E^{n+1} (cur), beta = E^{n+1/2} (half), out -> cur
-  T* const* Hold = half == 1 ? cur : hlf;
-  T* const* Hout = half == 1 ? hlf : cur;
+  // H lives in one buffer (cur) and is replaced by the new level:
+  // alpha = E^n (half 1) or E^{n+1} (half 2) in cur, beta = E^{n+1/2} in half
+  T* const* Hold = cur;
+  T* const* Hout = cur;
   for (int i = 0; i < 3; ++i) {
     prm.fields[i] = Hold[3 + i];
     prm.fields[3 + i] = cur[i];
@@ -1223,22 +1225,21 @@ template <typename T, int P>
 cudaError_t h_substep_uniform(Ctx& c, int half) {
   T** cur = reinterpret_cast<T**>(c.cur);
   T** hlf = reinterpret_cast<T**>(c.half);
-  T* const* Hold = half == 1 ? cur : hlf;
-  T* const* Hout = half == 1 ? hlf : cur;
-  T* const* Ea = cur;  // alpha: E^n (half 1) or E^{n+1} (half 2)
-  T* const* Eb = hlf;  // beta:  E^{n+1/2}
+  T* const* H = cur + 3;  // H is updated in place (H^n is dead once H^{n+1/2} exists)
+  T* const* Ea = cur;     // alpha: E^n (half 1) or E^{n+1} (half 2)
+  T* const* Eb = hlf;     // beta:  E^{n+1/2}
   const double d = c.d_uniform;
   LineJobs<T> js{};
-  js.job[0] = job_of<T>(Eb[1], Hout[3], Hold[3], d, 0);
-  js.job[1] = job_of<T>(Ea[0], Hout[4], Hold[4], -d, 0);
+  js.job[0] = job_of<T>(Eb[1], H[0], nullptr, d, 0);
+  js.job[1] = job_of<T>(Ea[0], H[1], nullptr, -d, 0);
   cudaError_t e = launch_line<T, P>(c, 2, LM_DERIV, js, 2, "line_z_deriv");
   if (e != cudaSuccess) return e;
-  js.job[0] = job_of<T>(Eb[2], Hout[4], Hout[4], d, 0);
-  js.job[1] = job_of<T>(Ea[1], Hout[5], Hold[5], -d, 0);
+  js.job[0] = job_of<T>(Eb[2], H[1], nullptr, d, 0);
+  js.job[1] = job_of<T>(Ea[1], H[2], nullptr, -d, 0);
   e = launch_line<T, P>(c, 0, LM_DERIV, js, 2, "line_x_deriv");
   if (e != cudaSuccess) return e;
-  js.job[0] = job_of<T>(Ea[2], Hout[3], Hout[3], -d, 0);
-  js.job[1] = job_of<T>(Eb[0], Hout[5], Hout[5], d, 0);
+  js.job[0] = job_of<T>(Ea[2], H[0], nullptr, -d, 0);
+  js.job[1] = job_of<T>(Eb[0], H[2], nullptr, d, 0);
   e = launch_line<T, P>(c, 1, LM_DERIV, js, 2, "line_y_deriv");
   if (e != cudaSuccess) return e;
   if (half == 2) e = advance_clock(c);
@@ -1284,9 +1285,12 @@ cudaError_t prepare_tp(int optin) {
   cudaError_t e = opt_in(rhs_kernel<T, P, 32, 8, 8>, optin);
   if (e == cudaSuccess) e = opt_in(rhs_e_kernel<T, P, 1>, optin);
   if (e == cudaSuccess) e = opt_in(rhs_e_kernel<T, P, 2>, optin);
-  if (e == cudaSuccess) e = opt_in(line_kernel<T, P, LM_MASS>, optin);
-  if (e == cudaSuccess) e = opt_in(line_kernel<T, P, LM_STIFF>, optin);
-  if (e == cudaSuccess) e = opt_in(line_kernel<T, P, LM_DERIV>, optin);
+  if (e == cudaSuccess) e = opt_in(line_kernel<T, P, LM_MASS, true>, optin);
+  if (e == cudaSuccess) e = opt_in(line_kernel<T, P, LM_STIFF, true>, optin);
+  if (e == cudaSuccess) e = opt_in(line_kernel<T, P, LM_DERIV, true>, optin);
+  if (e == cudaSuccess) e = opt_in(line_kernel<T, P, LM_MASS, false>, optin);
+  if (e == cudaSuccess) e = opt_in(line_kernel<T, P, LM_STIFF, false>, optin);
+  if (e == cudaSuccess) e = opt_in(line_kernel<T, P, LM_DERIV, false>, optin);
   return e;
 }
 
