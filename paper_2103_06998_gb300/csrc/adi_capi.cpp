@@ -35,7 +35,7 @@ void free_ctx(Ctx* c0) {
   adi_ctx* c = static_cast<adi_ctx*>(c0);
   if (c->graph) cudaGraphExecDestroy(c->graph);
   for (auto* l : c->pending) delete l;
-  void* ptrs[] = {c->d_eps, c->d_mu, c->d_sigma, c->stage, c->tab, c->d_clock_t0, c->d_clock_step};
+  void* ptrs[] = {c->d_eps, c->d_mu, c->d_sigma, c->stage, c->tab, c->d_clock_t0, c->d_clock_step, c->d_err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int i = 0; i < 6; ++i) {
@@ -165,6 +165,8 @@ adi_status adi_create(int nx, int ny, int nz, int p, double dt, const double* ep
   c->p = p;
   for (int d = 0; d < 3; ++d) c->N[d] = c->n[d] + p;
   c->Nc = (size_t)c->N[0] * c->N[1] * c->N[2];
+  c->pitch = (c->N[0] + 3) & ~3;  // 16-byte aligned rows (TMA strides) in FP32 and FP64
+  c->Np = (size_t)c->pitch * c->N[1] * c->N[2];
   c->precision = prec;
   c->use_graph = use_graph;
   c->esize = prec == ADI_PREC_FP64 ? 8 : 4;
@@ -180,7 +182,7 @@ adi_status adi_create(int nx, int ny, int nz, int p, double dt, const double* ep
     return cuda_fail(nullptr, e, "adi_create: cudaStreamCreate");
   }
   c->own_stream = true;
-  const size_t fb = c->Nc * c->esize;
+  const size_t fb = c->Np * c->esize;
   bool ok = true;
   auto alloc = [&](void** p, size_t bytes) {
     if (!ok) return;
@@ -196,6 +198,7 @@ adi_status adi_create(int nx, int ny, int nz, int p, double dt, const double* ep
   alloc((void**)&c->d_sigma, ne * sizeof(double));
   alloc((void**)&c->d_clock_t0, sizeof(double));
   alloc((void**)&c->d_clock_step, sizeof(long long));
+  alloc((void**)&c->d_err, sizeof(int));
   if (!ok) {
     cudaGetLastError();
     free_ctx(c);
@@ -236,6 +239,7 @@ adi_status adi_create(int nx, int ny, int nz, int p, double dt, const double* ep
     }
   }
   if (e == cudaSuccess) e = adi::set_clock(*c, 0.0);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
     free_ctx(c);
@@ -249,6 +253,7 @@ adi_status adi_create(int nx, int ny, int nz, int p, double dt, const double* ep
 adi_status adi_factor(adi_handle h) {
   if (!h) return fail(nullptr, ADI_EINVAL, "adi_factor: NULL handle");
   cudaError_t e = adi::upload_tables(*h);
+  if (e == cudaSuccess) e = adi::make_tensor_maps(*h);
   if (e != cudaSuccess) return cuda_fail(h, e, "adi_factor");
   drop_graph(h);
   h->factored = true;
@@ -368,6 +373,15 @@ adi_status adi_substep(adi_handle h, int which) {
   return ADI_OK;
 }
 
+static adi_status check_device_status(adi_handle h, const char* where) {
+  int err = 0;
+  cudaError_t e = cudaMemcpyAsync(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, where);
+  if (err) return fail(h, ADI_ETIMEOUT, std::string(where) + ": a bounded device wait gave up (TMA tile not delivered)");
+  return ADI_OK;
+}
+
 adi_status adi_fields(adi_handle h, double* EH, double* t) {
   if (!h) return fail(nullptr, ADI_EINVAL, "adi_fields: NULL handle");
   if (!EH) return fail(h, ADI_EINVAL, "adi_fields: EH is NULL");
@@ -383,6 +397,8 @@ adi_status adi_fields(adi_handle h, double* EH, double* t) {
   if (d_bad) cudaFree(d_bad);
   if (e != cudaSuccess) return cuda_fail(h, e, "adi_fields");
   if (t) *t = h->t_host + (double)h->steps_host * h->dt;
+  adi_status ds = check_device_status(h, "adi_fields");
+  if (ds != ADI_OK) return ds;
   if (bad) return fail(h, ADI_ENUMERIC, "adi_fields: NaN or Inf in the state");
   return ADI_OK;
 }
@@ -391,13 +407,14 @@ adi_status adi_fields_device(adi_handle h, void* dev_ptr, void* stream) {
   if (!h) return fail(nullptr, ADI_EINVAL, "adi_fields_device: NULL handle");
   if (!dev_ptr) return fail(h, ADI_EINVAL, "adi_fields_device: dev_ptr is NULL");
   cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
-  const size_t fb = h->Nc * h->esize;
+  const size_t fb = h->Nc * h->esize;  // dense output, N_x elements per row
   if (s != h->stream) {
     cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "adi_fields_device");
   }
   for (int i = 0; i < 6; ++i) {
-    cudaError_t e = cudaMemcpyAsync((char*)dev_ptr + i * fb, h->cur[i], fb, cudaMemcpyDeviceToDevice, s);
+    cudaError_t e = cudaMemcpy2DAsync((char*)dev_ptr + i * fb, h->N[0] * h->esize, h->cur[i], h->pitch * h->esize,
+                                      h->N[0] * h->esize, (size_t)h->N[1] * h->N[2], cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "adi_fields_device");
   }
   return ADI_OK;
@@ -416,7 +433,7 @@ adi_status adi_sync(adi_handle h) {
   if (!h) return fail(nullptr, ADI_EINVAL, "adi_sync: NULL handle");
   cudaError_t e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "adi_sync");
-  return ADI_OK;
+  return check_device_status(h, "adi_sync");
 }
 
 adi_status adi_set_profiling(adi_handle h, int on) {

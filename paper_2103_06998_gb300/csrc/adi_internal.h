@@ -2,6 +2,7 @@
 // (setup_host.cpp) and the CUDA kernels (adi_kernels.cu).
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (types only; the driver entry point is looked up at run time)
 #include <cuda_runtime.h>
 
 #include <string>
@@ -74,6 +75,7 @@ struct RhsParams {
   int nterms;
   int nfields;
   int Nx, Ny, Nz;
+  int pitch;           // elements between consecutive x rows (>= Nx, multiple of 4)
   // point source (E rows only): comp < 0 disables
   int src_comp;
   int src_i0[3];
@@ -84,6 +86,12 @@ struct RhsParams {
   long long* clock_step;
   int advance_clock;   // 1: block 0 thread 0 increments the step counter
   Stencils<T> st[3];   // interior stencils per axis (E kernel)
+  int* err;            // device status word: bit 0 = a bounded wait gave up
+};
+
+// TMA descriptors of the six input fields of one E right-hand side launch.
+struct TmaMaps {
+  CUtensorMap m[6];
 };
 
 struct LineParams {
@@ -91,6 +99,7 @@ struct LineParams {
   int N;          // line length
   long long nlines;
   int Nx, Ny, Nz;
+  int pitch;      // elements between consecutive x rows
 };
 
 enum LineMode : int { LM_MASS = 0, LM_STIFF = 1, LM_DERIV = 2 };
@@ -123,7 +132,9 @@ struct Ctx {
   int precision = ADI_PREC_FP32;
   int use_graph = 1;
   double dt = 0.0;
-  size_t Nc = 0;
+  size_t Nc = 0;      // coefficients per component (N_x N_y N_z)
+  int pitch = 0;      // device row pitch in elements: N_x rounded up to a multiple of 4
+  size_t Np = 0;      // device elements per component (pitch N_y N_z)
   size_t esize = 4;
   bool factored = false;
   std::string err;
@@ -164,6 +175,12 @@ struct Ctx {
   double src_w[3][kMaxP + 1] = {};
   double src_amp = 0, src_f0 = 0, src_t0 = 0, src_s = 1;
 
+  // TMA descriptors of the state arrays (E RHS tiles), built by adi_factor
+  CUtensorMap tmap_cur[6];
+  CUtensorMap tmap_half[3];
+  bool tmaps_ok = false;
+  int* d_err = nullptr;  // device status word written by bounded waits
+
   // graph of one step
   cudaGraphExec_t graph = nullptr;
 
@@ -180,6 +197,7 @@ cudaError_t run_substep(Ctx& c, int which);
 cudaError_t set_fields_dev(Ctx& c, const double* d_src);
 cudaError_t get_fields_dev(Ctx& c, double* d_dst, int* d_bad);
 cudaError_t set_clock(Ctx& c, double t0);
+cudaError_t make_tensor_maps(Ctx& c);
 
 // record a failure that has no handle (readable through adi_last_error(NULL))
 adi_status fail_global(adi_status s, const std::string& msg);

@@ -43,8 +43,8 @@ __global__ void __launch_bounds__(TX* TY) rhs_kernel(const RhsParams<T> prm) {
 
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
-  const int Nx = prm.Nx, Ny = prm.Ny, Nz = prm.Nz;
-  const long long sxy = (long long)Nx * Ny;
+  const int Nx = prm.Nx, Ny = prm.Ny, Nz = prm.Nz, pitch = prm.pitch;
+  const long long sxy = (long long)pitch * Ny;
   const int gx = x0 + tx, gy = y0 + ty;
   const bool col_in = gx < Nx && gy < Ny;
 
@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(TX* TY) rhs_kernel(const RhsParams<T> prm) {
 #pragma unroll
       for (int zz = 0; zz < TZ; ++zz) {
         int gz = z0 + zz;
-        if (gz < Nz) cf[k][zz] = prm.coef[k][gz * sxy + (long long)gy * Nx + gx];
+        if (gz < Nz) cf[k][zz] = prm.coef[k][gz * sxy + (long long)gy * pitch + gx];
       }
     }
   }
@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(TX* TY) rhs_kernel(const RhsParams<T> prm) {
         int xx = i % HX, r = i / HX, yy = r % HY, zz = r / HY;
         int X = x0 - P + xx, Y = y0 - P + yy, Z = z0 - P + zz;
         T v = T(0);
-        if (X >= 0 && X < Nx && Y >= 0 && Y < Ny && Z >= 0 && Z < Nz) v = f[Z * sxy + (long long)Y * Nx + X];
+        if (X >= 0 && X < Nx && Y >= 0 && Y < Ny && Z >= 0 && Z < Nz) v = f[Z * sxy + (long long)Y * pitch + X];
         s_in[i] = v;
       }
       cur_field = tm.field;
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(TX* TY) rhs_kernel(const RhsParams<T> prm) {
           if (ix >= 0 && ix <= P && iy >= 0 && iy <= P && iz >= 0 && iz <= P)
             v -= cf[2][zz] * T(g) * prm.src_w[0][ix] * prm.src_w[1][iy] * prm.src_w[2][iz];
         }
-        prm.out[c][gz * sxy + (long long)gy * Nx + gx] = v;
+        prm.out[c][gz * sxy + (long long)gy * pitch + gx] = v;
       }
     }
   }
@@ -261,11 +261,11 @@ __global__ void __launch_bounds__(64) line_kernel(const LineJobs<T> jobs, const 
   // ---- stage the tile (and c for STIFF)
   long long off = 0, stride = 1;  // first element and stride of this thread's line (columns)
   if (XDIR) {
-    const T* base = src + (long long)L0 * N;
-    const T* cb = MODE == LM_STIFF ? cvec + (long long)L0 * N : nullptr;
+    const T* base = src + (long long)L0 * lp.pitch;
+    const T* cb = MODE == LM_STIFF ? cvec + (long long)L0 * lp.pitch : nullptr;
     for (int line = 0; line < cnt; ++line) {
-      const T* g = base + (long long)line * N;
-      const T* gc = MODE == LM_STIFF ? cb + (long long)line * N : nullptr;
+      const T* g = base + (long long)line * lp.pitch;
+      const T* gc = MODE == LM_STIFF ? cb + (long long)line * lp.pitch : nullptr;
       for (int k = t; k < N; k += LINES) {
         cp_async_elem(&sr[k * LP + line], g + k);
         if (MODE == LM_STIFF) cp_async_elem(&su[k * LP + line], gc + k);
@@ -273,12 +273,12 @@ __global__ void __launch_bounds__(64) line_kernel(const LineJobs<T> jobs, const 
     }
   } else if (t < cnt) {
     const int L = L0 + t;
-    if (lp.dir == 1) {
-      off = (long long)(L / lp.Nx) * lp.Nx * lp.Ny + (L % lp.Nx);
-      stride = lp.Nx;
-    } else {
-      off = L;
-      stride = (long long)lp.Nx * lp.Ny;
+    if (lp.dir == 1) {  // line L = z * N_x + x
+      off = (long long)(L / lp.Nx) * lp.pitch * lp.Ny + (L % lp.Nx);
+      stride = lp.pitch;
+    } else {            // line L = y * N_x + x
+      off = (long long)(L / lp.Nx) * lp.pitch + (L % lp.Nx);
+      stride = (long long)lp.pitch * lp.Ny;
     }
     const T* g = src + off;
     const T* gc = MODE == LM_STIFF ? cvec + off : nullptr;
@@ -442,9 +442,9 @@ __global__ void __launch_bounds__(64) line_kernel(const LineJobs<T> jobs, const 
 
   // ---- write back (LM_DERIV: dst += scale * x, done by the L2)
   if (XDIR) {
-    T* base = dst + (long long)L0 * N;
+    T* base = dst + (long long)L0 * lp.pitch;
     for (int line = 0; line < cnt; ++line) {
-      T* g = base + (long long)line * N;
+      T* g = base + (long long)line * lp.pitch;
       for (int k = t; k < N; k += LINES) {
         const T v = sr[k * LP + line];
         if (MODE == LM_DERIV) red_add(g + k, scale * v);
@@ -519,17 +519,26 @@ __device__ __forceinline__ T bandv(const RhsParams<T>& prm, int r, int q) {
 template <typename T, int P>
 struct Smem {
   static constexpr int HX = TX + 2 * P, HY = TY + 2 * P, HZ = TZ + 2 * P;
-  static constexpr int TILE = HZ * HY * HX, ZR = TZ * HY * HX, YR = TZ * TY * HX;
+  static constexpr int BX = 40;       // tile row: x0-4 .. x0+35 (TMA box)
+  static constexpr int XOFF = 4 - P;  // position of x0-P inside a tile row
+  static constexpr int TILE = HZ * HY * BX, ZR = TZ * HY * HX, YR = TZ * TY * HX;
+  // dynamic shared memory: 128 bytes of alignment slack, the tiles (TMA
+  // destinations, 128-byte aligned), the pass buffers, then two mbarriers
+  static constexpr size_t DATA2 = sizeof(T) * (2 * (size_t)TILE + 2 * (size_t)ZR + 2 * (size_t)YR);
+  static constexpr int NBUF = DATA2 + 128 + 16 <= 227 * 1024 ? 2 : 1;  // double-buffer the tiles if it fits
+  static constexpr size_t DATA = sizeof(T) * (NBUF * (size_t)TILE + 2 * (size_t)ZR + 2 * (size_t)YR);
+  static constexpr size_t BYTES = 128 + DATA + 16;
 };
 
-// z pass: column i of the haloed plane, 8 outputs from a window of HZ values
+// z pass: column i = (yy, xx) of the haloed plane, 8 outputs from a window of HZ values
 template <typename T, int P, int OP, bool INNER>
 __device__ __forceinline__ void zpass(const RhsParams<T>& prm, const T* tl, T* zr, int z0, int i) {
   using S = Smem<T, P>;
   constexpr int W = 2 * P + 1;
+  const T* col = tl + (i / S::HX) * S::BX + S::XOFF + (i % S::HX);
   T w[S::HZ];
 #pragma unroll
-  for (int k = 0; k < S::HZ; ++k) w[k] = tl[k * S::HY * S::HX + i];
+  for (int k = 0; k < S::HZ; ++k) w[k] = col[k * S::HY * S::BX];
 #pragma unroll
   for (int zz = 0; zz < TZ; ++zz) {
     T s = T(0);
@@ -584,42 +593,60 @@ __device__ __forceinline__ void xpass(const RhsParams<T>& prm, const T* yr, int 
   }
 }
 
+// TMA: one 3D box per field tile; x starts at x0 - 4 so that x * sizeof(T) is a
+// multiple of 16 bytes; out-of-domain elements arrive as zeros.
+constexpr int BOXX = 40;
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(bar)) : "memory");
+}
+
 template <typename T, int P>
-__device__ __forceinline__ void stage(const RhsParams<T>& prm, int f, T* s, int x0, int y0, int z0) {
+__device__ __forceinline__ void tma_tile(const CUtensorMap* map, T* dst, unsigned long long* bar, int x, int y, int z) {
   using S = Smem<T, P>;
-  const T* __restrict__ g = prm.fields[f];
-  const int Nx = prm.Nx, Ny = prm.Ny, Nz = prm.Nz;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int row = warp; row < S::HZ * S::HY; row += NT / 32) {
-    const int yy = row % S::HY, zz = row / S::HY;
-    const int Y = y0 - P + yy, Z = z0 - P + zz;
-    T* srow = s + row * S::HX;
-    const bool rin = Y >= 0 && Y < Ny && Z >= 0 && Z < Nz;
-    const T* grow = g + ((long long)Z * Ny + Y) * Nx;
-    for (int xx = lane; xx < S::HX; xx += 32) {
-      const int X = x0 - P + xx;
-      if (rin && X >= 0 && X < Nx) cp_async_elem(&srow[xx], &grow[X]);
-      else srow[xx] = T(0);
-    }
+  constexpr unsigned bytes = BOXX * S::HY * S::HZ * sizeof(T);
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(
+          smem_addr(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Wait for phase `parity` of the barrier with an iteration limit; false if it gave up.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  const unsigned a = smem_addr(bar);
+  for (int it = 0; it < (1 << 22); ++it) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
   }
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  return false;
 }
 
 template <typename T, int P, int H, int F>
-__device__ __forceinline__ void do_field(const RhsParams<T>& prm, T* s_tile, T* s_zr, T* s_yr, int x0, int y0,
-                                         int z0, bool inZ, bool inY, bool inX, int xp, int rg,
-                                         T (&cf)[3][4][2], T (&acc)[3][4][2]) {
+__device__ __forceinline__ bool do_field(const RhsParams<T>& prm, const TmaMaps& maps, T* s_tile, T* s_zr,
+                                         T* s_yr, unsigned long long* bars, int x0, int y0, int z0, bool inZ,
+                                         bool inY, bool inX, int xp, int rg, T (&cf)[3][4][2],
+                                         T (&acc)[3][4][2]) {
   using S = Smem<T, P>;
   using PL = Plan<H, F>;
   const int tid = threadIdx.x;
-  if (F + 1 < 6) {
-    stage<T, P>(prm, F + 1, s_tile + ((F + 1) & 1) * S::TILE, x0, y0, z0);
-    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-  } else {
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-  }
-  __syncthreads();
-  const T* tl = s_tile + (F & 1) * S::TILE;
+  constexpr int B = S::NBUF == 2 ? (F & 1) : 0;          // buffer of this field
+  constexpr unsigned PAR = S::NBUF == 2 ? (F / 2) & 1 : F & 1;  // its barrier phase
+  if (S::NBUF == 2 && F + 1 < 6 && tid == 0)  // prefetch the next field into the other buffer
+    tma_tile<T, P>(&maps.m[F + 1], s_tile + ((F + 1) & 1) * S::TILE, &bars[(F + 1) & 1], x0 - 4, y0 - P, z0 - P);
+  // every thread waits for the tile; the give-up decision is made block-wide
+  if (!__syncthreads_and(mbar_wait(&bars[B], PAR))) return false;
+  const T* tl = s_tile + B * S::TILE;
   constexpr bool zshare = PL::z0 == PL::z1;
   for (int i = tid; i < S::HY * S::HX; i += NT) {
     if (inZ) zpass<T, P, PL::z0, true>(prm, tl, s_zr, z0, i);
@@ -650,21 +677,28 @@ __device__ __forceinline__ void do_field(const RhsParams<T>& prm, T* s_tile, T* 
     xpass<T, P, PL::x1, false, PL::o1, PL::c1 - CF_A>(prm, s_yr + S::YR, gx, xp, rg, PL::s1, cf, acc);
   }
   __syncthreads();
+  if (S::NBUF == 1 && F + 1 < 6 && tid == 0)  // single buffer: load the next field now
+    tma_tile<T, P>(&maps.m[F + 1], s_tile, &bars[0], x0 - 4, y0 - P, z0 - P);
+  return true;
 }
 }  // namespace rhs2
 
 template <typename T, int P, int H>
-__global__ void __launch_bounds__(rhs2::NT, sizeof(T) == 4 ? 2 : 1) rhs_e_kernel(const RhsParams<T> prm) {
+__global__ void __launch_bounds__(rhs2::NT, sizeof(T) == 4 ? 2 : 1)
+    rhs_e_kernel(const RhsParams<T> prm, const __grid_constant__ TmaMaps maps) {
   using namespace rhs2;
   using S = Smem<T, P>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* s_tile = reinterpret_cast<T*>(smem_raw);  // 2 x TILE (double buffer)
-  T* s_zr = s_tile + 2 * S::TILE;               // 2 x ZR
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  // TMA writes need a 128-byte aligned shared address: align at run time
+  unsigned char* sbase = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(sbase + S::DATA);  // 8-byte aligned
+  T* s_tile = reinterpret_cast<T*>(sbase);     // NBUF x TILE (TMA destinations)
+  T* s_zr = s_tile + S::NBUF * S::TILE;         // 2 x ZR
   T* s_yr = s_zr + 2 * S::ZR;                   // 2 x YR
   const int tid = threadIdx.x;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
-  const int Nx = prm.Nx, Ny = prm.Ny, Nz = prm.Nz;
-  const long long sxy = (long long)Nx * Ny;
+  const int Nx = prm.Nx, Ny = prm.Ny, Nz = prm.Nz, pitch = prm.pitch;
+  const long long sxy = (long long)pitch * Ny;
   // tile-level interior tests (band rows of all outputs of the tile)
   const bool inZ = z0 >= prm.st[2].lo && z0 + TZ - 1 <= prm.st[2].hi;
   const bool inY = y0 >= prm.st[1].lo && y0 + TY - 1 <= prm.st[1].hi;
@@ -680,7 +714,7 @@ __global__ void __launch_bounds__(rhs2::NT, sizeof(T) == 4 ? 2 : 1) rhs_e_kernel
     for (int j = 0; j < 2; ++j) {
       const int gx = x0 + xp + j;
       const bool in = gx < Nx && gy < Ny && gz < Nz;
-      const long long g = gz * sxy + (long long)gy * Nx + gx;
+      const long long g = gz * sxy + (long long)gy * pitch + gx;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         cf[c][r][j] = in ? prm.coef[1 + c][g] : T(0);
@@ -688,13 +722,26 @@ __global__ void __launch_bounds__(rhs2::NT, sizeof(T) == 4 ? 2 : 1) rhs_e_kernel
       }
     }
   }
-  stage<T, P>(prm, 0, s_tile, x0, y0, z0);
-  do_field<T, P, H, 0>(prm, s_tile, s_zr, s_yr, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
-  do_field<T, P, H, 1>(prm, s_tile, s_zr, s_yr, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
-  do_field<T, P, H, 2>(prm, s_tile, s_zr, s_yr, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
-  do_field<T, P, H, 3>(prm, s_tile, s_zr, s_yr, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
-  do_field<T, P, H, 4>(prm, s_tile, s_zr, s_yr, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
-  do_field<T, P, H, 5>(prm, s_tile, s_zr, s_yr, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+  if (tid == 0) {
+    mbar_init(&bars[0]);
+    mbar_init(&bars[1]);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0) tma_tile<T, P>(&maps.m[0], s_tile, &bars[0], x0 - 4, y0 - P, z0 - P);
+  bool ok = do_field<T, P, H, 0>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+  if (ok) ok = do_field<T, P, H, 1>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+  if (ok) ok = do_field<T, P, H, 2>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+  if (ok) ok = do_field<T, P, H, 3>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+  if (ok) ok = do_field<T, P, H, 4>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+  if (ok) ok = do_field<T, P, H, 5>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+  if (!ok) {
+    // a tile never arrived: report, give the copies in flight a bounded time, leave
+    if (tid == 0) atomicOr(prm.err, 1);
+    mbar_wait(&bars[0], 0);
+    mbar_wait(&bars[1], 0);
+    return;
+  }
 
   // ---- point source and store (two consecutive x per row)
   double g = 0.0;
@@ -720,7 +767,7 @@ __global__ void __launch_bounds__(rhs2::NT, sizeof(T) == 4 ? 2 : 1) rhs_e_kernel
           if (ix >= 0 && ix <= P && iy >= 0 && iy <= P && iz >= 0 && iz <= P)
             v -= cf[1][r][j] * T(g) * prm.src_w[0][ix] * prm.src_w[1][iy] * prm.src_w[2][iz];
         }
-        prm.out[c][gz * sxy + (long long)gy * Nx + gx] = v;
+        prm.out[c][gz * sxy + (long long)gy * pitch + gx] = v;
       }
     }
   }
@@ -742,7 +789,7 @@ __device__ __forceinline__ bool constrained(int comp, int i, int j, int k, int N
 
 template <typename T>
 __global__ void set_fields_kernel(const double* __restrict__ src, T* d0, T* d1, T* d2, T* d3, T* d4, T* d5,
-                                  int Nx, int Ny, int Nz) {
+                                  int Nx, int Ny, int Nz, int pitch) {
   const long long Nc = (long long)Nx * Ny * Nz;
   T* dst[6] = {d0, d1, d2, d3, d4, d5};
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < 6 * Nc;
@@ -751,18 +798,21 @@ __global__ void set_fields_kernel(const double* __restrict__ src, T* d0, T* d1, 
     long long r = g % Nc;
     int i = (int)(r % Nx), j = (int)((r / Nx) % Ny), k = (int)(r / ((long long)Nx * Ny));
     double v = src[g];
-    dst[comp][r] = constrained(comp, i, j, k, Nx, Ny, Nz) ? T(0) : T(v);
+    dst[comp][((long long)k * Ny + j) * pitch + i] = constrained(comp, i, j, k, Nx, Ny, Nz) ? T(0) : T(v);
   }
 }
 
 template <typename T>
 __global__ void get_fields_kernel(double* __restrict__ dst, const T* s0, const T* s1, const T* s2, const T* s3,
-                                  const T* s4, const T* s5, long long Nc, int* bad) {
+                                  const T* s4, const T* s5, int Nx, int Ny, int Nz, int pitch, int* bad) {
   const T* src[6] = {s0, s1, s2, s3, s4, s5};
+  const long long Nc = (long long)Nx * Ny * Nz;
   int local_bad = 0;
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < 6 * Nc;
        g += (long long)gridDim.x * blockDim.x) {
-    double v = (double)src[g / Nc][g % Nc];
+    const long long r = g % Nc;
+    const int i = (int)(r % Nx), j = (int)((r / Nx) % Ny), k = (int)(r / ((long long)Nx * Ny));
+    double v = (double)src[g / Nc][((long long)k * Ny + j) * pitch + i];
     if (!isfinite(v)) local_bad = 1;
     dst[g] = v;
   }
@@ -782,7 +832,7 @@ template <typename T>
 __global__ void coef_kernel(const double* __restrict__ eps, const double* __restrict__ mu,
                             const double* __restrict__ sig, const double* __restrict__ Gx,
                             const double* __restrict__ Gy, const double* __restrict__ Gz, int nx, int ny,
-                            int nz, int p, double tau, T* ca, T* cb, T* cc, T* cd,
+                            int nz, int p, int pitch, double tau, T* ca, T* cb, T* cc, T* cd,
                             unsigned long long* min_bits) {
   const int Nx = nx + p, Ny = ny + p, Nz = nz + p;
   const long long Nc = (long long)Nx * Ny * Nz;
@@ -813,10 +863,11 @@ __global__ void coef_kernel(const double* __restrict__ eps, const double* __rest
     }
     double eh = ne / den, mh = nm / den, sh = ns / den;
     double alpha = sh * tau / (4.0 * eh);
-    ca[g] = T((1.0 - alpha) / (1.0 + alpha));
-    cb[g] = T(tau / (2.0 * eh * (1.0 + alpha)));
-    cc[g] = T(tau * tau / (4.0 * eh * mh * (1.0 + alpha)));
-    cd[g] = T(tau / (2.0 * mh));
+    const long long o = ((long long)t * Ny + s) * pitch + r;
+    ca[o] = T((1.0 - alpha) / (1.0 + alpha));
+    cb[o] = T(tau / (2.0 * eh * (1.0 + alpha)));
+    cc[o] = T(tau * tau / (4.0 * eh * mh * (1.0 + alpha)));
+    cd[o] = T(tau / (2.0 * mh));
     local_min = fmin(local_min, eh * mh);
   }
   // positive doubles order like their bit patterns
@@ -1018,8 +1069,24 @@ cudaError_t advance_clock(Ctx& c) {
 
 template <typename T, int P>
 size_t rhs_e_smem() {
-  using S = rhs2::Smem<T, P>;
-  return sizeof(T) * (2 * (size_t)S::TILE + 2 * (size_t)S::ZR + 2 * (size_t)S::YR);
+  return rhs2::Smem<T, P>::BYTES;
+}
+
+// TMA descriptor of one state array: dims (N_x, N_y, N_z), row pitch c.pitch,
+// box (40, 8 + 2p, 8 + 2p) for the E right-hand side tiles.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+cudaError_t encode_map(Ctx& c, EncodeTiledFn fn, void* base, CUtensorMap* out) {
+  const cuuint64_t dims[3] = {(cuuint64_t)c.N[0], (cuuint64_t)c.N[1], (cuuint64_t)c.N[2]};
+  const cuuint64_t strides[2] = {(cuuint64_t)c.pitch * c.esize, (cuuint64_t)c.pitch * c.N[1] * c.esize};
+  const cuuint32_t box[3] = {(cuuint32_t)rhs2::BOXX, (cuuint32_t)(rhs2::TY + 2 * c.p), (cuuint32_t)(rhs2::TZ + 2 * c.p)};
+  const cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = fn(out, c.precision == ADI_PREC_FP64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                  3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 template <typename T>
@@ -1039,11 +1106,18 @@ Stencils<T> stencils_of(const Axis1D& ax) {
 template <typename T, int P>
 cudaError_t launch_rhs_e(Ctx& c, RhsParams<T>& prm, int half, double bytes) {
   using namespace rhs2;
+  if (!c.tmaps_ok) return cudaErrorInvalidValue;
   for (int d = 0; d < 3; ++d) prm.st[d] = stencils_of<T>(c.axes[d]);
+  prm.err = c.d_err;
+  TmaMaps maps;
+  for (int i = 0; i < 3; ++i) {
+    maps.m[i] = half == 1 ? c.tmap_cur[i] : c.tmap_half[i];  // E^n or E^{n+1/2}
+    maps.m[3 + i] = c.tmap_cur[3 + i];                         // H (one buffer)
+  }
   dim3 grid((c.N[0] + TX - 1) / TX, (c.N[1] + TY - 1) / TY, (c.N[2] + TZ - 1) / TZ);
   prof_begin(c, "rhs_E", bytes);
-  if (half == 1) rhs_e_kernel<T, P, 1><<<grid, NT, rhs_e_smem<T, P>(), c.stream>>>(prm);
-  else rhs_e_kernel<T, P, 2><<<grid, NT, rhs_e_smem<T, P>(), c.stream>>>(prm);
+  if (half == 1) rhs_e_kernel<T, P, 1><<<grid, NT, rhs_e_smem<T, P>(), c.stream>>>(prm, maps);
+  else rhs_e_kernel<T, P, 2><<<grid, NT, rhs_e_smem<T, P>(), c.stream>>>(prm, maps);
   prof_end(c);
   return cudaGetLastError();
 }
@@ -1056,6 +1130,7 @@ cudaError_t launch_line(Ctx& c, int dir, int mode, const LineJobs<T>& jobs, int 
   lp.Nx = c.N[0];
   lp.Ny = c.N[1];
   lp.Nz = c.N[2];
+  lp.pitch = c.pitch;
   lp.nlines = (long long)c.N[0] * c.N[1] * c.N[2] / c.N[dir];
   const int W = 2 * P + 1;
   const int tabw = mode == LM_STIFF ? 2 * W : (mode == LM_DERIV ? 3 * P + 1 + W : 3 * P + 1);
@@ -1128,6 +1203,7 @@ cudaError_t e_substep(Ctx& c, int half) {
   prm.Nx = c.N[0];
   prm.Ny = c.N[1];
   prm.Nz = c.N[2];
+  prm.pitch = c.pitch;
   prm.src_comp = (c.src_comp >= 0 && c.src_amp != 0.0) ? c.src_comp : -1;
   for (int d = 0; d < 3; ++d) {
     prm.src_i0[d] = c.src_i0[d];
@@ -1195,6 +1271,7 @@ cudaError_t h_substep_general(Ctx& c, int half) {
   prm.Nx = c.N[0];
   prm.Ny = c.N[1];
   prm.Nz = c.N[2];
+  prm.pitch = c.pitch;
   prm.src_comp = -1;
   prm.clock_t0 = c.d_clock_t0;
   prm.clock_step = c.d_clock_step;
@@ -1330,10 +1407,10 @@ cudaError_t set_fields_dev(Ctx& c, const double* d_src) {
   unsigned g = grid_for(6LL * (long long)c.Nc, 256);
   if (c.precision == ADI_PREC_FP64) {
     double** d = reinterpret_cast<double**>(c.cur);
-    set_fields_kernel<double><<<g, 256, 0, c.stream>>>(d_src, d[0], d[1], d[2], d[3], d[4], d[5], c.N[0], c.N[1], c.N[2]);
+    set_fields_kernel<double><<<g, 256, 0, c.stream>>>(d_src, d[0], d[1], d[2], d[3], d[4], d[5], c.N[0], c.N[1], c.N[2], c.pitch);
   } else {
     float** d = reinterpret_cast<float**>(c.cur);
-    set_fields_kernel<float><<<g, 256, 0, c.stream>>>(d_src, d[0], d[1], d[2], d[3], d[4], d[5], c.N[0], c.N[1], c.N[2]);
+    set_fields_kernel<float><<<g, 256, 0, c.stream>>>(d_src, d[0], d[1], d[2], d[3], d[4], d[5], c.N[0], c.N[1], c.N[2], c.pitch);
   }
   return cudaGetLastError();
 }
@@ -1342,12 +1419,25 @@ cudaError_t get_fields_dev(Ctx& c, double* d_dst, int* d_bad) {
   unsigned g = grid_for(6LL * (long long)c.Nc, 256);
   if (c.precision == ADI_PREC_FP64) {
     double** s = reinterpret_cast<double**>(c.cur);
-    get_fields_kernel<double><<<g, 256, 0, c.stream>>>(d_dst, s[0], s[1], s[2], s[3], s[4], s[5], (long long)c.Nc, d_bad);
+    get_fields_kernel<double><<<g, 256, 0, c.stream>>>(d_dst, s[0], s[1], s[2], s[3], s[4], s[5], c.N[0], c.N[1], c.N[2], c.pitch, d_bad);
   } else {
     float** s = reinterpret_cast<float**>(c.cur);
-    get_fields_kernel<float><<<g, 256, 0, c.stream>>>(d_dst, s[0], s[1], s[2], s[3], s[4], s[5], (long long)c.Nc, d_bad);
+    get_fields_kernel<float><<<g, 256, 0, c.stream>>>(d_dst, s[0], s[1], s[2], s[3], s[4], s[5], c.N[0], c.N[1], c.N[2], c.pitch, d_bad);
   }
   return cudaGetLastError();
+}
+
+cudaError_t make_tensor_maps(Ctx& c) {
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+  if (e != cudaSuccess) return e;
+  if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+  EncodeTiledFn enc = reinterpret_cast<EncodeTiledFn>(fn);
+  for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = encode_map(c, enc, c.cur[i], &c.tmap_cur[i]);
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = encode_map(c, enc, c.half[i], &c.tmap_half[i]);
+  c.tmaps_ok = e == cudaSuccess;
+  return e;
 }
 
 cudaError_t set_clock(Ctx& c, double t0) {
@@ -1376,11 +1466,11 @@ cudaError_t compute_coefficients(Ctx& c) {
   if (c.precision == ADI_PREC_FP64) {
     double** cf = reinterpret_cast<double**>(c.coef);
     coef_kernel<double><<<g, 256, 0, c.stream>>>(c.d_eps, c.d_mu, c.d_sigma, dG + offs[0], dG + offs[1], dG + offs[2],
-                                                c.n[0], c.n[1], c.n[2], p, c.dt, cf[0], cf[1], cf[2], cf[3], dmin);
+                                                c.n[0], c.n[1], c.n[2], p, c.pitch, c.dt, cf[0], cf[1], cf[2], cf[3], dmin);
   } else {
     float** cf = reinterpret_cast<float**>(c.coef);
     coef_kernel<float><<<g, 256, 0, c.stream>>>(c.d_eps, c.d_mu, c.d_sigma, dG + offs[0], dG + offs[1], dG + offs[2],
-                                               c.n[0], c.n[1], c.n[2], p, c.dt, cf[0], cf[1], cf[2], cf[3], dmin);
+                                               c.n[0], c.n[1], c.n[2], p, c.pitch, c.dt, cf[0], cf[1], cf[2], cf[3], dmin);
   }
   e = cudaGetLastError();
   unsigned long long bits = 0;
