@@ -21,6 +21,10 @@ struct Axis1D {
   std::vector<double> M, S, A, B;  // bands, row k: [k*(2p+1) + d] = X[k][k+d-p]
   std::vector<double> G;           // G[r*(p+1) + a] = int over element r-p+a of B_r
 };
+struct LuConst {  // rows lo..hi of a mass LU share the factors v (in the working precision)
+  int lo = 1, hi = 0;
+  double v[3 * kMaxP + 1] = {};
+};
 struct BandLU {
   int N = 0, p = 0, lo = 0, hi = 0;
   std::vector<double> L, inv_d, U;  // L[k*p+q-1], U[k*p+q-1] for q = 1..p
@@ -47,6 +51,10 @@ struct AxisDev {
   // rows inner_lo .. inner_hi of M, S, A, B equal the interior stencil inner[op]
   T inner[4][2 * kMaxP + 1];
   int inner_lo, inner_hi;
+  // rows lu_lo[f] .. lu_hi[f] of the mass LU f have the factors luc[f] in T:
+  // [L(1..p), 1/pivot, U(1..p)]
+  T luc[2][3 * kMaxP + 1];
+  int lu_lo[2], lu_hi[2];
 };
 
 struct Term {
@@ -102,15 +110,16 @@ struct LineParams {
   int pitch;      // elements between consecutive x rows
 };
 
-enum LineMode : int { LM_MASS = 0, LM_STIFF = 1, LM_DERIV = 2 };
+enum LineMode : int { LM_MASS = 0, LM_STIFF = 1, LM_DERIV = 2, LM_PIVOT = 3 };
 
 // One array's line solve inside a launch (blockIdx.y selects the job).
 template <typename T>
 struct LineJob {
   const T* src;   // right-hand side (MASS, STIFF) or the differentiated field (DERIV)
-  T* dst;         // result (may alias src or aux)
-  const T* aux;   // c (STIFF) or the field the derivative is added to (DERIV)
-  T scale;        // DERIV: dst = aux + scale * M^-1 A src
+  T* dst;         // result (may alias src); DERIV adds into it; PIVOT writes 1/pivot
+  const T* aux;   // c (STIFF, PIVOT)
+  const T* aux2;  // STIFF: inverse pivots of M + c S from an LM_PIVOT pass
+  T scale;        // DERIV: dst += scale * M^-1 A src
   int dirichlet;  // 1: first and last coefficient are fixed to zero
 };
 template <typename T>
@@ -159,11 +168,13 @@ struct Ctx {
   void* rhs[3] = {};
   void* coef[4] = {};   // a, b, c, d
   void* stage = nullptr;  // Nc doubles for host transfers (FP32 mode)
+  void* pivots[3] = {};   // inverse pivots of the row-scaled M + c S, per stiffness axis
 
   // 1D tables on device (element type T)
   void* tab = nullptr;
   size_t tab_bytes = 0;
   Axis1D axes[3];
+  LuConst luconst[3][2];  // per axis: full and Dirichlet-reduced mass LU
   double* d_clock_t0 = nullptr;
   long long* d_clock_step = nullptr;
   double t_host = 0.0;

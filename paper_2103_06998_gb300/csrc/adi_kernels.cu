@@ -201,45 +201,47 @@ __device__ __forceinline__ void red_add(double* p, double v) {
 // Banded solves along one axis, one thread per line (Gaussian elimination
 // without pivoting restricted to the band; Appendix, eqs. split1/split2).
 //   LM_MASS : dst = M^-1 src with the precomputed (full or Dirichlet) mass LU.
-//   LM_STIFF: dst = (M + diag(c) S)^-1 src; the LU of each line is formed row by
-//             row from c (per-test-function material), and its normalised upper
-//             factors are kept in shared memory for the back substitution.
+//   LM_STIFF: dst = (M + diag(c) S)^-1 src; the LU of each line is formed row
+//             by row from c (per-test-function material) and the inverse
+//             pivots of an LM_PIVOT pass (they depend only on c and tau), so
+//             no reciprocal lies on the recurrence; the normalised upper factors
+//             are kept in shared memory for the back substitution.
 //   LM_DERIV: dst += scale * M^-1 (A src): the 1D derivative in the L2 sense,
 //             added in place with red.global.add (H half steps, uniform mu).
+//   LM_PIVOT: dst = 1 / pivots of the LU of M + diag(c) S (run once per dt).
 // A tile of LINES lines is staged with cp.async into shared memory as
 // [row][line] (x lines transposed; pitch LINES+1 for x so both the staging and
 // the per-thread recurrence are bank-conflict free), solved in place, written
-// back.  The 1D tables of the axis are staged into shared memory as well.
+// back.  The 1D tables of the axis are staged into shared memory; rows whose
+// factors equal the mid-line factors in T use register constants instead.
 // blockIdx.y selects one of up to three independent jobs on the same axis.
 template <typename T, int P, int MODE, bool XDIR>
 __global__ void __launch_bounds__(64) line_kernel(const LineJobs<T> jobs, const LineParams lp, const AxisDev<T> ax) {
   constexpr int W = 2 * P + 1;
+  constexpr bool FACT = MODE == LM_STIFF || MODE == LM_PIVOT;  // works on M + c S
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // static parameter offsets (a dynamic index would copy the struct to the stack)
   const LineJob<T> job = blockIdx.y == 0 ? jobs.job[0] : (blockIdx.y == 1 ? jobs.job[1] : jobs.job[2]);
-  const T* __restrict__ src = job.src;
-  T* dst = job.dst;
-  const T* __restrict__ cvec = job.aux;
   const int dch = job.dirichlet;
-  const T scale = job.scale;
   const int LINES = blockDim.x, LP = XDIR ? LINES + 1 : LINES, N = lp.N;
-  // shared memory: tables | data [N][LP] | STIFF: c then P factor planes
-  constexpr int TABW = MODE == LM_STIFF ? 2 * W : (MODE == LM_DERIV ? 3 * P + 1 + W : 3 * P + 1);
+  constexpr int TABW = FACT ? 2 * W : (MODE == LM_DERIV ? 3 * P + 1 + W : 3 * P + 1);
   T* tab = reinterpret_cast<T*>(smem_raw);
-  T* sr = tab + ((N * TABW + 3) & ~3);
-  T* su = sr + N * LP;
+  T* sr = tab + ((N * TABW + 3) & ~3);  // [N][LP]: rhs, then y', then x (PIVOT: 1/pivot)
+  T* su = sr + N * LP;                  // FACT: c; STIFF: 1/pivot, then the P upper-factor planes
+  const int plane = N * LP;
   const int t = threadIdx.x;
   const int L0 = blockIdx.x * LINES;
   const int cnt = min(LINES, (int)(lp.nlines - L0));
 
-  // ---- 1D tables: MASS/DERIV [L(P) inv U(P) (A(W))], STIFF [M(W) S(W)], row-major per row
+  // ---- 1D tables: MASS/DERIV [L(P) inv U(P) (A(W))], FACT [M(W) S(W)], row-major per row
+  // (asynchronous, in flight together with the tile below)
   for (int i = t; i < N; i += LINES) {
     T* row = tab + i * TABW;
-    if (MODE == LM_STIFF) {
+    if (FACT) {
 #pragma unroll
       for (int d = 0; d < W; ++d) {
-        row[d] = ax.band[OP_M][i * W + d];
-        row[W + d] = ax.band[OP_S][i * W + d];
+        cp_async_elem(&row[d], &ax.band[OP_M][i * W + d]);
+        cp_async_elem(&row[W + d], &ax.band[OP_S][i * W + d]);
       }
     } else {
       const T* Lt = dch ? ax.luL[1] : ax.luL[0];
@@ -247,28 +249,31 @@ __global__ void __launch_bounds__(64) line_kernel(const LineJobs<T> jobs, const 
       const T* Ut = dch ? ax.luU[1] : ax.luU[0];
 #pragma unroll
       for (int q = 0; q < P; ++q) {
-        row[q] = Lt[i * P + q];
-        row[P + 1 + q] = Ut[i * P + q];
+        cp_async_elem(&row[q], &Lt[i * P + q]);
+        cp_async_elem(&row[P + 1 + q], &Ut[i * P + q]);
       }
-      row[P] = It[i];
+      cp_async_elem(&row[P], &It[i]);
       if (MODE == LM_DERIV) {
 #pragma unroll
-        for (int d = 0; d < W; ++d) row[3 * P + 1 + d] = ax.band[OP_A][i * W + d];
+        for (int d = 0; d < W; ++d) cp_async_elem(&row[3 * P + 1 + d], &ax.band[OP_A][i * W + d]);
       }
     }
   }
 
-  // ---- stage the tile (and c for STIFF)
+  // ---- stage the tile: src (not PIVOT), c (FACT), inverse pivots (STIFF)
+  const T* in0 = MODE == LM_PIVOT ? nullptr : job.src;
+  const T* in1 = FACT ? job.aux : nullptr;
+  const T* in2 = MODE == LM_STIFF ? job.aux2 : nullptr;
+  T* s2 = su + plane;  // STIFF: staging plane of the inverse pivots
   long long off = 0, stride = 1;  // first element and stride of this thread's line (columns)
   if (XDIR) {
-    const T* base = src + (long long)L0 * lp.pitch;
-    const T* cb = MODE == LM_STIFF ? cvec + (long long)L0 * lp.pitch : nullptr;
+    const long long b0 = (long long)L0 * lp.pitch;
     for (int line = 0; line < cnt; ++line) {
-      const T* g = base + (long long)line * lp.pitch;
-      const T* gc = MODE == LM_STIFF ? cb + (long long)line * lp.pitch : nullptr;
+      const long long g = b0 + (long long)line * lp.pitch;
       for (int k = t; k < N; k += LINES) {
-        cp_async_elem(&sr[k * LP + line], g + k);
-        if (MODE == LM_STIFF) cp_async_elem(&su[k * LP + line], gc + k);
+        if (MODE != LM_PIVOT) cp_async_elem(&sr[k * LP + line], in0 + g + k);
+        if (FACT) cp_async_elem(&su[k * LP + line], in1 + g + k);
+        if (MODE == LM_STIFF) cp_async_elem(&s2[k * LP + line], in2 + g + k);
       }
     }
   } else if (t < cnt) {
@@ -280,18 +285,13 @@ __global__ void __launch_bounds__(64) line_kernel(const LineJobs<T> jobs, const 
       off = (long long)(L / lp.Nx) * lp.pitch + (L % lp.Nx);
       stride = (long long)lp.pitch * lp.Ny;
     }
-    const T* g = src + off;
-    const T* gc = MODE == LM_STIFF ? cvec + off : nullptr;
-    T* s = sr + t;
-    T* sc = su + t;
+    long long g = off;
 #pragma unroll 8
     for (int k = 0; k < N; ++k) {
-      cp_async_elem(s, g);
-      if (MODE == LM_STIFF) cp_async_elem(sc, gc);
-      s += LP;
-      sc += LP;
+      if (MODE != LM_PIVOT) cp_async_elem(&sr[k * LP + t], in0 + g);
+      if (FACT) cp_async_elem(&su[k * LP + t], in1 + g);
+      if (MODE == LM_STIFF) cp_async_elem(&s2[k * LP + t], in2 + g);
       g += stride;
-      if (MODE == LM_STIFF) gc += stride;
     }
   }
   cp_async_wait_all();
@@ -300,8 +300,7 @@ __global__ void __launch_bounds__(64) line_kernel(const LineJobs<T> jobs, const 
   if (t < cnt) {
     const int lo = dch ? 1 : 0, hi = dch ? N - 2 : N - 1;
     T* col = sr + t;
-    if (MODE == LM_STIFF) {
-      const int plane = N * LP;
+    if (FACT) {
       T Uq[P][P + 1], invq[P], yq[P];
 #pragma unroll
       for (int m = 0; m < P; ++m) {
@@ -310,9 +309,8 @@ __global__ void __launch_bounds__(64) line_kernel(const LineJobs<T> jobs, const 
 #pragma unroll
         for (int e = 0; e <= P; ++e) Uq[m][e] = T(0);
       }
-      // one row of the on-the-fly Doolittle LU of M + c S and the forward step
-      auto row = [&](int k, bool inner) {
-        const T ck = su[k * LP + t];
+      // one row of the Doolittle LU of M + c S (and, for STIFF, the forward step)
+      auto row = [&](int k, bool inner, T ck, T rk, T ik) {
         const T* tb = tab + k * TABW;
         T a[W];
 #pragma unroll
@@ -343,46 +341,88 @@ __global__ void __launch_bounds__(64) line_kernel(const LineJobs<T> jobs, const 
             if (e + m <= P) s -= l[m] * Uq[m - 1][e + m];
           Un[e] = s;
         }
-        const T inv = fast_rcp(Un[0]);
-        T y = col[k * LP];
+        T inv;
+        if (MODE == LM_PIVOT) {
+          inv = fast_rcp(Un[0]);
+          col[k * LP] = inv;
+        } else {
+          inv = ik;
+          T y = rk;
 #pragma unroll
-        for (int m = 1; m <= P; ++m) y -= l[m] * yq[m - 1];
-        col[k * LP] = y * inv;
+          for (int m = 1; m <= P; ++m) y -= l[m] * yq[m - 1];
+          col[k * LP] = y * inv;
 #pragma unroll
-        for (int e = 1; e <= P; ++e) su[(e - 1) * plane + k * LP + t] = Un[e] * inv;
+          for (int e = 1; e <= P; ++e) su[(e - 1) * plane + k * LP + t] = Un[e] * inv;
+#pragma unroll
+          for (int m = P - 1; m >= 1; --m) yq[m] = yq[m - 1];
+          yq[0] = y;
+        }
 #pragma unroll
         for (int m = P - 1; m >= 1; --m) {
           invq[m] = invq[m - 1];
-          yq[m] = yq[m - 1];
 #pragma unroll
           for (int e = 0; e <= P; ++e) Uq[m][e] = Uq[m - 1][e];
         }
         invq[0] = inv;
-        yq[0] = y;
 #pragma unroll
         for (int e = 0; e <= P; ++e) Uq[0][e] = Un[e];
       };
       // rows whose band lies inside the solved range and in the interior stencil
       const int kin0 = max(lo + P, ax.inner_lo), kin1 = min(hi - P, ax.inner_hi);
+      auto row1 = [&](int k, bool inner) {
+        row(k, inner, su[k * LP + t], MODE == LM_STIFF ? col[k * LP] : T(0),
+            MODE == LM_STIFF ? s2[k * LP + t] : T(0));
+      };
       int k = lo;
-      for (; k < kin0 && k <= hi; ++k) row(k, false);
-#pragma unroll 4
-      for (; k <= kin1; ++k) row(k, true);
-      for (; k <= hi; ++k) row(k, false);
-      T xq[P];
+      for (; k < kin0 && k <= hi; ++k) row1(k, false);
+      // interior rows in blocks of 4: all loads of a block precede its stores
+      for (; k + 3 <= kin1; k += 4) {
+        T cc[4], rr[4], ii[4];
 #pragma unroll
-      for (int m = 0; m < P; ++m) xq[m] = T(0);
-#pragma unroll 4
-      for (k = hi; k >= lo; --k) {
-        T x = col[k * LP];
+        for (int u = 0; u < 4; ++u) {
+          cc[u] = su[(k + u) * LP + t];
+          rr[u] = MODE == LM_STIFF ? col[(k + u) * LP] : T(0);
+          ii[u] = MODE == LM_STIFF ? s2[(k + u) * LP + t] : T(0);
+        }
 #pragma unroll
-        for (int e = 1; e <= P; ++e) x -= su[(e - 1) * plane + k * LP + t] * xq[e - 1];
-        col[k * LP] = x;
+        for (int u = 0; u < 4; ++u) row(k + u, true, cc[u], rr[u], ii[u]);
+      }
+      for (; k <= kin1; ++k) row1(k, true);
+      for (; k <= hi; ++k) row1(k, false);
+      if (MODE == LM_STIFF) {
+        T xq[P];
 #pragma unroll
-        for (int m = P - 1; m >= 1; --m) xq[m] = xq[m - 1];
-        xq[0] = x;
+        for (int m = 0; m < P; ++m) xq[m] = T(0);
+        auto back = [&](int k, T yk, const T* uk) {
+          T x = yk;
+#pragma unroll
+          for (int e = 1; e <= P; ++e) x -= uk[e - 1] * xq[e - 1];
+          col[k * LP] = x;
+#pragma unroll
+          for (int m = P - 1; m >= 1; --m) xq[m] = xq[m - 1];
+          xq[0] = x;
+        };
+        k = hi;
+        for (; k - 7 >= lo; k -= 8) {
+          T yy[8], uu[8][P];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            yy[u] = col[(k - u) * LP];
+#pragma unroll
+            for (int e = 1; e <= P; ++e) uu[u][e - 1] = su[(e - 1) * plane + (k - u) * LP + t];
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) back(k - u, yy[u], uu[u]);
+        }
+        for (; k >= lo; --k) {
+          T uk[P];
+#pragma unroll
+          for (int e = 1; e <= P; ++e) uk[e - 1] = su[(e - 1) * plane + k * LP + t];
+          back(k, col[k * LP], uk);
+        }
       }
     } else {
+      const int f = dch ? 1 : 0;
       // LM_DERIV: the right-hand side of row k is (A u)_k; a register window
       // keeps u[k-P .. k+P] because col[k] is overwritten by the elimination.
       T win[W];
@@ -396,44 +436,78 @@ __global__ void __launch_bounds__(64) line_kernel(const LineJobs<T> jobs, const 
       T yq[P];
 #pragma unroll
       for (int m = 0; m < P; ++m) yq[m] = T(0);
-      int k;
-#pragma unroll 4
-      for (k = lo; k <= hi; ++k) {
+      // forward row k; CONST: factors (and A) are the mid-line constants
+      // rk: r[k] (MASS) or u[k + P + 1] (DERIV), loaded by the caller
+      auto fwd = [&](int k, bool cst, T rk) {
         const T* tb = tab + k * TABW;
         T y;
         if (MODE == LM_DERIV) {
-          const int j = k + P + 1;
-          const T nxt = j < N ? col[j * LP] : T(0);
+          const T nxt = rk;
           y = T(0);
 #pragma unroll
-          for (int d = 0; d < W; ++d) y += tb[3 * P + 1 + d] * win[d];
+          for (int d = 0; d < W; ++d) y += (cst ? ax.inner[OP_A][d] : tb[3 * P + 1 + d]) * win[d];
 #pragma unroll
           for (int d = 0; d < W - 1; ++d) win[d] = win[d + 1];
           win[W - 1] = nxt;
         } else {
-          y = col[k * LP];
+          y = rk;
         }
 #pragma unroll
-        for (int m = 1; m <= P; ++m) y -= tb[m - 1] * yq[m - 1];
+        for (int m = 1; m <= P; ++m) y -= (cst ? ax.luc[f][m - 1] : tb[m - 1]) * yq[m - 1];
         col[k * LP] = y;
 #pragma unroll
         for (int m = P - 1; m >= 1; --m) yq[m] = yq[m - 1];
         yq[0] = y;
+      };
+      int c0 = max(lo, ax.lu_lo[f]), c1 = min(hi, ax.lu_hi[f]);
+      if (MODE == LM_DERIV) {
+        c0 = max(c0, ax.inner_lo);
+        c1 = min(c1, ax.inner_hi);
       }
+      auto ld = [&](int k) -> T {
+        if (MODE == LM_DERIV) {
+          const int j = k + P + 1;
+          return j < N ? col[j * LP] : T(0);
+        }
+        return col[k * LP];
+      };
+      int k = lo;
+      for (; k < c0 && k <= hi; ++k) fwd(k, false, ld(k));
+      // constant rows in blocks of 8: all loads of a block precede its stores
+      for (; k + 7 <= c1; k += 8) {
+        T rr[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) rr[u] = ld(k + u);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) fwd(k + u, true, rr[u]);
+      }
+      for (; k <= c1; ++k) fwd(k, true, ld(k));
+      for (; k <= hi; ++k) fwd(k, false, ld(k));
       T xq[P];
 #pragma unroll
       for (int m = 0; m < P; ++m) xq[m] = T(0);
-#pragma unroll 4
-      for (k = hi; k >= lo; --k) {
+      auto bwd = [&](int k, bool cst, T yk) {
         const T* tb = tab + k * TABW;
-        T x = tb[P] * col[k * LP];
+        T x = (cst ? ax.luc[f][P] : tb[P]) * yk;
 #pragma unroll
-        for (int e = 1; e <= P; ++e) x -= tb[P + e] * xq[e - 1];
+        for (int e = 1; e <= P; ++e) x -= (cst ? ax.luc[f][P + e] : tb[P + e]) * xq[e - 1];
         col[k * LP] = x;
 #pragma unroll
         for (int m = P - 1; m >= 1; --m) xq[m] = xq[m - 1];
         xq[0] = x;
+      };
+      const int b0 = max(lo, ax.lu_lo[f]), b1 = min(hi, ax.lu_hi[f]);
+      k = hi;
+      for (; k > b1; --k) bwd(k, false, col[k * LP]);
+      for (; k - 7 >= b0; k -= 8) {
+        T yy[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) yy[u] = col[(k - u) * LP];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) bwd(k - u, true, yy[u]);
       }
+      for (; k >= b0; --k) bwd(k, true, col[k * LP]);
+      for (; k >= lo; --k) bwd(k, false, col[k * LP]);
     }
     for (int k = 0; k < lo; ++k) col[k * LP] = T(0);
     for (int k = hi + 1; k < N; ++k) col[k * LP] = T(0);
@@ -441,10 +515,43 @@ __global__ void __launch_bounds__(64) line_kernel(const LineJobs<T> jobs, const 
   __syncthreads();
 
   // ---- write back (LM_DERIV: dst += scale * x, done by the L2)
+  const T scale = job.scale;
+  T* dst = job.dst;
   if (XDIR) {
-    T* base = dst + (long long)L0 * lp.pitch;
-    for (int line = 0; line < cnt; ++line) {
-      T* g = base + (long long)line * lp.pitch;
+    const long long b0 = (long long)L0 * lp.pitch;
+    int line = 0;
+    for (; line + 3 < cnt; line += 4) {  // four lines per batch: loads before stores
+      T v[4][5];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+          const int k = t + q * LINES;
+          v[u][q] = k < N ? sr[k * LP + line + u] : T(0);
+        }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        T* g = dst + b0 + (long long)(line + u) * lp.pitch;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+          const int k = t + q * LINES;
+          if (k < N) {
+            if (MODE == LM_DERIV) red_add(g + k, scale * v[u][q]);
+            else g[k] = v[u][q];
+          }
+        }
+      }
+      for (int k = t + 5 * LINES; k < N; k += LINES)  // lines longer than 5 * LINES
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          T* g = dst + b0 + (long long)(line + u) * lp.pitch;
+          const T vv = sr[k * LP + line + u];
+          if (MODE == LM_DERIV) red_add(g + k, scale * vv);
+          else g[k] = vv;
+        }
+    }
+    for (; line < cnt; ++line) {
+      T* g = dst + b0 + (long long)line * lp.pitch;
       for (int k = t; k < N; k += LINES) {
         const T v = sr[k * LP + line];
         if (MODE == LM_DERIV) red_add(g + k, scale * v);
@@ -454,8 +561,20 @@ __global__ void __launch_bounds__(64) line_kernel(const LineJobs<T> jobs, const 
   } else if (t < cnt) {
     T* g = dst + off;
     const T* s = sr + t;
-#pragma unroll 8
-    for (int k = 0; k < N; ++k) {
+    int k = 0;
+    for (; k + 7 < N; k += 8) {  // eight shared loads, then eight global stores
+      T v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = s[u * LP];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (MODE == LM_DERIV) red_add(g + u * stride, scale * v[u]);
+        else g[u * stride] = v[u];
+      }
+      g += 8 * stride;
+      s += 8 * LP;
+    }
+    for (; k < N; ++k) {
       if (MODE == LM_DERIV) red_add(g, scale * *s);
       else *g = *s;
       g += stride;
@@ -930,6 +1049,12 @@ AxisDev<T> axis_dev(const Ctx& c, int d) {
     for (int o = 0; o < 4; ++o)
       for (int q = 0; q < W; ++q) a.inner[o][q] = T((*src[o])[(size_t)a.inner_lo * W + q]);
   }
+  for (int f = 0; f < 2; ++f) {
+    const LuConst& lc = c.luconst[d][f];
+    a.lu_lo[f] = lc.lo;
+    a.lu_hi[f] = lc.hi;
+    for (int q = 0; q < 3 * kMaxP + 1; ++q) a.luc[f][q] = T(q < 3 * p + 1 ? lc.v[q] : 0.0);
+  }
   return a;
 }
 
@@ -947,6 +1072,34 @@ cudaError_t upload_tables_t(Ctx& c) {
       BandLU lu;
       int N = ax.N;
       band_lu(ax.M, nullptr, N, p, f ? 1 : 0, f ? N - 2 : N - 1, lu);
+      // rows whose factors round to the mid-line factors in T
+      {
+        auto vals = [&](int r, double* v) {
+          for (int q = 0; q < p; ++q) {
+            v[q] = lu.L[(size_t)r * p + q];
+            v[p + 1 + q] = lu.U[(size_t)r * p + q];
+          }
+          v[p] = lu.inv_d[r];
+        };
+        auto same = [&](int r, const double* ref) {
+          double v[3 * kMaxP + 1];
+          vals(r, v);
+          for (int q = 0; q < 3 * p + 1; ++q)
+            if (T(v[q]) != T(ref[q])) return false;
+          return true;
+        };
+        LuConst& lc = c.luconst[d][f];
+        const int mid = N / 2;
+        vals(mid, lc.v);
+        lc.lo = mid;
+        while (lc.lo - 1 >= (f ? 1 : 0) && same(lc.lo - 1, lc.v)) --lc.lo;
+        lc.hi = mid;
+        while (lc.hi + 1 <= (f ? N - 2 : N - 1) && same(lc.hi + 1, lc.v)) ++lc.hi;
+        if (N < 8) {
+          lc.lo = 1;
+          lc.hi = 0;
+        }
+      }
       for (int k = 0; k < N; ++k) {
         h[L.lu[d][f][1] + k] = T(lu.inv_d[k]);
         for (int q = 0; q < p; ++q) {
@@ -1133,8 +1286,10 @@ cudaError_t launch_line(Ctx& c, int dir, int mode, const LineJobs<T>& jobs, int 
   lp.pitch = c.pitch;
   lp.nlines = (long long)c.N[0] * c.N[1] * c.N[2] / c.N[dir];
   const int W = 2 * P + 1;
-  const int tabw = mode == LM_STIFF ? 2 * W : (mode == LM_DERIV ? 3 * P + 1 + W : 3 * P + 1);
-  const int planes = mode == LM_STIFF ? 1 + P : 1;
+  const bool fact = mode == LM_STIFF || mode == LM_PIVOT;
+  const int tabw = fact ? 2 * W : (mode == LM_DERIV ? 3 * P + 1 + W : 3 * P + 1);
+  // shared planes: rhs/result, then c, pivots and the P upper-factor planes
+  const int planes = mode == LM_STIFF ? 1 + (P > 2 ? P : 2) : (mode == LM_PIVOT ? 2 : 1);
   const size_t limit = (size_t)c.smem_optin;
   auto smem_for = [&](int lines) {
     const int lp_ = dir == 0 ? lines + 1 : lines;
@@ -1146,7 +1301,7 @@ cudaError_t launch_line(Ctx& c, int dir, int mode, const LineJobs<T>& jobs, int 
   if (smem_for(lines) > limit) return cudaErrorInvalidValue;
   size_t smem = smem_for(lines);
   long long blocks = (lp.nlines + lines - 1) / lines;
-  double per_job = (double)c.Nc * sizeof(T) * (mode == LM_MASS ? 2.0 : 3.0);
+  double per_job = (double)c.Nc * sizeof(T) * (mode == LM_MASS || mode == LM_PIVOT ? 2.0 : (mode == LM_STIFF ? 4.0 : 3.0));
   prof_begin(c, name, per_job * njobs);
   dim3 grid((unsigned)blocks, njobs);
   const AxisDev<T> ax = axis_dev<T>(c, dir);
@@ -1154,6 +1309,9 @@ cudaError_t launch_line(Ctx& c, int dir, int mode, const LineJobs<T>& jobs, int 
   if (mode == LM_STIFF) {
     if (x) line_kernel<T, P, LM_STIFF, true><<<grid, lines, smem, c.stream>>>(jobs, lp, ax);
     else line_kernel<T, P, LM_STIFF, false><<<grid, lines, smem, c.stream>>>(jobs, lp, ax);
+  } else if (mode == LM_PIVOT) {
+    if (x) line_kernel<T, P, LM_PIVOT, true><<<grid, lines, smem, c.stream>>>(jobs, lp, ax);
+    else line_kernel<T, P, LM_PIVOT, false><<<grid, lines, smem, c.stream>>>(jobs, lp, ax);
   } else if (mode == LM_DERIV) {
     if (x) line_kernel<T, P, LM_DERIV, true><<<grid, lines, smem, c.stream>>>(jobs, lp, ax);
     else line_kernel<T, P, LM_DERIV, false><<<grid, lines, smem, c.stream>>>(jobs, lp, ax);
@@ -1166,11 +1324,12 @@ cudaError_t launch_line(Ctx& c, int dir, int mode, const LineJobs<T>& jobs, int 
 }
 
 template <typename T>
-LineJob<T> job_of(const T* src, T* dst, const T* aux, double scale, int dirichlet) {
+LineJob<T> job_of(const T* src, T* dst, const T* aux, double scale, int dirichlet, const T* aux2 = nullptr) {
   LineJob<T> j;
   j.src = src;
   j.dst = dst;
   j.aux = aux;
+  j.aux2 = aux2;
   j.scale = T(scale);
   j.dirichlet = dirichlet;
   return j;
@@ -1228,7 +1387,7 @@ cudaError_t e_substep(Ctx& c, int half) {
   for (int i = 0; i < 3; ++i) {
     int sd = stiff_dir[half - 1][i];
     LineJobs<T> js{};
-    js.job[0] = job_of<T>(R[i], R[i], cf[2], 0.0, 1);
+    js.job[0] = job_of<T>(R[i], R[i], cf[2], 0.0, 1, reinterpret_cast<const T*>(c.pivots[sd]));
     e = launch_line<T, P>(c, sd, LM_STIFF, js, 1, stiff_name[sd]);
     if (e != cudaSuccess) return e;
     int md[2], m = 0;
@@ -1328,6 +1487,26 @@ cudaError_t h_substep(Ctx& c, int half) {
   return c.mu_uniform ? h_substep_uniform<T, P>(c, half) : h_substep_general<T, P>(c, half);
 }
 
+// Inverse pivots of the row-scaled M + c S along each axis (Dirichlet-reduced,
+// as every stiffness solve of the E half steps); they depend only on c, i.e.
+// on the material and tau, so they are computed once by adi_factor.
+template <typename T, int P>
+cudaError_t pivots_tp(Ctx& c) {
+  T** cf = reinterpret_cast<T**>(c.coef);
+  static const char* name[3] = {"pivots_x", "pivots_y", "pivots_z"};
+  for (int d = 0; d < 3; ++d) {
+    if (!c.pivots[d]) {
+      cudaError_t e = cudaMalloc(&c.pivots[d], c.Np * sizeof(T));
+      if (e != cudaSuccess) return e;
+    }
+    LineJobs<T> js{};
+    js.job[0] = job_of<T>(nullptr, reinterpret_cast<T*>(c.pivots[d]), cf[2], 0.0, 1);
+    cudaError_t e = launch_line<T, P>(c, d, LM_PIVOT, js, 1, name[d]);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaStreamSynchronize(c.stream);
+}
+
 template <typename T, int P>
 cudaError_t substep_tp(Ctx& c, int which) {
   switch (which) {
@@ -1365,6 +1544,8 @@ cudaError_t prepare_tp(int optin) {
   if (e == cudaSuccess) e = opt_in(line_kernel<T, P, LM_MASS, true>, optin);
   if (e == cudaSuccess) e = opt_in(line_kernel<T, P, LM_STIFF, true>, optin);
   if (e == cudaSuccess) e = opt_in(line_kernel<T, P, LM_DERIV, true>, optin);
+  if (e == cudaSuccess) e = opt_in(line_kernel<T, P, LM_PIVOT, true>, optin);
+  if (e == cudaSuccess) e = opt_in(line_kernel<T, P, LM_PIVOT, false>, optin);
   if (e == cudaSuccess) e = opt_in(line_kernel<T, P, LM_MASS, false>, optin);
   if (e == cudaSuccess) e = opt_in(line_kernel<T, P, LM_STIFF, false>, optin);
   if (e == cudaSuccess) e = opt_in(line_kernel<T, P, LM_DERIV, false>, optin);
@@ -1389,6 +1570,15 @@ unsigned grid_for(long long n, int threads) {
 
 }  // namespace
 
+template <typename T>
+cudaError_t pivots_t(Ctx& c) {
+  switch (c.p) {
+    case 1: return pivots_tp<T, 1>(c);
+    case 2: return pivots_tp<T, 2>(c);
+    default: return pivots_tp<T, 3>(c);
+  }
+}
+
 cudaError_t upload_tables(Ctx& c) {
   int optin = 0;
   cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c.device);
@@ -1396,7 +1586,9 @@ cudaError_t upload_tables(Ctx& c) {
   c.smem_optin = optin;
   e = c.precision == ADI_PREC_FP64 ? prepare_t<double>(c.p, optin) : prepare_t<float>(c.p, optin);
   if (e != cudaSuccess) return e;
-  return c.precision == ADI_PREC_FP64 ? upload_tables_t<double>(c) : upload_tables_t<float>(c);
+  e = c.precision == ADI_PREC_FP64 ? upload_tables_t<double>(c) : upload_tables_t<float>(c);
+  if (e != cudaSuccess) return e;
+  return c.precision == ADI_PREC_FP64 ? pivots_t<double>(c) : pivots_t<float>(c);
 }
 
 cudaError_t run_substep(Ctx& c, int which) {
