@@ -640,7 +640,8 @@ struct Smem {
   static constexpr int HX = TX + 2 * P, HY = TY + 2 * P, HZ = TZ + 2 * P;
   static constexpr int BX = 40;       // tile row: x0-4 .. x0+35 (TMA box)
   static constexpr int XOFF = 4 - P;  // position of x0-P inside a tile row
-  static constexpr int TILE = HZ * HY * BX, ZR = TZ * HY * HX, YR = TZ * TY * HX;
+  static constexpr int HXP = HX + 1;  // odd row pitch of the y-pass results (bank-conflict free x pass)
+  static constexpr int TILE = HZ * HY * BX, ZR = TZ * HY * HX, YR = TZ * TY * HXP;
   // dynamic shared memory: 128 bytes of alignment slack, the tiles (TMA
   // destinations, 128-byte aligned), the pass buffers, then two mbarriers
   static constexpr size_t DATA2 = sizeof(T) * (2 * (size_t)TILE + 2 * (size_t)ZR + 2 * (size_t)YR);
@@ -669,20 +670,25 @@ __device__ __forceinline__ void zpass(const RhsParams<T>& prm, const T* tl, T* z
 
 // y pass: column (zz, xx), 8 outputs from a window of HY values
 template <typename T, int P, int OP, bool INNER>
-__device__ __forceinline__ void ypass(const RhsParams<T>& prm, const T* zr, T* yr, int y0, int zz, int xx) {
+__device__ __forceinline__ void yapply(const RhsParams<T>& prm, const T (&w)[Smem<T, P>::HY], T* yr, int y0, int zz,
+                                       int xx) {
   using S = Smem<T, P>;
   constexpr int W = 2 * P + 1;
-  T w[S::HY];
-  const T* src = zr + zz * S::HY * S::HX + xx;
-#pragma unroll
-  for (int k = 0; k < S::HY; ++k) w[k] = src[k * S::HX];
 #pragma unroll
   for (int yy = 0; yy < TY; ++yy) {
     T s = T(0);
 #pragma unroll
     for (int q = 0; q < W; ++q) s += bandv<T, P, 1, OP, INNER>(prm, y0 + yy, q) * w[yy + q];
-    yr[(zz * TY + yy) * S::HX + xx] = s;
+    yr[(zz * TY + yy) * S::HXP + xx] = s;
   }
+}
+
+template <typename T, int P>
+__device__ __forceinline__ void yload(const T* zr, int zz, int xx, T (&w)[Smem<T, P>::HY]) {
+  using S = Smem<T, P>;
+  const T* src = zr + zz * S::HY * S::HX + xx;
+#pragma unroll
+  for (int k = 0; k < S::HY; ++k) w[k] = src[k * S::HX];
 }
 
 // x pass for two consecutive x outputs in four rows; adds coef * sign * value
@@ -698,7 +704,7 @@ __device__ __forceinline__ void xpass(const RhsParams<T>& prm, const T* yr, int 
     for (int q = 0; q < W; ++q) bx[j][q] = bandv<T, P, 0, OP, INNER>(prm, min(gx + j, prm.Nx - 1), q);
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
-    const T* src = yr + (rg * 4 + r) * S::HX + xp;
+    const T* src = yr + (r * 16 + rg) * S::HXP + xp;  // half-warps read adjacent rows
     T w[W + 1];
 #pragma unroll
     for (int q = 0; q < W + 1; ++q) w[q] = src[q];
@@ -778,13 +784,13 @@ __device__ __forceinline__ bool do_field(const RhsParams<T>& prm, const TmaMaps&
   __syncthreads();
   for (int i = tid; i < TZ * S::HX; i += NT) {
     const int zz = i / S::HX, xx = i % S::HX;
-    if (inY) {
-      ypass<T, P, PL::y0, true>(prm, s_zr, s_yr, y0, zz, xx);
-      ypass<T, P, PL::y1, true>(prm, s_zr + (zshare ? 0 : S::ZR), s_yr + S::YR, y0, zz, xx);
-    } else {
-      ypass<T, P, PL::y0, false>(prm, s_zr, s_yr, y0, zz, xx);
-      ypass<T, P, PL::y1, false>(prm, s_zr + (zshare ? 0 : S::ZR), s_yr + S::YR, y0, zz, xx);
-    }
+    T w[S::HY];
+    yload<T, P>(s_zr, zz, xx, w);
+    if (inY) yapply<T, P, PL::y0, true>(prm, w, s_yr, y0, zz, xx);
+    else yapply<T, P, PL::y0, false>(prm, w, s_yr, y0, zz, xx);
+    if (!zshare) yload<T, P>(s_zr + S::ZR, zz, xx, w);
+    if (inY) yapply<T, P, PL::y1, true>(prm, w, s_yr + S::YR, y0, zz, xx);
+    else yapply<T, P, PL::y1, false>(prm, w, s_yr + S::YR, y0, zz, xx);
   }
   __syncthreads();
   const int gx = x0 + xp;  // band rows are clamped per output inside xpass
@@ -821,13 +827,13 @@ __global__ void __launch_bounds__(rhs2::NT, sizeof(T) == 4 ? 2 : 1)
   // tile-level interior tests (band rows of all outputs of the tile)
   const bool inZ = z0 >= prm.st[2].lo && z0 + TZ - 1 <= prm.st[2].hi;
   const bool inY = y0 >= prm.st[1].lo && y0 + TY - 1 <= prm.st[1].hi;
-  // x pass: two consecutive x (xp) in four consecutive (z',y) rows
+  // x pass: two consecutive x (xp) in the four (z',y) rows rg, rg+16, rg+32, rg+48
   const int xp = (tid % 16) * 2, rg = tid / 16;
   const bool inX = x0 + xp >= prm.st[0].lo && x0 + xp + 1 <= prm.st[0].hi;
   T cf[3][4][2], acc[3][4][2];
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
-    const int row = rg * 4 + r, zz = row / TY, yy = row % TY;
+    const int row = r * 16 + rg, zz = row / TY, yy = row % TY;
     const int gz = z0 + zz, gy = y0 + yy;
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
@@ -873,7 +879,7 @@ __global__ void __launch_bounds__(rhs2::NT, sizeof(T) == 4 ? 2 : 1)
   for (int c = 0; c < 3; ++c) {
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-      const int row = rg * 4 + r, zz = row / TY, yy = row % TY;
+      const int row = r * 16 + rg, zz = row / TY, yy = row % TY;
       const int gz = z0 + zz, gy = y0 + yy;
       if (gz >= Nz || gy >= Ny) continue;
 #pragma unroll
