@@ -595,7 +595,18 @@ __global__ void __launch_bounds__(64) line_kernel(const LineJobs<T> jobs, const 
 // table, so interior stencils are constant operands.  Rows near the boundary
 // (outside 2p .. N-1-2p) read their band rows from the tables instead.
 namespace rhs2 {
-constexpr int TX = 32, TY = 8, TZ = 8, NT = 256;
+#ifndef ADI_RHS_NT
+#define ADI_RHS_NT 256
+#endif
+#ifndef ADI_RHS_NBUF
+#define ADI_RHS_NBUF 2
+#endif
+#ifndef ADI_RHS_MINB
+#define ADI_RHS_MINB 2
+#endif
+constexpr int TX = 32, TY = 8, TZ = 8, NT = ADI_RHS_NT;  // compile-time tile and launch shape
+constexpr int RG = NT / 16;                // x-pass row groups: 16 threads x 2 outputs cover a row of 32
+constexpr int RPT = TZ * TY / RG;          // (z', y) rows per thread in the x pass
 
 // the two terms of field F in half step H: ops per axis, output, coefficient, sign
 template <int H, int F>
@@ -645,7 +656,7 @@ struct Smem {
   // dynamic shared memory: 128 bytes of alignment slack, the tiles (TMA
   // destinations, 128-byte aligned), the pass buffers, then two mbarriers
   static constexpr size_t DATA2 = sizeof(T) * (2 * (size_t)TILE + 2 * (size_t)ZR + 2 * (size_t)YR);
-  static constexpr int NBUF = DATA2 + 128 + 16 <= 227 * 1024 ? 2 : 1;  // double-buffer the tiles if it fits
+  static constexpr int NBUF = (ADI_RHS_NBUF == 2 && DATA2 + 128 + 16 <= 227 * 1024) ? 2 : 1;  // double-buffer if it fits
   static constexpr size_t DATA = sizeof(T) * (NBUF * (size_t)TILE + 2 * (size_t)ZR + 2 * (size_t)YR);
   static constexpr size_t BYTES = 128 + DATA + 16;
 };
@@ -694,7 +705,7 @@ __device__ __forceinline__ void yload(const T* zr, int zz, int xx, T (&w)[Smem<T
 // x pass for two consecutive x outputs in four rows; adds coef * sign * value
 template <typename T, int P, int OP, bool INNER, int OUT, int CK>
 __device__ __forceinline__ void xpass(const RhsParams<T>& prm, const T* yr, int gx, int xp, int rg, float sg,
-                                      T (&cf)[3][4][2], T (&acc)[3][4][2]) {
+                                      T (&cf)[3][RPT][2], T (&acc)[3][RPT][2]) {
   using S = Smem<T, P>;
   constexpr int W = 2 * P + 1;
   T bx[2][W];
@@ -703,8 +714,8 @@ __device__ __forceinline__ void xpass(const RhsParams<T>& prm, const T* yr, int 
 #pragma unroll
     for (int q = 0; q < W; ++q) bx[j][q] = bandv<T, P, 0, OP, INNER>(prm, min(gx + j, prm.Nx - 1), q);
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const T* src = yr + (r * 16 + rg) * S::HXP + xp;  // half-warps read adjacent rows
+  for (int r = 0; r < RPT; ++r) {
+    const T* src = yr + (r * RG + rg) * S::HXP + xp;  // half-warps read adjacent rows
     T w[W + 1];
 #pragma unroll
     for (int q = 0; q < W + 1; ++q) w[q] = src[q];
@@ -760,8 +771,8 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 template <typename T, int P, int H, int F>
 __device__ __forceinline__ bool do_field(const RhsParams<T>& prm, const TmaMaps& maps, T* s_tile, T* s_zr,
                                          T* s_yr, unsigned long long* bars, int x0, int y0, int z0, bool inZ,
-                                         bool inY, bool inX, int xp, int rg, T (&cf)[3][4][2],
-                                         T (&acc)[3][4][2]) {
+                                         bool inY, bool inX, int xp, int rg, T (&cf)[3][RPT][2],
+                                         T (&acc)[3][RPT][2]) {
   using S = Smem<T, P>;
   using PL = Plan<H, F>;
   const int tid = threadIdx.x;
@@ -809,7 +820,7 @@ __device__ __forceinline__ bool do_field(const RhsParams<T>& prm, const TmaMaps&
 }  // namespace rhs2
 
 template <typename T, int P, int H>
-__global__ void __launch_bounds__(rhs2::NT, sizeof(T) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(rhs2::NT, sizeof(T) == 4 ? ADI_RHS_MINB : 1)
     rhs_e_kernel(const RhsParams<T> prm, const __grid_constant__ TmaMaps maps) {
   using namespace rhs2;
   using S = Smem<T, P>;
@@ -827,13 +838,13 @@ __global__ void __launch_bounds__(rhs2::NT, sizeof(T) == 4 ? 2 : 1)
   // tile-level interior tests (band rows of all outputs of the tile)
   const bool inZ = z0 >= prm.st[2].lo && z0 + TZ - 1 <= prm.st[2].hi;
   const bool inY = y0 >= prm.st[1].lo && y0 + TY - 1 <= prm.st[1].hi;
-  // x pass: two consecutive x (xp) in the four (z',y) rows rg, rg+16, rg+32, rg+48
+  // x pass: two consecutive x (xp) in the (z',y) rows rg, rg + RG, ...
   const int xp = (tid % 16) * 2, rg = tid / 16;
   const bool inX = x0 + xp >= prm.st[0].lo && x0 + xp + 1 <= prm.st[0].hi;
-  T cf[3][4][2], acc[3][4][2];
+  T cf[3][RPT][2], acc[3][RPT][2];
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const int row = r * 16 + rg, zz = row / TY, yy = row % TY;
+  for (int r = 0; r < RPT; ++r) {
+    const int row = r * RG + rg, zz = row / TY, yy = row % TY;
     const int gz = z0 + zz, gy = y0 + yy;
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
@@ -878,8 +889,8 @@ __global__ void __launch_bounds__(rhs2::NT, sizeof(T) == 4 ? 2 : 1)
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int row = r * 16 + rg, zz = row / TY, yy = row % TY;
+    for (int r = 0; r < RPT; ++r) {
+      const int row = r * RG + rg, zz = row / TY, yy = row % TY;
       const int gz = z0 + zz, gy = y0 + yy;
       if (gz >= Nz || gy >= Ny) continue;
 #pragma unroll
