@@ -91,7 +91,9 @@ adi_status adi_factor(adi_handle h);
  * be called again before the next adi_step. */
 adi_status adi_set_dt(adi_handle h, double dt);
 
-/* Use the given cudaStream_t (NULL = legacy default stream) for all later work. */
+/* Use the given cudaStream_t (NULL = legacy default stream) for all later work.
+ * On the legacy default stream adi_step cannot capture a CUDA graph and issues
+ * the kernels one by one. */
 adi_status adi_set_stream(adi_handle h, void* cuda_stream);
 
 /* Copy 6 N_c doubles (host) into the state and set the time to t.  The
@@ -158,6 +160,52 @@ double adi_cfl_dt(adi_handle h);
  * ADI_ECUDA, ADI_ENUMERIC (eps or mu <= 0); message via adi_last_error(NULL). */
 adi_status adi_cfl_dt_noalloc(int nx, int ny, int nz, int p, const double* d_eps, const double* d_mu,
                               void* cuda_stream, double* dt_out);
+
+/* Lines per CTA of the line-solve kernels: 8, 16, 32 or 64, or 0 for the
+ * default (the largest that leaves room for two CTAs per SM).  A width whose
+ * shared memory does not fit falls back to the default.  Used by the
+ * autotuner of the batched mode; results do not depend on it. */
+adi_status adi_set_line_tile(adi_handle h, int lines);
+
+/* ---------------------------------------------------------------- batches
+ * Many independent problems of different sizes, materials, degrees and time
+ * steps stepped together (the paper steps one patch; batching is a library
+ * service).  Each instance is an ordinary handle owned by the batch: set its
+ * fields, source and time step through adi_batch_handle and the calls above.
+ * adi_batch_step advances every instance by n steps: one step of all instances
+ * is captured once as a CUDA graph whose branches are the instances' sub-step
+ * kernels on their own streams (forked from and joined to the batch stream),
+ * so the GPU runs small instances concurrently; the graph is replayed n times.
+ * Results equal those of each instance stepped alone, bit for bit. */
+typedef struct adi_batch_ctx* adi_batch;
+typedef struct {
+  int nx, ny, nz, p; /* as adi_create */
+  double dt;
+  const double* eps; /* per-element material, NULL = 1, 1, 0 */
+  const double* mu;
+  const double* sigma;
+} adi_instance_desc;
+
+/* Create count >= 1 instances (adi_create each, same options).  On failure
+ * nothing is kept and the message is in adi_last_error(NULL). */
+adi_status adi_batch_create(int count, const adi_instance_desc* desc, const adi_options* opt, adi_batch* out);
+/* The handle of instance i (owned by the batch: do not destroy it). */
+adi_status adi_batch_handle(adi_batch b, int i, adi_handle* h);
+/* Run the batch on the given cudaStream_t (not owned; NULL = the batch's own stream). */
+adi_status adi_batch_set_stream(adi_batch b, void* cuda_stream);
+/* adi_factor of every instance. */
+adi_status adi_batch_factor(adi_batch b);
+/* Advance every instance by n >= 1 steps (asynchronous on the batch stream). */
+adi_status adi_batch_step(adi_batch b, int n);
+/* Block until the batch stream is idle; ADI_ETIMEOUT if a bounded device wait gave up. */
+adi_status adi_batch_sync(adi_batch b);
+/* Pick the line-tile width of every instance by timed trials (8..64 lines,
+ * three steps each, on the instance alone) unless cache_path (may be NULL)
+ * already holds a choice for its (p, N_x, N_y, N_z, precision); new choices
+ * are appended to cache_path.  The fields are restored afterwards. */
+adi_status adi_batch_autotune(adi_batch b, const char* cache_path);
+/* Release the batch and all its instances.  NULL is ignored. */
+void adi_batch_destroy(adi_batch b);
 
 /* Block until all work on the handle's stream is done. */
 adi_status adi_sync(adi_handle h);

@@ -19,11 +19,19 @@ PREC_FP64, PREC_FP32 = 0, 1
 EXPORTS = ("adi_create", "adi_factor", "adi_set_dt", "adi_set_stream", "adi_set_fields",
            "adi_set_source", "adi_step", "adi_substep", "adi_fields", "adi_fields_device",
            "adi_cfl_dt", "adi_cfl_dt_noalloc", "adi_sync", "adi_set_profiling", "adi_kernel_stats", "adi_dims",
-           "adi_destroy", "adi_last_error", "adi_status_string")
+           "adi_destroy", "adi_last_error", "adi_status_string", "adi_set_line_tile",
+           "adi_batch_create", "adi_batch_set_stream", "adi_batch_handle", "adi_batch_factor", "adi_batch_step", "adi_batch_sync",
+           "adi_batch_autotune", "adi_batch_destroy")
 
 
 class AdiOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("use_graph", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+
+
+class AdiInstanceDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("p", ctypes.c_int),
+                ("dt", ctypes.c_double), ("eps", ctypes.POINTER(ctypes.c_double)),
+                ("mu", ctypes.POINTER(ctypes.c_double)), ("sigma", ctypes.POINTER(ctypes.c_double))]
 
 
 class AdiKernelStat(ctypes.Structure):
@@ -66,6 +74,15 @@ def load_library(path=LIB_PATH):
         "adi_destroy": (None, [H]),
         "adi_last_error": (ctypes.c_char_p, [H]),
         "adi_status_string": (ctypes.c_char_p, [I]),
+        "adi_set_line_tile": (I, [H, I]),
+        "adi_batch_create": (I, [I, P(AdiInstanceDesc), P(AdiOptions), P(H)]),
+        "adi_batch_handle": (I, [H, I, P(H)]),
+        "adi_batch_set_stream": (I, [H, ctypes.c_void_p]),
+        "adi_batch_factor": (I, [H]),
+        "adi_batch_step": (I, [H, I]),
+        "adi_batch_sync": (I, [H]),
+        "adi_batch_autotune": (I, [H, ctypes.c_char_p]),
+        "adi_batch_destroy": (None, [H]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -88,9 +105,19 @@ def _dptr(a):
 class Solver:
     """One ADI Maxwell problem on the GPU (owns an adi_handle)."""
 
-    def __init__(self, n, p, dt, eps=None, mu=None, sigma=None, precision="fp32", use_graph=True):
+    def __init__(self, n, p, dt, eps=None, mu=None, sigma=None, precision="fp32", use_graph=True, _handle=None):
         lib = load_library()
         self._lib = lib
+        if _handle is not None:  # an instance owned by a Batch
+            self.n = tuple(int(v) for v in n)
+            self.p = int(p)
+            self.dtype = np.float64 if precision == "fp64" else np.float32
+            self.h = _handle
+            self.shape = (self.n[2] + p, self.n[1] + p, self.n[0] + p)
+            self.dt = float(dt)
+            self._owned = False
+            return
+        self._owned = True
         self.n = tuple(int(v) for v in n)
         self.p = int(p)
         opt = AdiOptions()
@@ -180,10 +207,85 @@ class Solver:
         return [dict(name=buf[i].name.decode(), launches=buf[i].launches, total_ms=buf[i].total_ms,
                      bytes_per_launch=buf[i].bytes_per_launch) for i in range(min(cnt.value, 64))]
 
+    def set_line_tile(self, lines):
+        self._check(self._lib.adi_set_line_tile(self.h, int(lines)))
+
     def close(self):
-        if getattr(self, "h", None):
+        if getattr(self, "h", None) and getattr(self, "_owned", True):
             self._lib.adi_destroy(self.h)
-            self.h = None
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many independent problems stepped together (adi_batch_* of the C-ABI).
+
+    ``instances``: list of dicts with keys n (nx, ny, nz), p, dt and optional
+    eps, mu, sigma (per-element arrays).  ``solvers[i]`` gives access to the
+    single-instance calls (fields, sources) of instance i.
+    """
+
+    def __init__(self, instances, precision="fp32"):
+        lib = load_library()
+        self._lib = lib
+        keep = []
+        descs = (AdiInstanceDesc * len(instances))()
+        for d, inst in zip(descs, instances):
+            d.nx, d.ny, d.nz = (int(v) for v in inst["n"])
+            d.p = int(inst["p"])
+            d.dt = float(inst["dt"])
+            for name in ("eps", "mu", "sigma"):
+                a = inst.get(name)
+                if a is None:
+                    setattr(d, name, None)
+                else:
+                    a = np.ascontiguousarray(a, dtype=np.float64)
+                    keep.append(a)
+                    setattr(d, name, _dptr(a))
+        opt = AdiOptions()
+        opt.precision = PREC_FP64 if precision == "fp64" else PREC_FP32
+        opt.use_graph = 1
+        b = ctypes.c_void_p()
+        st = lib.adi_batch_create(len(instances), descs, ctypes.byref(opt), ctypes.byref(b))
+        if st != ADI_OK:
+            raise AdiError(st, lib.adi_last_error(None).decode())
+        self.b = b
+        self.solvers = []
+        for i, inst in enumerate(instances):
+            h = ctypes.c_void_p()
+            self._check(lib.adi_batch_handle(b, i, ctypes.byref(h)))
+            self.solvers.append(Solver(inst["n"], inst["p"], inst["dt"], precision=precision, _handle=h))
+
+    def _check(self, st):
+        if st != ADI_OK:
+            raise AdiError(st, self._lib.adi_last_error(None).decode())
+
+    def factor(self):
+        self._check(self._lib.adi_batch_factor(self.b))
+
+    def set_stream(self, stream_ptr):
+        self._check(self._lib.adi_batch_set_stream(self.b, ctypes.c_void_p(int(stream_ptr))))
+
+    def step(self, n=1):
+        self._check(self._lib.adi_batch_step(self.b, int(n)))
+
+    def sync(self):
+        self._check(self._lib.adi_batch_sync(self.b))
+
+    def autotune(self, cache_path=None):
+        self._check(self._lib.adi_batch_autotune(self.b, cache_path.encode() if cache_path else None))
+
+    def close(self):
+        if getattr(self, "b", None):
+            for s in self.solvers:
+                s.h = None
+            self._lib.adi_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:

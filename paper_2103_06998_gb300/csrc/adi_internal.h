@@ -140,6 +140,7 @@ struct Ctx {
   int p = 2;
   int precision = ADI_PREC_FP32;
   int use_graph = 1;
+  int line_tile = 0;  // lines per line-solve CTA (0: largest that leaves two CTAs per SM)
   double dt = 0.0;
   size_t Nc = 0;      // coefficients per component (N_x N_y N_z)
   int pitch = 0;      // device row pitch in elements: N_x rounded up to a multiple of 4

@@ -1315,6 +1315,7 @@ cudaError_t launch_line(Ctx& c, int dir, int mode, const LineJobs<T>& jobs, int 
   // largest tile (<= 64 lines) that leaves room for two CTAs per SM
   int lines = 64;
   while (lines > 8 && smem_for(lines) > limit / 2) lines /= 2;
+  if (c.line_tile > 0 && smem_for(c.line_tile) <= limit) lines = c.line_tile;  // autotuned width
   if (smem_for(lines) > limit) return cudaErrorInvalidValue;
   size_t smem = smem_for(lines);
   long long blocks = (lp.nlines + lines - 1) / lines;

@@ -30,7 +30,7 @@ _C1 = np.uint64(0xBF58476D1CE4E5B9)
 _C2 = np.uint64(0x94D049BB133111EB)
 
 # streams of the generator
-S_CENTRE, S_AXES, S_EPS, S_SIGMA, S_DIPOLE, S_FIELD = 0, 1, 2, 3, 4, 5
+S_CENTRE, S_AXES, S_EPS, S_SIGMA, S_DIPOLE, S_FIELD, S_SIZE = 0, 1, 2, 3, 4, 5, 6
 
 
 def splitmix64(x):
@@ -108,3 +108,18 @@ def random_material(n, seed, eps_range=(1.0, 50.0), sigma_range=(0.0, 0.7),
     sigma = sigma_range[0] + (sigma_range[1] - sigma_range[0]) * us
     mu = mu_range[0] + (mu_range[1] - mu_range[0]) * um
     return eps, mu, sigma
+
+
+def batch_instances(count=48, seed=2103, n_lo=32, n_hi=128):
+    """Heterogeneous batch: instance i has elements per axis drawn from
+    U{n_lo..n_hi} and p from {2, 3} (seed + i), its own head map and dipole
+    (seed + i).  Returns dicts with n, p, eps, mu, sigma, source."""
+    out = []
+    for i in range(count):
+        s = seed + i
+        u = uniform(s, S_SIZE, np.arange(4))
+        n = tuple(int(n_lo + np.floor(u[k] * (n_hi - n_lo + 1))) for k in range(3))
+        p = 2 if u[3] < 0.5 else 3
+        eps, mu, sigma, _ = head_map(n, s)
+        out.append(dict(n=n, p=p, eps=eps, mu=mu, sigma=sigma, source=dipole(s)))
+    return out
