@@ -23,6 +23,8 @@ propagation in non-regular biological tissues" (arXiv 2103.06998):
                    weak1-weak4, discrete1-discrete4, dupa1ab, Appendix order).
 * ``manufactured`` the manufactured solution u_A and L2 / H(curl) norms
                    ("Numerical code verification with manufactured solution").
+* ``convnet``      the learned coarse-step corrector (not in the paper): 3D
+                   convolution net, MSE, gradients, Adam, input features.
 
 Parity status per function is listed in each module header.  Every function is
 pinned by a ``-m "not gpu"`` test in ``tests/test_oracle_*.py`` except where a

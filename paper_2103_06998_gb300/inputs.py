@@ -123,3 +123,19 @@ def batch_instances(count=48, seed=2103, n_lo=32, n_hi=128):
         eps, mu, sigma, _ = head_map(n, s)
         out.append(dict(n=n, p=p, eps=eps, mu=mu, sigma=sigma, source=dipole(s)))
     return out
+
+
+S_NET = 7
+
+
+def net_init(seed, layers=((9, 32), (32, 32), (32, 32), (32, 6)), last_scale=0.1):
+    """Initial corrector weights: w[dz, dy, dx, ci, co] ~ U(-r, r), r = sqrt(6 / (27 ci))
+    (He-uniform for ReLU), the last layer scaled by ``last_scale``; biases 0.
+    Returns a list of (w, b) FP64 arrays."""
+    out = []
+    for l, (ci, co) in enumerate(layers):
+        size = 27 * ci * co
+        u = uniform(seed, S_NET, np.arange(size, dtype=np.uint64) + np.uint64(l << 24))
+        r = np.sqrt(6.0 / (27 * ci)) * (last_scale if l == len(layers) - 1 else 1.0)
+        out.append((((u * 2.0 - 1.0) * r).reshape(3, 3, 3, ci, co), np.zeros(co)))
+    return out
