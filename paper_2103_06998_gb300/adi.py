@@ -1,4 +1,5 @@
-"""Python binding of the C-ABI in include/adi_maxwell.h (ctypes, marshalling only).
+"""Python binding of the C-ABI in include/adi_maxwell.h and include/adi_corrector.h
+(ctypes, marshalling only).
 
 Every step of the method runs in the CUDA kernels of ``libadi_maxwell.so``;
 this module only converts arguments.  Loading fails loudly when the library is
@@ -21,7 +22,11 @@ EXPORTS = ("adi_create", "adi_factor", "adi_set_dt", "adi_set_stream", "adi_set_
            "adi_cfl_dt", "adi_cfl_dt_noalloc", "adi_sync", "adi_set_profiling", "adi_kernel_stats", "adi_dims",
            "adi_destroy", "adi_last_error", "adi_status_string", "adi_set_line_tile",
            "adi_batch_create", "adi_batch_set_stream", "adi_batch_handle", "adi_batch_factor", "adi_batch_step", "adi_batch_sync",
-           "adi_batch_autotune", "adi_batch_destroy")
+           "adi_batch_autotune", "adi_batch_destroy",
+           "adi_net_create", "adi_net_set_stream", "adi_net_set_params", "adi_net_get_params", "adi_net_features",
+           "adi_net_target", "adi_net_forward", "adi_net_apply", "adi_net_train_step", "adi_net_gradient",
+           "adi_net_loss", "adi_fields_distance", "adi_copy_state", "adi_corrector_run", "adi_net_destroy",
+           "adi_net_last_error")
 
 
 class AdiOptions(ctypes.Structure):
@@ -83,6 +88,22 @@ def load_library(path=LIB_PATH):
         "adi_batch_sync": (I, [H]),
         "adi_batch_autotune": (I, [H, ctypes.c_char_p]),
         "adi_batch_destroy": (None, [H]),
+        "adi_net_create": (I, [I, I, I, P(H)]),
+        "adi_net_set_stream": (I, [H, ctypes.c_void_p]),
+        "adi_net_set_params": (I, [H, P(ctypes.c_float), ctypes.c_size_t]),
+        "adi_net_get_params": (I, [H, P(ctypes.c_float), ctypes.c_size_t]),
+        "adi_net_features": (I, [H, H, ctypes.c_void_p]),
+        "adi_net_target": (I, [H, H, H, ctypes.c_void_p]),
+        "adi_net_forward": (I, [H, ctypes.c_void_p, ctypes.c_void_p]),
+        "adi_net_apply": (I, [H, H, ctypes.c_void_p]),
+        "adi_net_train_step": (I, [H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float]),
+        "adi_net_gradient": (I, [H, ctypes.c_void_p, ctypes.c_void_p, P(ctypes.c_float), P(D)]),
+        "adi_net_loss": (I, [H, P(D), P(I)]),
+        "adi_fields_distance": (I, [H, H, P(D)]),
+        "adi_copy_state": (I, [H, H]),
+        "adi_corrector_run": (I, [H, H, H, I, I, I, D, P(I), P(D)]),
+        "adi_net_destroy": (None, [H]),
+        "adi_net_last_error": (ctypes.c_char_p, [H]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -292,3 +313,139 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------ learned corrector
+NET_PARAMS = 83056
+NET_CI = (16, 32, 32, 32)     # padded channels of the parameter vector
+NET_CO = (32, 32, 32, 16)
+NET_REAL = ((9, 32), (32, 32), (32, 32), (32, 6))
+
+
+def net_flatten(params):
+    """List of (w[3,3,3,ci,co], b[co]) with the real channel counts -> the padded
+    FP32 parameter vector of include/adi_corrector.h (tap = 9 dz + 3 dy + dx)."""
+    out = np.zeros(NET_PARAMS, dtype=np.float32)
+    off = 0
+    for (w, b), CI, CO in zip(params, NET_CI, NET_CO):
+        ci, co = w.shape[3], w.shape[4]
+        blk = np.zeros((27, CI, CO), dtype=np.float32)
+        blk[:, :ci, :co] = np.asarray(w).reshape(27, ci, co)
+        out[off:off + 27 * CI * CO] = blk.ravel()
+        off += 27 * CI * CO
+        out[off:off + co] = b
+        off += CO
+    assert off == NET_PARAMS
+    return out
+
+
+def net_unflatten(flat):
+    """Inverse of net_flatten (drops the padding)."""
+    out = []
+    off = 0
+    for (ci, co), CI, CO in zip(NET_REAL, NET_CI, NET_CO):
+        blk = np.asarray(flat[off:off + 27 * CI * CO], dtype=np.float64).reshape(27, CI, CO)
+        off += 27 * CI * CO
+        b = np.asarray(flat[off:off + co], dtype=np.float64)
+        off += CO
+        out.append((blk[:, :ci, :co].reshape(3, 3, 3, ci, co).copy(), b.copy()))
+    return out
+
+
+class Net:
+    """The corrector net on a coefficient grid N = (N_x, N_y, N_z) (owns an adi_net).
+
+    Device arrays are passed as integer device pointers (e.g. torch
+    ``tensor.data_ptr()``): features X bf16 [V][16], targets / outputs fp32 [V][8]."""
+
+    def __init__(self, N):
+        lib = load_library()
+        self._lib = lib
+        self.N = tuple(int(v) for v in N)
+        h = ctypes.c_void_p()
+        st = lib.adi_net_create(self.N[0], self.N[1], self.N[2], ctypes.byref(h))
+        if st != ADI_OK:
+            raise AdiError(st, lib.adi_net_last_error(None).decode())
+        self.h = h
+
+    def _check(self, st):
+        if st != ADI_OK:
+            raise AdiError(st, self._lib.adi_net_last_error(self.h).decode())
+
+    def set_stream(self, stream_ptr):
+        self._check(self._lib.adi_net_set_stream(self.h, ctypes.c_void_p(int(stream_ptr))))
+
+    def set_params(self, flat):
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        self._check(self._lib.adi_net_set_params(self.h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), a.size))
+
+    def get_params(self):
+        a = np.zeros(NET_PARAMS, dtype=np.float32)
+        self._check(self._lib.adi_net_get_params(self.h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), a.size))
+        return a
+
+    def features(self, solver, X):
+        self._check(self._lib.adi_net_features(self.h, solver.h, ctypes.c_void_p(int(X))))
+
+    def target(self, fine, coarse, T):
+        self._check(self._lib.adi_net_target(self.h, fine.h, coarse.h, ctypes.c_void_p(int(T))))
+
+    def forward(self, X, Y):
+        self._check(self._lib.adi_net_forward(self.h, ctypes.c_void_p(int(X)), ctypes.c_void_p(int(Y))))
+
+    def apply(self, solver, Y):
+        self._check(self._lib.adi_net_apply(self.h, solver.h, ctypes.c_void_p(int(Y))))
+
+    def train_step(self, X, T, lr):
+        self._check(self._lib.adi_net_train_step(self.h, ctypes.c_void_p(int(X)), ctypes.c_void_p(int(T)),
+                                                 float(lr)))
+
+    def gradient(self, X, T):
+        g = np.zeros(NET_PARAMS, dtype=np.float32)
+        loss = ctypes.c_double()
+        self._check(self._lib.adi_net_gradient(self.h, ctypes.c_void_p(int(X)), ctypes.c_void_p(int(T)),
+                                               g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(loss)))
+        return g, loss.value
+
+    def loss(self):
+        s = ctypes.c_double()
+        c = ctypes.c_int()
+        self._check(self._lib.adi_net_loss(self.h, ctypes.byref(s), ctypes.byref(c)))
+        return s.value, c.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.adi_net_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fields_distance(a, b):
+    """||fields(a) - fields(b)|| / ||fields(b)|| of two FP32 solvers."""
+    lib = load_library()
+    r = ctypes.c_double()
+    st = lib.adi_fields_distance(a.h, b.h, ctypes.byref(r))
+    if st != ADI_OK:
+        raise AdiError(st, lib.adi_net_last_error(None).decode())
+    return r.value
+
+
+def copy_state(dst, src):
+    lib = load_library()
+    st = lib.adi_copy_state(dst.h, src.h)
+    if st != ADI_OK:
+        raise AdiError(st, lib.adi_net_last_error(None).decode())
+
+
+def corrector_run(net, coarse, fine, m, k=8, guard_every=8, tol=1e-4):
+    """Guarded corrected time loop; returns (fallback windows, largest guard distance)."""
+    nf = ctypes.c_int()
+    me = ctypes.c_double()
+    net._check(net._lib.adi_corrector_run(net.h, coarse.h, fine.h, int(m), int(k), int(guard_every), float(tol),
+                                          ctypes.byref(nf), ctypes.byref(me)))
+    return nf.value, me.value

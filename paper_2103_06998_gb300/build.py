@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libadi_maxwell.so")
-SOURCES = ["adi_kernels.cu", "adi_capi.cpp", "setup_host.cpp", "adi_noalloc.cu", "adi_batch.cpp"]
+SOURCES = ["adi_kernels.cu", "adi_capi.cpp", "setup_host.cpp", "adi_noalloc.cu", "adi_batch.cpp", "adi_net.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

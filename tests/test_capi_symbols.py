@@ -7,11 +7,12 @@ import re
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "adi_maxwell.h")
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
 
 
 def _declared():
-    txt = open(HEADER).read()
+    txt = "".join(open(h).read() for h in HEADERS)
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
     return sorted(set(re.findall(r"\b(adi_[a-z_]+)\s*\(", txt)))
 
@@ -57,3 +58,21 @@ def test_invalid_arguments_rejected_before_any_cuda_call(lib):
     assert L.adi_create(4, 4, 4, 2, 0.1, adi._dptr(bad), None, None, None, ctypes.byref(h)) == adi.ADI_EINVAL
     assert b"eps and mu" in L.adi_last_error(None)
     assert L.adi_step(None, 1) == adi.ADI_EINVAL
+
+
+def test_net_parameter_vector_layout():
+    # 27 CI CO + CO per layer with the padded channel counts of the header
+    import numpy as np
+    from paper_2103_06998_gb300 import adi, inputs
+    assert sum(27 * ci * co + co for ci, co in zip(adi.NET_CI, adi.NET_CO)) == adi.NET_PARAMS
+    txt = open(os.path.join(ROOT, "include", "adi_corrector.h")).read()
+    assert "#define ADI_NET_PARAMS %d" % adi.NET_PARAMS in txt
+    ps = inputs.net_init(5)
+    flat = adi.net_flatten(ps)
+    back = adi.net_unflatten(flat)
+    for (w, b), (w2, b2) in zip(ps, back):
+        np.testing.assert_array_equal(np.float32(w), w2)
+        np.testing.assert_array_equal(np.float32(b), b2)
+    # weight of layer 0, tap (dz, dy, dx) = (1, 2, 0), ci 3, co 7 sits at
+    # (9 + 6 + 0) * 16 * 32 + 3 * 32 + 7
+    assert flat[15 * 16 * 32 + 3 * 32 + 7] == np.float32(ps[0][0][1, 2, 0, 3, 7])
