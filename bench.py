@@ -44,8 +44,11 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--mode", default="single", choices=["single", "batched"],
-                    help="batched: 48 heterogeneous instances (32-128 elements per axis, p in {2,3})")
+    ap.add_argument("--mode", default="single", choices=["single", "batched", "learned"],
+                    help="batched: 48 heterogeneous instances (32-128 elements per axis, p in {2,3}); "
+                         "learned: guarded corrector at 128^3 against plain steps")
+    ap.add_argument("--weights", default=None, help="learned: corrector parameter file (FP32)")
+    ap.add_argument("--coarse-steps", type=int, default=400, help="learned: coarse steps of the guarded run")
     return ap.parse_args()
 
 
@@ -243,6 +246,129 @@ def run_batched(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def run_learned(args, rank, world, local):
+    """Learned coarse-step corrector (weights trained by paper_2103_06998_gb300.corrector
+    at 64^3) on a 128^3-element head map: the guarded loop (k = 8, guard on the
+    first step of every window of 8 coarse steps, tolerance 1e-4 relative l2)
+    against plain steps of tau, in simulated time per second; an untimed
+    verification compares every corrected and every plain coarse step with 8
+    plain steps from the same state."""
+    import torch
+    from paper_2103_06998_gb300 import adi, corrector
+    torch.cuda.set_device(local)
+    n = args.n if args.n != N_ELEM else 128
+    k, every, tol, m = 8, 8, 1e-4, args.coarse_steps
+    N = (n + P,) * 3
+    Nc = N[0] * N[1] * N[2]
+    fine, coarse, tau = corrector.solver_pair((n, n, n), P, k, SEED)
+    start, extra1, _ = corrector.solver_pair((n, n, n), P, k, SEED, tau=tau)
+    probe, extra2, _ = corrector.solver_pair((n, n, n), P, k, SEED, tau=k * tau)
+    extra1.close()
+    extra2.close()
+    stream = torch.cuda.Stream()  # one stream for all: graphs replay, no cross-stream waits
+    torch.cuda.set_stream(stream)
+    for sv in (fine, coarse, start, probe):
+        sv.set_stream(stream.cuda_stream)
+    net = adi.Net(N)
+    net.set_stream(stream.cuda_stream)
+    net.set_params(corrector.load(args.weights or corrector.WEIGHTS))
+    warm = int(round(1.0 / tau))
+    start.set_fields(np.zeros((6,) + N), 0.0)
+    start.step(warm)                               # t ~ 1: the pulse has left the dipole
+    # ---- plain steps of tau
+    adi.copy_state(fine, start)
+    fine.step(max(3, args.warmup))
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nplain = 8 * max(8, args.steps)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        fine.step(nplain)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms_plain = ev0.elapsed_time(ev1) / nplain
+        # ---- the net alone (features + forward + apply of one coarse step)
+        X = torch.zeros((Nc, 16), dtype=torch.bfloat16, device="cuda")
+        Y = torch.zeros((Nc, 8), dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        adi.copy_state(coarse, start)
+        coarse.step(1)
+        net.features(coarse, X.data_ptr())
+        for _ in range(3):
+            net.forward(X.data_ptr(), Y.data_ptr())
+        torch.cuda.synchronize()
+        R = 20
+        ev0.record(stream)
+        for _ in range(R):
+            net.forward(X.data_ptr(), Y.data_ptr())
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms_net = ev0.elapsed_time(ev1) / R
+        ev0.record(stream)
+        coarse.step(R)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms_coarse = ev0.elapsed_time(ev1) / R
+        # ---- the guarded loop (host decisions at every guard: wall clock)
+        adi.copy_state(coarse, start)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nfall, gmax = adi.corrector_run(net, coarse, fine, m, k, every, tol)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    # ---- verification (untimed): along the plain trajectory from the same start,
+    # every coarse step (plain and corrected) against k plain steps from its state
+    state, extra3, _ = corrector.solver_pair((n, n, n), P, k, SEED, tau=tau)
+    extra3.close()
+    state.set_stream(stream.cuda_stream)
+    adi.copy_state(state, start)
+    e_fix, e_plain = [], []
+    for _ in range(m):
+        adi.copy_state(fine, state)
+        fine.step(k)
+        adi.copy_state(probe, state)
+        probe.step(1)
+        e_plain.append(adi.fields_distance(probe, fine))
+        adi.copy_state(coarse, state)
+        coarse.step(1)
+        net.features(coarse, X.data_ptr())
+        net.forward(X.data_ptr(), Y.data_ptr())
+        net.apply(coarse, Y.data_ptr())
+        e_fix.append(adi.fields_distance(coarse, fine))
+        adi.copy_state(state, fine)
+    state.close()
+    for sv in (fine, coarse, start, probe):
+        sv.close()
+    net.close()
+    flops_alg = 27 * 2 * sum(ci * co for ci, co in adi.NET_REAL) * Nc
+    d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    peak = float(d["bf16_tflops"])
+    sim_plain = tau / (ms_plain * 1e-3)
+    sim_learned = m * k * tau / wall
+    if rank == 0:
+        line = {"metric": "simulated time per second, learned corrector vs plain FP32 ADI, %d^3 p=2" % n,
+                "value": sim_learned, "unit": "simulated s / s", "n_gpus": world, "steps": m, "warmup": args.warmup,
+                "ms_per_step": wall * 1e3 / m, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "bf16 net / f32 solver", "data": "synthetic",
+                "config": {"workload": "%d^3 elements, p=2, head-like map seed %d, dipole, tau = 4 dt_CFL, k = %d, "
+                                       "guard every %d coarse steps, tol %g, start t = %.3f" % (n, SEED, k, every, tol, warm * tau),
+                           "tau": tau, "coarse_steps": m},
+                "plain": {"sim_per_s": sim_plain, "ms_per_step": ms_plain, "dof_steps_per_s": 6 * Nc / (ms_plain * 1e-3)},
+                "learned": {"sim_per_s": sim_learned, "speedup_vs_plain": sim_learned / sim_plain,
+                            "fallback_windows": nfall, "windows": (m + every - 1) // every, "guard_max_err": gmax,
+                            "ms_coarse_step": ms_coarse, "ms_net_forward": ms_net},
+                "verification": {"corrected_err_median": float(np.median(e_fix)), "corrected_err_max": float(np.max(e_fix)),
+                                 "plain_coarse_err_median": float(np.median(e_plain)),
+                                 "plain_coarse_err_max": float(np.max(e_plain)),
+                                 "gain_median": float(np.median(np.array(e_plain) / np.array(e_fix)))},
+                "roofline": {"bound": "tensor", "kernel": "conv_kernel (4 launches of one forward)",
+                             "achieved": flops_alg / (ms_net * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                             "frac": flops_alg / (ms_net * 1e-3) / 1e12 / peak, "traffic": None,
+                             "peak_source": "measured (MEASURED_PEAKS.json bf16_tflops)"},
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -252,6 +378,8 @@ def main():
         return run_reference(args, rank, world)
     if args.mode == "batched":
         return run_batched(args, rank, world, local)
+    if args.mode == "learned":
+        return run_learned(args, rank, world, local)
 
     import torch
     import torch.distributed as dist
