@@ -32,6 +32,7 @@ UNIT = "DOF-steps/s"
 N_ELEM = 256
 P = 2
 SEED = 2103
+FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 of GB300
 
 
 def parse():
@@ -41,7 +42,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--n", type=int, default=N_ELEM, help="elements per axis (default 256)")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--mode", default="single", choices=["single", "batched", "learned"],
@@ -444,13 +445,20 @@ def main():
     traffic = ncu_traffic(dom["name"], n)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": traffic, "kernel": dom["name"], "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"
-                if peak_kind == "measured" else "fallback 6.8 TB/s",
-                "step_frac": (50 * Nc * (4 if args.precision == "fp32" else 8)) / (ms_max * 1e-3 / args.steps) / 1e9 / hbm,
+                if peak_kind == "measured" else "fallback 6.8 TB/s"}
+    if dom["name"] == "resid_E64":
+        # FP64-ALU bound: 18 Kronecker terms x 3 passes x (2p+1) FMAs per point
+        flops = 18 * 3 * (2 * P + 1) * 2 * Nc
+        roofline.update({"bound": "alu", "achieved": flops / (avg_ms * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": flops / (avg_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+                         "peak_source": "nominal FP64 of GB300 (no measured FP64 peak)"})
+    roofline.update({
+                "step_frac": (50 * Nc * (8 if args.precision == "fp64" else 4)) / (ms_max * 1e-3 / args.steps) / 1e9 / hbm,
                 "kernels": {k["name"]: {"launches_per_step": k["launches"] / args.steps,
                                         "ms_per_launch": k["total_ms"] / k["launches"],
                                         "share": k["total_ms"] / tot,
                                         "GBps": k["bytes_per_launch"] / (k["total_ms"] / k["launches"] * 1e-3) / 1e9}
-                            for k in stats}}
+                            for k in stats}})
 
     # ---- end to end through the C-ABI with pinned host buffers
     host_in = torch.empty(6 * Nc, dtype=torch.float64, pin_memory=True)
@@ -470,6 +478,21 @@ def main():
     e2e = {"value": world * dof_steps / float(te.item()), "unit": UNIT,
            "h2d_bytes_per_step": 6 * Nc * 8, "d2h_bytes_per_step": 6 * Nc * 8}
 
+    # ---- per-step error against the FP64 GPU step from the same state (untimed)
+    err64 = None
+    if args.precision != "fp64" and rank == 0:
+        st = inputs.random_fields((n + P,) * 3, 7) * 1e-3
+        s64 = adi.Solver((n, n, n), P, tau, eps, mu, sigma, precision="fp64")
+        s64.factor()
+        for sv in (s, s64):
+            sv.set_source(src["x0"], src["comp"], src["amp"], src["f0"], src["t0"], src["s"])
+            sv.set_fields(st, 1.5)
+            sv.step(1)
+        a, _ = s.fields()
+        b, _ = s64.fields()
+        s64.close()
+        err64 = float(np.sqrt(np.sum((a - b) ** 2) / np.sum(b ** 2)))
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(n, eps, mu, sigma, src, tau)
@@ -477,8 +500,9 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
-                "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": {"fp32": "f32", "fp64": "f64", "mixed": "bf16 tiles / f32 / f64 residual"}[args.precision],
+                "data": "synthetic", "error_vs_fp64_per_step": err64,
                 "config": {"workload": "ADI IGA Maxwell step, %d^3 elements, p=2, head-like 3-phase map seed %d, "
                                        "dipole, tau=4 dt_CFL" % (n, SEED), "n": n, "p": P, "tau": tau,
                            "l2": "working set 0.7 GB >> 129 MB L2 (no flush needed)",

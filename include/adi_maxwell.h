@@ -55,13 +55,22 @@ typedef enum {
   ADI_ETIMEOUT = 6  /* a bounded device wait gave up */
 } adi_status;
 
-/* Arithmetic of the time step. */
-enum { ADI_PREC_FP64 = 0, ADI_PREC_FP32 = 1 };
+/* Arithmetic of the time step.
+ *  ADI_PREC_FP32, ADI_PREC_FP64: every kernel in that type.
+ *  ADI_PREC_MIXED: FP32 state and line solves; in each E half step the
+ *  right-hand side is contracted from field tiles rounded to BF16 with FP32
+ *  accumulation, giving E*; then one refinement: the residual
+ *  r = RHS - T E* of the E system T E = RHS is evaluated in FP64 arithmetic
+ *  (from the FP32 state), T delta = r is solved in FP32 and E = E* + delta.
+ *  The 1D factorisations are FP64 in every mode.  The paper states no
+ *  precision; this mode is an addition. */
+enum { ADI_PREC_FP64 = 0, ADI_PREC_FP32 = 1, ADI_PREC_MIXED = 2 };
 
 typedef struct {
-  int precision;   /* ADI_PREC_FP32 (default) or ADI_PREC_FP64 */
-  int use_graph;   /* 1 (default): adi_step replays a captured CUDA graph of one step */
-  int reserved[6]; /* must be 0 */
+  int precision;        /* ADI_PREC_FP32 (default), ADI_PREC_FP64 or ADI_PREC_MIXED */
+  int use_graph;        /* 1 (default): adi_step replays a captured CUDA graph of one step */
+  int mixed_no_refine;  /* ADI_PREC_MIXED only: 1 skips the refinement (E = E*, for error studies) */
+  int reserved[5];      /* must be 0 */
 } adi_options;
 
 /* Create a problem on the unit cube.

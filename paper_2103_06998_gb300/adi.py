@@ -14,7 +14,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libadi_maxwell.so")
 
 ADI_OK, ADI_EINVAL, ADI_ENOMEM, ADI_ECUDA, ADI_ESTATE, ADI_ENUMERIC, ADI_ETIMEOUT = range(7)
-PREC_FP64, PREC_FP32 = 0, 1
+PREC_FP64, PREC_FP32, PREC_MIXED = 0, 1, 2
+_PREC = {"fp64": PREC_FP64, "fp32": PREC_FP32, "mixed": PREC_MIXED}
 
 # every symbol declared in include/adi_maxwell.h
 EXPORTS = ("adi_create", "adi_factor", "adi_set_dt", "adi_set_stream", "adi_set_fields",
@@ -30,7 +31,8 @@ EXPORTS = ("adi_create", "adi_factor", "adi_set_dt", "adi_set_stream", "adi_set_
 
 
 class AdiOptions(ctypes.Structure):
-    _fields_ = [("precision", ctypes.c_int), ("use_graph", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+    _fields_ = [("precision", ctypes.c_int), ("use_graph", ctypes.c_int), ("mixed_no_refine", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
 
 
 class AdiInstanceDesc(ctypes.Structure):
@@ -126,7 +128,8 @@ def _dptr(a):
 class Solver:
     """One ADI Maxwell problem on the GPU (owns an adi_handle)."""
 
-    def __init__(self, n, p, dt, eps=None, mu=None, sigma=None, precision="fp32", use_graph=True, _handle=None):
+    def __init__(self, n, p, dt, eps=None, mu=None, sigma=None, precision="fp32", use_graph=True, _handle=None,
+                 refine=True):
         lib = load_library()
         self._lib = lib
         if _handle is not None:  # an instance owned by a Batch
@@ -142,8 +145,9 @@ class Solver:
         self.n = tuple(int(v) for v in n)
         self.p = int(p)
         opt = AdiOptions()
-        opt.precision = PREC_FP64 if precision == "fp64" else PREC_FP32
+        opt.precision = _PREC[precision]
         opt.use_graph = 1 if use_graph else 0
+        opt.mixed_no_refine = 0 if refine else 1
         self.dtype = np.float64 if precision == "fp64" else np.float32
         keep = []
 

@@ -14,6 +14,7 @@ namespace adi {
 
 constexpr int kMaxP = 3;
 constexpr int kMaxTerms = 12;
+constexpr int kMaxResidTerms = 18;  // E right-hand side (12) and T E* (6) of the mixed-mode residual
 
 // ---------------------------------------------------------------- host setup
 struct Axis1D {
@@ -138,7 +139,8 @@ struct Ctx {
   int n[3] = {0, 0, 0};  // elements x, y, z
   int N[3] = {0, 0, 0};  // coefficients per axis
   int p = 2;
-  int precision = ADI_PREC_FP32;
+  int precision = ADI_PREC_FP32;  // FP32 and MIXED keep FP32 state (element type float)
+  int mixed_refine = 0;           // MIXED: one FP64 residual refinement per E half step
   int use_graph = 1;
   int line_tile = 0;  // lines per line-solve CTA (0: largest that leaves two CTAs per SM)
   double dt = 0.0;
@@ -174,6 +176,8 @@ struct Ctx {
   // 1D tables on device (element type T)
   void* tab = nullptr;
   size_t tab_bytes = 0;
+  double* tab64 = nullptr;  // MIXED: the band tables in FP64 for the residual
+  size_t tab64_bytes = 0;
   Axis1D axes[3];
   LuConst luconst[3][2];  // per axis: full and Dirichlet-reduced mass LU
   double* d_clock_t0 = nullptr;

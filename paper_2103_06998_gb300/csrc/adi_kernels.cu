@@ -18,6 +18,7 @@
 //                memory (coalesced, transposed to line-major for x), solved in
 //                place and written back.  STIFF=true factors the row-scaled
 //                M + c S on the fly; otherwise the precomputed mass LU is used.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -28,6 +29,8 @@
 namespace adi {
 
 namespace {
+
+unsigned grid_for(long long n, int threads);
 
 // ------------------------------------------------------------------ RHS
 template <typename T, int P, int TX, int TY, int TZ>
@@ -170,6 +173,160 @@ __global__ void __launch_bounds__(TX* TY) rhs_kernel(const RhsParams<T> prm) {
   }
   if (prm.advance_clock && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && tid == 0)
     *prm.clock_step += 1;
+}
+
+// ------------------------------------------------ mixed-mode FP64 residual
+// r = RHS - T E* of the E system, in FP64 arithmetic from FP32 arrays:
+// fields 0..5 are the inputs of the E right-hand side (E, H of the old level),
+// 6..8 the FP32 solution E* of T E = RHS(BF16 tiles); the terms are the 12 of
+// the right-hand side and, per component, -M(x)M(x)M E*_k and -c S_s(x)M(x)M
+// E*_k (S along the stiffness axis s of component k).  Same tiling as
+// rhs_kernel; band tables in FP64.
+struct ResidParams {
+  const float* fields[9];
+  const float* coef[5];  // [CF_A], [CF_B], [CF_C]
+  float* out[3];
+  const double* band[3][4];  // [axis][op]
+  Term terms[kMaxResidTerms];
+  int nterms;
+  int Nx, Ny, Nz, pitch;
+  int src_comp;
+  int src_i0[3];
+  double src_w[3][kMaxP + 1];
+  double src_amp, src_f0, src_t0, src_s;
+  double tau, t_frac;
+  const double* clock_t0;
+  const long long* clock_step;
+};
+
+template <int P>
+__global__ void __launch_bounds__(256) resid_kernel(const ResidParams prm) {
+  constexpr int TX = 32, TY = 8, TZ = 8;
+  constexpr int W = 2 * P + 1;
+  constexpr int HX = TX + 2 * P, HY = TY + 2 * P, HZ = TZ + 2 * P;
+  constexpr int NT = TX * TY;
+  extern __shared__ __align__(16) unsigned char resid_smem[];
+  double* s_in = reinterpret_cast<double*>(resid_smem);
+  double* s_z = s_in + HZ * HY * HX;
+  double* s_y = s_z + TZ * HY * HX;
+  __shared__ double s_bx[TX][W], s_by[TY][W], s_bz[TZ][W];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
+  const int Nx = prm.Nx, Ny = prm.Ny, Nz = prm.Nz, pitch = prm.pitch;
+  const long long sxy = (long long)pitch * Ny;
+  const int gx = x0 + tx, gy = y0 + ty;
+  const bool col_in = gx < Nx && gy < Ny;
+  double cf[4][TZ];  // 1, a, b, c
+#pragma unroll
+  for (int zz = 0; zz < TZ; ++zz) {
+    const int gz = z0 + zz;
+    const bool in = col_in && gz < Nz;
+    const long long g = gz * sxy + (long long)gy * pitch + gx;
+    cf[0][zz] = 1.0;
+#pragma unroll
+    for (int k = 1; k < 4; ++k) cf[k][zz] = in ? (double)prm.coef[k][g] : 0.0;
+  }
+  double acc[3][TZ];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int zz = 0; zz < TZ; ++zz) acc[c][zz] = 0.0;
+  int cur_field = -1;
+  for (int t = 0; t < prm.nterms; ++t) {
+    const Term tm = prm.terms[t];
+    __syncthreads();
+    if (tm.field != cur_field) {
+      const float* __restrict__ f = prm.fields[tm.field];
+      for (int i = tid; i < HZ * HY * HX; i += NT) {
+        const int xx = i % HX, r = i / HX, yy = r % HY, zz = r / HY;
+        const int X = x0 - P + xx, Y = y0 - P + yy, Z = z0 - P + zz;
+        double v = 0.0;
+        if (X >= 0 && X < Nx && Y >= 0 && Y < Ny && Z >= 0 && Z < Nz) v = f[Z * sxy + (long long)Y * pitch + X];
+        s_in[i] = v;
+      }
+      cur_field = tm.field;
+    }
+    {
+      const double* bx = prm.band[0][tm.op[0]];
+      const double* by = prm.band[1][tm.op[1]];
+      const double* bz = prm.band[2][tm.op[2]];
+      for (int i = tid; i < (TX + TY + TZ) * W; i += NT) {
+        const int row = i / W, q = i % W;
+        if (row < TX) {
+          const int g = x0 + row;
+          s_bx[row][q] = g < Nx ? bx[g * W + q] : 0.0;
+        } else if (row < TX + TY) {
+          const int g = y0 + row - TX;
+          s_by[row - TX][q] = g < Ny ? by[g * W + q] : 0.0;
+        } else {
+          const int g = z0 + row - TX - TY;
+          s_bz[row - TX - TY][q] = g < Nz ? bz[g * W + q] : 0.0;
+        }
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < TZ * HY * HX; i += NT) {
+      const int rem = i % (HY * HX), zz = i / (HY * HX);
+      double v = 0.0;
+#pragma unroll
+      for (int q = 0; q < W; ++q) v += s_bz[zz][q] * s_in[(zz + q) * HY * HX + rem];
+      s_z[i] = v;
+    }
+    __syncthreads();
+    for (int i = tid; i < TZ * TY * HX; i += NT) {
+      const int xx = i % HX, r = i / HX, yy = r % TY, zz = r / TY;
+      double v = 0.0;
+#pragma unroll
+      for (int q = 0; q < W; ++q) v += s_by[yy][q] * s_z[(zz * HY + yy + q) * HX + xx];
+      s_y[i] = v;
+    }
+    __syncthreads();
+    const int ck = tm.coef == CF_A ? 1 : tm.coef == CF_B ? 2 : tm.coef == CF_C ? 3 : 0;
+#pragma unroll
+    for (int zz = 0; zz < TZ; ++zz) {
+      double v = 0.0;
+#pragma unroll
+      for (int q = 0; q < W; ++q) v += s_bx[tx][q] * s_y[(zz * TY + ty) * HX + tx + q];
+      const double w = (double)tm.sign * cf[ck][zz] * v;
+      if (tm.out == 0) acc[0][zz] += w;
+      else if (tm.out == 1) acc[1][zz] += w;
+      else acc[2][zz] += w;
+    }
+  }
+  double g = 0.0;
+  if (prm.src_comp >= 0) {
+    const double tmid = *prm.clock_t0 + ((double)*prm.clock_step + prm.t_frac) * prm.tau;
+    const double u = tmid - prm.src_t0;
+    g = prm.src_amp * sin(2.0 * 3.14159265358979323846 * prm.src_f0 * u) * exp(-(u / prm.src_s) * (u / prm.src_s));
+  }
+  if (!col_in) return;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+#pragma unroll
+    for (int zz = 0; zz < TZ; ++zz) {
+      const int gz = z0 + zz;
+      if (gz >= Nz) continue;
+      double v = acc[c][zz];
+      if (c == prm.src_comp) {
+        const int ix = gx - prm.src_i0[0], iy = gy - prm.src_i0[1], iz = gz - prm.src_i0[2];
+        if (ix >= 0 && ix <= P && iy >= 0 && iy <= P && iz >= 0 && iz <= P)
+          v -= cf[2][zz] * g * prm.src_w[0][ix] * prm.src_w[1][iy] * prm.src_w[2][iz];
+      }
+      prm.out[c][gz * sxy + (long long)gy * pitch + gx] = (float)v;
+    }
+  }
+}
+
+// E += delta on the N_x columns of every row (mixed-mode refinement)
+__global__ void add_delta_kernel(float* e0, float* e1, float* e2, const float* d0, const float* d1,
+                                 const float* d2, int Nx, int pitch, long long rows) {
+  const long long n = rows * (long long)Nx;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long g = (i / Nx) * pitch + i % Nx;
+    e0[g] += d0[g];
+    e1[g] += d1[g];
+    e2[g] += d2[g];
+  }
 }
 
 // ----------------------------------------------------------- line solves
@@ -768,7 +925,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
   return false;
 }
 
-template <typename T, int P, int H, int F>
+template <typename T, int P, int H, int F, bool BFT>
 __device__ __forceinline__ bool do_field(const RhsParams<T>& prm, const TmaMaps& maps, T* s_tile, T* s_zr,
                                          T* s_yr, unsigned long long* bars, int x0, int y0, int z0, bool inZ,
                                          bool inY, bool inX, int xp, int rg, T (&cf)[3][RPT][2],
@@ -783,6 +940,12 @@ __device__ __forceinline__ bool do_field(const RhsParams<T>& prm, const TmaMaps&
   // every thread waits for the tile; the give-up decision is made block-wide
   if (!__syncthreads_and(mbar_wait(&bars[B], PAR))) return false;
   const T* tl = s_tile + B * S::TILE;
+  if (BFT) {  // mixed precision: the field tile rounded to BF16 (FP32 accumulation below)
+    T* tw = s_tile + B * S::TILE;
+    for (int i = tid; i < S::TILE; i += NT) tw[i] = T(__bfloat162float(__float2bfloat16_rn(float(tw[i]))));
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // before TMA reuses the buffer
+    __syncthreads();
+  }
   constexpr bool zshare = PL::z0 == PL::z1;
   for (int i = tid; i < S::HY * S::HX; i += NT) {
     if (inZ) zpass<T, P, PL::z0, true>(prm, tl, s_zr, z0, i);
@@ -819,7 +982,7 @@ __device__ __forceinline__ bool do_field(const RhsParams<T>& prm, const TmaMaps&
 }
 }  // namespace rhs2
 
-template <typename T, int P, int H>
+template <typename T, int P, int H, bool BFT>
 __global__ void __launch_bounds__(rhs2::NT, sizeof(T) == 4 ? ADI_RHS_MINB : 1)
     rhs_e_kernel(const RhsParams<T> prm, const __grid_constant__ TmaMaps maps) {
   using namespace rhs2;
@@ -865,12 +1028,12 @@ __global__ void __launch_bounds__(rhs2::NT, sizeof(T) == 4 ? ADI_RHS_MINB : 1)
   }
   __syncthreads();
   if (tid == 0) tma_tile<T, P>(&maps.m[0], s_tile, &bars[0], x0 - 4, y0 - P, z0 - P);
-  bool ok = do_field<T, P, H, 0>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
-  if (ok) ok = do_field<T, P, H, 1>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
-  if (ok) ok = do_field<T, P, H, 2>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
-  if (ok) ok = do_field<T, P, H, 3>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
-  if (ok) ok = do_field<T, P, H, 4>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
-  if (ok) ok = do_field<T, P, H, 5>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+  bool ok = do_field<T, P, H, 0, BFT>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+  if (ok) ok = do_field<T, P, H, 1, BFT>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+  if (ok) ok = do_field<T, P, H, 2, BFT>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+  if (ok) ok = do_field<T, P, H, 3, BFT>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+  if (ok) ok = do_field<T, P, H, 4, BFT>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+  if (ok) ok = do_field<T, P, H, 5, BFT>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
   if (!ok) {
     // a tile never arrived: report, give the copies in flight a bounded time, leave
     if (tid == 0) atomicOr(prm.err, 1);
@@ -1274,7 +1437,7 @@ Stencils<T> stencils_of(const Axis1D& ax) {
 }
 
 template <typename T, int P>
-cudaError_t launch_rhs_e(Ctx& c, RhsParams<T>& prm, int half, double bytes) {
+cudaError_t launch_rhs_e(Ctx& c, RhsParams<T>& prm, int half, double bytes, bool bf16_tiles) {
   using namespace rhs2;
   if (!c.tmaps_ok) return cudaErrorInvalidValue;
   for (int d = 0; d < 3; ++d) prm.st[d] = stencils_of<T>(c.axes[d]);
@@ -1286,8 +1449,18 @@ cudaError_t launch_rhs_e(Ctx& c, RhsParams<T>& prm, int half, double bytes) {
   }
   dim3 grid((c.N[0] + TX - 1) / TX, (c.N[1] + TY - 1) / TY, (c.N[2] + TZ - 1) / TZ);
   prof_begin(c, "rhs_E", bytes);
-  if (half == 1) rhs_e_kernel<T, P, 1><<<grid, NT, rhs_e_smem<T, P>(), c.stream>>>(prm, maps);
-  else rhs_e_kernel<T, P, 2><<<grid, NT, rhs_e_smem<T, P>(), c.stream>>>(prm, maps);
+  bool done = false;
+  if constexpr (sizeof(T) == 4) {  // BF16 field tiles: mixed mode, FP32 only
+    if (bf16_tiles) {
+      if (half == 1) rhs_e_kernel<T, P, 1, true><<<grid, NT, rhs_e_smem<T, P>(), c.stream>>>(prm, maps);
+      else rhs_e_kernel<T, P, 2, true><<<grid, NT, rhs_e_smem<T, P>(), c.stream>>>(prm, maps);
+      done = true;
+    }
+  }
+  if (!done) {
+    if (half == 1) rhs_e_kernel<T, P, 1, false><<<grid, NT, rhs_e_smem<T, P>(), c.stream>>>(prm, maps);
+    else rhs_e_kernel<T, P, 2, false><<<grid, NT, rhs_e_smem<T, P>(), c.stream>>>(prm, maps);
+  }
   prof_end(c);
   return cudaGetLastError();
 }
@@ -1353,8 +1526,101 @@ LineJob<T> job_of(const T* src, T* dst, const T* aux, double scale, int dirichle
   return j;
 }
 
-// E half step: RHS, then per component the stiffness direction first, then the
-// two mass directions (order of the Appendix, eqs. split1/split2).
+// stiffness direction of E_i: half 1 (y, z, x), half 2 (z, x, y)
+constexpr int kStiffDir[2][3] = {{1, 2, 0}, {2, 0, 1}};
+
+// Solve T E = R per component: the stiffness direction first, then the two
+// mass directions (order of the Appendix, eqs. split1/split2); R is overwritten
+// and the result goes to out (may be R itself).
+template <typename T, int P>
+cudaError_t e_solve(Ctx& c, int half, T* const* R, T* const* out) {
+  T** cf = reinterpret_cast<T**>(c.coef);
+  static const char* stiff_name[3] = {"line_x_stiff", "line_y_stiff", "line_z_stiff"};
+  static const char* mass_name[3] = {"line_x_mass", "line_y_mass", "line_z_mass"};
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+    const int sd = kStiffDir[half - 1][i];
+    LineJobs<T> js{};
+    js.job[0] = job_of<T>(R[i], R[i], cf[2], 0.0, 1, reinterpret_cast<const T*>(c.pivots[sd]));
+    e = launch_line<T, P>(c, sd, LM_STIFF, js, 1, stiff_name[sd]);
+    if (e != cudaSuccess) return e;
+    int md[2], m = 0;
+    for (int d = 0; d < 3; ++d)
+      if (d != sd) md[m++] = d;
+    js.job[0] = job_of<T>(R[i], R[i], nullptr, 0.0, md[0] != i);
+    e = launch_line<T, P>(c, md[0], LM_MASS, js, 1, mass_name[md[0]]);
+    if (e != cudaSuccess) return e;
+    js.job[0] = job_of<T>(R[i], out[i], nullptr, 0.0, md[1] != i);
+    e = launch_line<T, P>(c, md[1], LM_MASS, js, 1, mass_name[md[1]]);
+  }
+  return e;
+}
+
+// FP64 band table of (axis d, op o) inside c.tab64
+inline const double* band64(const Ctx& c, int d, int o) {
+  size_t off = 0;
+  const int W = 2 * c.p + 1;
+  for (int k = 0; k < d; ++k) off += 4 * (size_t)c.N[k] * W;
+  return c.tab64 + off + (size_t)o * c.N[d] * W;
+}
+
+template <int P>
+cudaError_t launch_resid(Ctx& c, int half, float* const* Ein, float* const* Hin, float* const* Estar, float* const* R) {
+  float** cf = reinterpret_cast<float**>(c.coef);
+  ResidParams prm{};
+  for (int i = 0; i < 3; ++i) {
+    prm.fields[i] = Ein[i];
+    prm.fields[3 + i] = Hin[3 + i];
+    prm.fields[6 + i] = Estar[i];
+    prm.out[i] = R[i];
+  }
+  prm.coef[CF_A] = cf[0];
+  prm.coef[CF_B] = cf[1];
+  prm.coef[CF_C] = cf[2];
+  for (int d = 0; d < 3; ++d)
+    for (int o = 0; o < 4; ++o) prm.band[d][o] = band64(c, d, o);
+  int n = e_terms(half, prm.terms);
+  for (int k = 0; k < 3; ++k) {
+    Term t{};
+    t.field = 6 + k;
+    t.out = k;
+    t.op[0] = t.op[1] = t.op[2] = OP_M;
+    t.coef = CF_ONE;
+    t.sign = -1.f;
+    prm.terms[n++] = t;
+    t.op[kStiffDir[half - 1][k]] = OP_S;
+    t.coef = CF_C;
+    prm.terms[n++] = t;
+  }
+  prm.nterms = n;
+  prm.Nx = c.N[0];
+  prm.Ny = c.N[1];
+  prm.Nz = c.N[2];
+  prm.pitch = c.pitch;
+  prm.src_comp = (c.src_comp >= 0 && c.src_amp != 0.0) ? c.src_comp : -1;
+  for (int d = 0; d < 3; ++d) {
+    prm.src_i0[d] = c.src_i0[d];
+    for (int q = 0; q <= kMaxP; ++q) prm.src_w[d][q] = c.src_w[d][q];
+  }
+  prm.src_amp = c.src_amp;
+  prm.src_f0 = c.src_f0;
+  prm.src_t0 = c.src_t0;
+  prm.src_s = c.src_s;
+  prm.tau = c.dt;
+  prm.t_frac = half == 1 ? 0.25 : 0.75;
+  prm.clock_t0 = c.d_clock_t0;
+  prm.clock_step = c.d_clock_step;
+  constexpr int TX = 32, TY = 8, TZ = 8;
+  const size_t smem = sizeof(double) * ((size_t)(TZ + 2 * P) * (TY + 2 * P) * (TX + 2 * P) +
+                                        (size_t)TZ * (TY + 2 * P) * (TX + 2 * P) + (size_t)TZ * TY * (TX + 2 * P));
+  dim3 grid((c.N[0] + TX - 1) / TX, (c.N[1] + TY - 1) / TY, (c.N[2] + TZ - 1) / TZ);
+  prof_begin(c, "resid_E64", (double)c.Nc * 4.0 * 15.0);  // reads 9 fields + a, b, c, writes 3
+  resid_kernel<P><<<grid, dim3(TX, TY), smem, c.stream>>>(prm);
+  prof_end(c);
+  return cudaGetLastError();
+}
+
+// E half step: the right-hand side, then the line solves (e_solve).
 template <typename T, int P>
 cudaError_t e_substep(Ctx& c, int half) {
   T** cur = reinterpret_cast<T**>(c.cur);
@@ -1396,29 +1662,25 @@ cudaError_t e_substep(Ctx& c, int half) {
   prm.clock_step = c.d_clock_step;
   prm.advance_clock = 0;
   double bytes = (double)c.Nc * sizeof(T) * 12.0;
-  cudaError_t e = launch_rhs_e<T, P>(c, prm, half, bytes);
+  const bool mixed = c.precision == ADI_PREC_MIXED;
+  cudaError_t e = launch_rhs_e<T, P>(c, prm, half, bytes, mixed);
   if (e != cudaSuccess) return e;
-  // stiffness direction of E_i: half 1 (y, z, x), half 2 (z, x, y)
-  static const int stiff_dir[2][3] = {{1, 2, 0}, {2, 0, 1}};
-  static const char* stiff_name[3] = {"line_x_stiff", "line_y_stiff", "line_z_stiff"};
-  static const char* mass_name[3] = {"line_x_mass", "line_y_mass", "line_z_mass"};
-  for (int i = 0; i < 3; ++i) {
-    int sd = stiff_dir[half - 1][i];
-    LineJobs<T> js{};
-    js.job[0] = job_of<T>(R[i], R[i], cf[2], 0.0, 1, reinterpret_cast<const T*>(c.pivots[sd]));
-    e = launch_line<T, P>(c, sd, LM_STIFF, js, 1, stiff_name[sd]);
-    if (e != cudaSuccess) return e;
-    int md[2], m = 0;
-    for (int d = 0; d < 3; ++d)
-      if (d != sd) md[m++] = d;
-    js.job[0] = job_of<T>(R[i], R[i], nullptr, 0.0, md[0] != i);
-    e = launch_line<T, P>(c, md[0], LM_MASS, js, 1, mass_name[md[0]]);
-    if (e != cudaSuccess) return e;
-    js.job[0] = job_of<T>(R[i], Eout[i], nullptr, 0.0, md[1] != i);
-    e = launch_line<T, P>(c, md[1], LM_MASS, js, 1, mass_name[md[1]]);
-    if (e != cudaSuccess) return e;
+  e = e_solve<T, P>(c, half, R, Eout);
+  if (e != cudaSuccess || !mixed || !c.mixed_refine) return e;
+  if constexpr (sizeof(T) == 4) {
+    // one refinement: R = RHS - T E* in FP64, T delta = R in place, E = E* + delta
+    e = launch_resid<P>(c, half, Ein, Hin, Eout, R);
+    if (e == cudaSuccess) e = e_solve<T, P>(c, half, R, R);
+    if (e == cudaSuccess) {
+      const long long rows = (long long)c.N[1] * c.N[2];
+      prof_begin(c, "add_delta", (double)c.Nc * 4.0 * 9.0);
+      add_delta_kernel<<<grid_for(rows * c.N[0], 256), 256, 0, c.stream>>>(Eout[0], Eout[1], Eout[2], R[0], R[1], R[2],
+                                                                          c.N[0], c.pitch, rows);
+      prof_end(c);
+      e = cudaGetLastError();
+    }
   }
-  return cudaSuccess;
+  return e;
 }
 
 // H half step, general material: M H_new = M H_old - d C1 E_alpha + d C2 E_beta
@@ -1557,8 +1819,13 @@ cudaError_t opt_in(K kern, int optin) {
 template <typename T, int P>
 cudaError_t prepare_tp(int optin) {
   cudaError_t e = opt_in(rhs_kernel<T, P, 32, 8, 8>, optin);
-  if (e == cudaSuccess) e = opt_in(rhs_e_kernel<T, P, 1>, optin);
-  if (e == cudaSuccess) e = opt_in(rhs_e_kernel<T, P, 2>, optin);
+  if (e == cudaSuccess) e = opt_in(rhs_e_kernel<T, P, 1, false>, optin);
+  if (e == cudaSuccess) e = opt_in(rhs_e_kernel<T, P, 2, false>, optin);
+  if constexpr (sizeof(T) == 4) {
+    if (e == cudaSuccess) e = opt_in(rhs_e_kernel<T, P, 1, true>, optin);
+    if (e == cudaSuccess) e = opt_in(rhs_e_kernel<T, P, 2, true>, optin);
+    if (e == cudaSuccess) e = opt_in(resid_kernel<P>, optin);
+  }
   if (e == cudaSuccess) e = opt_in(line_kernel<T, P, LM_MASS, true>, optin);
   if (e == cudaSuccess) e = opt_in(line_kernel<T, P, LM_STIFF, true>, optin);
   if (e == cudaSuccess) e = opt_in(line_kernel<T, P, LM_DERIV, true>, optin);
@@ -1606,6 +1873,21 @@ cudaError_t upload_tables(Ctx& c) {
   if (e != cudaSuccess) return e;
   e = c.precision == ADI_PREC_FP64 ? upload_tables_t<double>(c) : upload_tables_t<float>(c);
   if (e != cudaSuccess) return e;
+  if (c.precision == ADI_PREC_MIXED) {  // FP64 bands for the residual: per axis M, S, A, B
+    std::vector<double> h;
+    for (int d = 0; d < 3; ++d) {
+      const Axis1D& ax = c.axes[d];
+      for (const std::vector<double>* v : {&ax.M, &ax.S, &ax.A, &ax.B}) h.insert(h.end(), v->begin(), v->end());
+    }
+    if (!c.tab64) {
+      e = cudaMalloc((void**)&c.tab64, h.size() * sizeof(double));
+      if (e != cudaSuccess) return e;
+      c.tab64_bytes = h.size() * sizeof(double);
+    }
+    e = cudaMemcpyAsync(c.tab64, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) return e;
+  }
   return c.precision == ADI_PREC_FP64 ? pivots_t<double>(c) : pivots_t<float>(c);
 }
 
