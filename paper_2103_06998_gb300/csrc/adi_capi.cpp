@@ -46,8 +46,11 @@ void free_ctx(Ctx* c0) {
     if (c->rhs[i]) cudaFree(c->rhs[i]);
   for (int i = 0; i < 4; ++i)
     if (c->coef[i]) cudaFree(c->coef[i]);
-  for (int i = 0; i < 3; ++i)
+  for (int i = 0; i < 3; ++i) {
     if (c->pivots[i]) cudaFree(c->pivots[i]);
+    for (int m = 0; m < 2 * adi::kMaxP; ++m)
+      if (c->stiff_fac[i][m]) cudaFree(c->stiff_fac[i][m]);
+  }
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }

@@ -122,6 +122,10 @@ struct LineJob {
   const T* aux2;  // STIFF: inverse pivots of M + c S from an LM_PIVOT pass
   T scale;        // DERIV: dst += scale * M^-1 A src
   int dirichlet;  // 1: first and last coefficient are fixed to zero
+  T* work;        // DERIV along y / z: the forward sweep's intermediate (an array in the state layout)
+  // PIVOT: also store the row factors of M + c S for the streaming stiffness solve
+  // (fac[m-1] = multiplier of row k-m, fac[P+e-1] = upper factor e / pivot), or NULL
+  T* fac[2 * kMaxP];
 };
 template <typename T>
 struct LineJobs {
@@ -143,6 +147,7 @@ struct Ctx {
   int mixed_refine = 0;           // MIXED: one FP64 residual refinement per E half step
   int use_graph = 1;
   int line_tile = 0;  // lines per line-solve CTA (0: largest that leaves two CTAs per SM)
+  bool line_stream = true;  // y / z stiffness solves on the streaming kernel (precomputed factors)
   double dt = 0.0;
   size_t Nc = 0;      // coefficients per component (N_x N_y N_z)
   int pitch = 0;      // device row pitch in elements: N_x rounded up to a multiple of 4
@@ -172,6 +177,10 @@ struct Ctx {
   void* coef[4] = {};   // a, b, c, d
   void* stage = nullptr;  // Nc doubles for host transfers (FP32 mode)
   void* pivots[3] = {};   // inverse pivots of the row-scaled M + c S, per stiffness axis
+  // LU factors of the row-scaled M + c S along y and z ([axis][m]: P multipliers,
+  // then P normalised upper factors), computed with the pivots; the streaming
+  // y / z stiffness solves read them instead of refactoring every step
+  void* stiff_fac[3][2 * kMaxP] = {};
 
   // 1D tables on device (element type T)
   void* tab = nullptr;

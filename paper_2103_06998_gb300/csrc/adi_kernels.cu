@@ -32,6 +32,15 @@ namespace {
 
 unsigned grid_for(long long n, int threads);
 
+// Does the tile [x0, x0+tx) x [y0, y0+ty) x [z0, z0+tz) hold a coefficient of the
+// point source's support i0 .. i0 + p (per axis)?  Only such tiles evaluate the
+// source's time profile (sin and exp in FP64).
+__device__ __forceinline__ bool src_in_tile(const int (&i0)[3], int p, int x0, int y0, int z0, int tx, int ty,
+                                            int tz) {
+  return i0[0] <= x0 + tx - 1 && i0[0] + p >= x0 && i0[1] <= y0 + ty - 1 && i0[1] + p >= y0 &&
+         i0[2] <= z0 + tz - 1 && i0[2] + p >= z0;
+}
+
 // ------------------------------------------------------------------ RHS
 template <typename T, int P, int TX, int TY, int TZ>
 __global__ void __launch_bounds__(TX* TY) rhs_kernel(const RhsParams<T> prm) {
@@ -147,9 +156,10 @@ __global__ void __launch_bounds__(TX* TY) rhs_kernel(const RhsParams<T> prm) {
     }
   }
 
-  // point source: -b amp g(t_mid) B_r(x0) B_s(y0) B_t(z0) on its component
+  // point source: -b amp g(t_mid) B_r(x0) B_s(y0) B_t(z0) on its component;
+  // g is evaluated only by tiles that hold the source's (p+1)^3 support
   double g = 0.0;
-  if (prm.src_comp >= 0) {
+  if (prm.src_comp >= 0 && src_in_tile(prm.src_i0, P, x0, y0, z0, TX, TY, TZ)) {
     double tm = *prm.clock_t0 + ((double)*prm.clock_step + prm.t_frac) * prm.tau;
     double u = tm - prm.src_t0;
     g = prm.src_amp * sin(2.0 * 3.14159265358979323846 * prm.src_f0 * u) * exp(-(u / prm.src_s) * (u / prm.src_s));
@@ -294,7 +304,7 @@ __global__ void __launch_bounds__(256) resid_kernel(const ResidParams prm) {
     }
   }
   double g = 0.0;
-  if (prm.src_comp >= 0) {
+  if (prm.src_comp >= 0 && src_in_tile(prm.src_i0, P, x0, y0, z0, TX, TY, TZ)) {
     const double tmid = *prm.clock_t0 + ((double)*prm.clock_step + prm.t_frac) * prm.tau;
     const double u = tmid - prm.src_t0;
     g = prm.src_amp * sin(2.0 * 3.14159265358979323846 * prm.src_f0 * u) * exp(-(u / prm.src_s) * (u / prm.src_s));
@@ -457,6 +467,10 @@ __global__ void __launch_bounds__(64) line_kernel(const LineJobs<T> jobs, const 
   if (t < cnt) {
     const int lo = dch ? 1 : 0, hi = dch ? N - 2 : N - 1;
     T* col = sr + t;
+    const long long gfac = XDIR ? (long long)(L0 + t) * lp.pitch : off;  // this line in the state layout
+    const long long sfac = XDIR ? 1 : stride;
+    (void)gfac;
+    (void)sfac;
     if (FACT) {
       T Uq[P][P + 1], invq[P], yq[P];
 #pragma unroll
@@ -502,6 +516,13 @@ __global__ void __launch_bounds__(64) line_kernel(const LineJobs<T> jobs, const 
         if (MODE == LM_PIVOT) {
           inv = fast_rcp(Un[0]);
           col[k * LP] = inv;
+          if (job.fac[0]) {  // row factors for the streaming stiffness solve
+            const long long g = gfac + k * sfac;
+#pragma unroll
+            for (int q = 1; q <= P; ++q) job.fac[q - 1][g] = l[q];
+#pragma unroll
+            for (int e = 1; e <= P; ++e) job.fac[P + e - 1][g] = Un[e] * inv;
+          }
         } else {
           inv = ik;
           T y = rk;
@@ -737,6 +758,251 @@ __global__ void __launch_bounds__(64) line_kernel(const LineJobs<T> jobs, const 
       g += stride;
       s += LP;
     }
+  }
+}
+
+// Streaming banded solves along y or z (Appendix, eqs. split1/split2): one
+// thread per line, consecutive threads on consecutive x, so every row of a warp
+// is one coalesced access; nothing is staged in shared memory, and the warps of
+// a whole launch are resident at once.  The forward sweep writes y to dst (DERIV:
+// to job.work) and the backward sweep reads it back through the L2.  Loads of
+// the next block of rows are issued before the stores of the current block.
+//   LM_MASS : dst = M^-1 src (precomputed mass LU; mid-line rows use constants).
+//   LM_DERIV: dst += scale * M^-1 (A src)  (red.global.add).
+//   LM_STIFF: dst = (M + diag(c) S)^-1 src with the row factors precomputed per
+//             dt by the LM_PIVOT pass (job.fac: multipliers, normalised upper
+//             factors; job.aux2: inverse pivots).
+template <typename T, int P, int MODE>
+__global__ void __launch_bounds__(128) line_direct_kernel(const LineJobs<T> jobs, const LineParams lp,
+                                                          const AxisDev<T> ax) {
+  constexpr int W = 2 * P + 1;
+  constexpr int B = 8;  // rows per block of loads
+  const LineJob<T> job = blockIdx.y == 0 ? jobs.job[0] : (blockIdx.y == 1 ? jobs.job[1] : jobs.job[2]);
+  const long long L = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (L >= lp.nlines) return;
+  long long off, stride;
+  if (lp.dir == 1) {  // line L = z * N_x + x
+    off = (L / lp.Nx) * (long long)lp.pitch * lp.Ny + (L % lp.Nx);
+    stride = lp.pitch;
+  } else {            // line L = y * N_x + x
+    off = (L / lp.Nx) * (long long)lp.pitch + (L % lp.Nx);
+    stride = (long long)lp.pitch * lp.Ny;
+  }
+  const int N = lp.N;
+  const int dch = job.dirichlet;
+  const int lo = dch ? 1 : 0, hi = dch ? N - 2 : N - 1;
+  const int f = dch ? 1 : 0;
+  const T* src = job.src + off;  // may alias dst (in-place solves)
+  T* yv = (MODE == LM_DERIV ? job.work : job.dst) + off;
+
+  // ---- forward sweep
+  T yq[P];
+#pragma unroll
+  for (int m = 0; m < P; ++m) yq[m] = T(0);
+  T win[W];  // DERIV: u[k-P .. k+P]
+  if (MODE == LM_DERIV) {
+#pragma unroll
+    for (int d = 0; d < W; ++d) {
+      const int j = lo + d - P;
+      win[d] = (j >= 0 && j < N) ? src[j * stride] : T(0);
+    }
+  }
+  // right-hand side of row k: r[k] (MASS, STIFF) or u[k+P+1] (DERIV, window feed)
+  auto ld = [&](int k) -> T {
+    if (MODE == LM_DERIV) {
+      const int j = k + P + 1;
+      return j < N ? src[j * stride] : T(0);
+    }
+    return src[k * stride];
+  };
+  // one forward row; cst: mid-line constants (MASS, DERIV); lk: STIFF multipliers
+  auto fwd = [&](int k, bool cst, T rk, const T* lk) {
+    T y;
+    if (MODE == LM_DERIV) {
+      y = T(0);
+#pragma unroll
+      for (int d = 0; d < W; ++d) y += (cst ? ax.inner[OP_A][d] : ax.band[OP_A][k * W + d]) * win[d];
+#pragma unroll
+      for (int d = 0; d < W - 1; ++d) win[d] = win[d + 1];
+      win[W - 1] = rk;
+    } else {
+      y = rk;
+    }
+#pragma unroll
+    for (int m = 1; m <= P; ++m) {
+      T lm;
+      if (MODE == LM_STIFF) lm = lk[m - 1];
+      else lm = cst ? ax.luc[f][m - 1] : ax.luL[f][k * P + m - 1];
+      y -= lm * yq[m - 1];
+    }
+    yv[k * stride] = y;
+#pragma unroll
+    for (int m = P - 1; m >= 1; --m) yq[m] = yq[m - 1];
+    yq[0] = y;
+  };
+  if (MODE == LM_STIFF) {
+    int k = lo;
+    if (k + B - 1 <= hi) {  // blocks of rows; the next block's loads precede this block's stores
+      T rr[B], ll[B][P], rn[B], ln[B][P];
+#pragma unroll
+      for (int u = 0; u < B; ++u) {
+        rr[u] = src[(k + u) * stride];
+#pragma unroll
+        for (int m = 0; m < P; ++m) ll[u][m] = job.fac[m][off + (k + u) * stride];
+      }
+      for (; k + B - 1 <= hi; k += B) {
+        const bool more = k + 2 * B - 1 <= hi;
+        if (more) {
+#pragma unroll
+          for (int u = 0; u < B; ++u) {
+            rn[u] = src[(k + B + u) * stride];
+#pragma unroll
+            for (int m = 0; m < P; ++m) ln[u][m] = job.fac[m][off + (k + B + u) * stride];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < B; ++u) fwd(k + u, false, rr[u], ll[u]);
+        if (more) {
+#pragma unroll
+          for (int u = 0; u < B; ++u) {
+            rr[u] = rn[u];
+#pragma unroll
+            for (int m = 0; m < P; ++m) ll[u][m] = ln[u][m];
+          }
+        }
+      }
+    }
+    for (; k <= hi; ++k) {
+      T lk[P];
+#pragma unroll
+      for (int m = 0; m < P; ++m) lk[m] = job.fac[m][off + k * stride];
+      fwd(k, false, src[k * stride], lk);
+    }
+  } else {
+    int c0 = max(lo, ax.lu_lo[f]), c1 = min(hi, ax.lu_hi[f]);
+    if (MODE == LM_DERIV) {
+      c0 = max(c0, ax.inner_lo);
+      c1 = min(c1, ax.inner_hi);
+    }
+    int k = lo;
+    for (; k < c0 && k <= hi; ++k) fwd(k, false, ld(k), nullptr);
+    if (k + B - 1 <= c1) {  // constant rows: the next block's loads precede this block's stores
+      T cur[B], nxt[B];
+#pragma unroll
+      for (int u = 0; u < B; ++u) cur[u] = ld(k + u);
+      for (; k + B - 1 <= c1; k += B) {
+        const bool more = k + 2 * B - 1 <= c1;
+        if (more) {
+#pragma unroll
+          for (int u = 0; u < B; ++u) nxt[u] = ld(k + B + u);
+        }
+#pragma unroll
+        for (int u = 0; u < B; ++u) fwd(k + u, true, cur[u], nullptr);
+        if (more) {
+#pragma unroll
+          for (int u = 0; u < B; ++u) cur[u] = nxt[u];
+        }
+      }
+    }
+    for (; k <= c1; ++k) fwd(k, true, ld(k), nullptr);
+    for (; k <= hi; ++k) fwd(k, false, ld(k), nullptr);
+  }
+
+  // ---- backward sweep
+  T xq[P];
+#pragma unroll
+  for (int m = 0; m < P; ++m) xq[m] = T(0);
+  const T scale = job.scale;
+  T* out = job.dst + off;
+  auto bwd = [&](int k, bool cst, T yk, T ik, const T* uk) {
+    T x;
+    if (MODE == LM_STIFF) {
+      x = ik * yk;
+#pragma unroll
+      for (int e = 1; e <= P; ++e) x -= uk[e - 1] * xq[e - 1];
+    } else {
+      x = (cst ? ax.luc[f][P] : ax.luInv[f][k]) * yk;
+#pragma unroll
+      for (int e = 1; e <= P; ++e) x -= (cst ? ax.luc[f][P + e] : ax.luU[f][k * P + e - 1]) * xq[e - 1];
+    }
+    if (MODE == LM_DERIV) red_add(out + k * stride, scale * x);
+    else out[k * stride] = x;
+#pragma unroll
+    for (int m = P - 1; m >= 1; --m) xq[m] = xq[m - 1];
+    xq[0] = x;
+  };
+  if (MODE == LM_STIFF) {
+    int k = hi;
+    if (k - B + 1 >= lo) {
+      T yy[B], ii[B], uu[B][P], yn[B], in_[B], un[B][P];
+#pragma unroll
+      for (int u = 0; u < B; ++u) {
+        const long long g = off + (k - u) * stride;
+        yy[u] = yv[(k - u) * stride];
+        ii[u] = job.aux2[g];
+#pragma unroll
+        for (int e = 0; e < P; ++e) uu[u][e] = job.fac[P + e][g];
+      }
+      for (; k - B + 1 >= lo; k -= B) {
+        const bool more = k - 2 * B + 1 >= lo;
+        if (more) {
+#pragma unroll
+          for (int u = 0; u < B; ++u) {
+            const long long g = off + (k - B - u) * stride;
+            yn[u] = yv[(k - B - u) * stride];
+            in_[u] = job.aux2[g];
+#pragma unroll
+            for (int e = 0; e < P; ++e) un[u][e] = job.fac[P + e][g];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < B; ++u) bwd(k - u, false, yy[u], ii[u], uu[u]);
+        if (more) {
+#pragma unroll
+          for (int u = 0; u < B; ++u) {
+            yy[u] = yn[u];
+            ii[u] = in_[u];
+#pragma unroll
+            for (int e = 0; e < P; ++e) uu[u][e] = un[u][e];
+          }
+        }
+      }
+    }
+    for (; k >= lo; --k) {
+      const long long g = off + k * stride;
+      T uk[P];
+#pragma unroll
+      for (int e = 0; e < P; ++e) uk[e] = job.fac[P + e][g];
+      bwd(k, false, yv[k * stride], job.aux2[g], uk);
+    }
+  } else {
+    const int b0 = max(lo, ax.lu_lo[f]), b1 = min(hi, ax.lu_hi[f]);
+    int k = hi;
+    for (; k > b1; --k) bwd(k, false, yv[k * stride], T(0), nullptr);
+    if (k - B + 1 >= b0) {
+      T cur[B], nxt[B];
+#pragma unroll
+      for (int u = 0; u < B; ++u) cur[u] = yv[(k - u) * stride];
+      for (; k - B + 1 >= b0; k -= B) {
+        const bool more = k - 2 * B + 1 >= b0;
+        if (more) {
+#pragma unroll
+          for (int u = 0; u < B; ++u) nxt[u] = yv[(k - B - u) * stride];
+        }
+#pragma unroll
+        for (int u = 0; u < B; ++u) bwd(k - u, true, cur[u], T(0), nullptr);
+        if (more) {
+#pragma unroll
+          for (int u = 0; u < B; ++u) cur[u] = nxt[u];
+        }
+      }
+    }
+    for (; k >= b0; --k) bwd(k, true, yv[k * stride], T(0), nullptr);
+    for (; k >= lo; --k) bwd(k, false, yv[k * stride], T(0), nullptr);
+  }
+  if (MODE != LM_DERIV && dch) {  // fixed coefficients
+    out[0] = T(0);
+    out[(N - 1) * stride] = T(0);
   }
 }
 
@@ -1042,9 +1308,9 @@ __global__ void __launch_bounds__(rhs2::NT, sizeof(T) == 4 ? ADI_RHS_MINB : 1)
     return;
   }
 
-  // ---- point source and store (two consecutive x per row)
+  // ---- point source (only tiles holding its support evaluate g) and store
   double g = 0.0;
-  if (prm.src_comp >= 0) {
+  if (prm.src_comp >= 0 && src_in_tile(prm.src_i0, P, x0, y0, z0, TX, TY, TZ)) {
     double tm = *prm.clock_t0 + ((double)*prm.clock_step + prm.t_frac) * prm.tau;
     double u = tm - prm.src_t0;
     g = prm.src_amp * sin(2.0 * 3.14159265358979323846 * prm.src_f0 * u) * exp(-(u / prm.src_s) * (u / prm.src_s));
@@ -1475,6 +1741,23 @@ cudaError_t launch_line(Ctx& c, int dir, int mode, const LineJobs<T>& jobs, int 
   lp.Nz = c.N[2];
   lp.pitch = c.pitch;
   lp.nlines = (long long)c.N[0] * c.N[1] * c.N[2] / c.N[dir];
+  const double per_job = (double)c.Nc * sizeof(T) *
+                         (mode == LM_MASS || mode == LM_PIVOT ? 2.0 : (mode == LM_STIFF ? 4.0 : 3.0));
+  // y and z stiffness lines: the streaming kernel with precomputed factors (no
+  // shared memory).  Mass and derivative lines stay on the staged kernel: their
+  // streaming forms measured slower (the forward sweep's intermediate of a whole
+  // launch, 1 KB per line, does not stay in L2 for the backward sweep).
+  const bool stream_ok = dir != 0 && mode == LM_STIFF && jobs.job[0].fac[0] != nullptr && c.line_stream;
+  if (stream_ok) {
+    const AxisDev<T> axs = axis_dev<T>(c, dir);
+    dim3 g2((unsigned)((lp.nlines + 127) / 128), njobs);
+    prof_begin(c, name, per_job * njobs);
+    if (mode == LM_STIFF) line_direct_kernel<T, P, LM_STIFF><<<g2, 128, 0, c.stream>>>(jobs, lp, axs);
+    else if (mode == LM_DERIV) line_direct_kernel<T, P, LM_DERIV><<<g2, 128, 0, c.stream>>>(jobs, lp, axs);
+    else line_direct_kernel<T, P, LM_MASS><<<g2, 128, 0, c.stream>>>(jobs, lp, axs);
+    prof_end(c);
+    return cudaGetLastError();
+  }
   const int W = 2 * P + 1;
   const bool fact = mode == LM_STIFF || mode == LM_PIVOT;
   const int tabw = fact ? 2 * W : (mode == LM_DERIV ? 3 * P + 1 + W : 3 * P + 1);
@@ -1492,7 +1775,6 @@ cudaError_t launch_line(Ctx& c, int dir, int mode, const LineJobs<T>& jobs, int 
   if (smem_for(lines) > limit) return cudaErrorInvalidValue;
   size_t smem = smem_for(lines);
   long long blocks = (lp.nlines + lines - 1) / lines;
-  double per_job = (double)c.Nc * sizeof(T) * (mode == LM_MASS || mode == LM_PIVOT ? 2.0 : (mode == LM_STIFF ? 4.0 : 3.0));
   prof_begin(c, name, per_job * njobs);
   dim3 grid((unsigned)blocks, njobs);
   const AxisDev<T> ax = axis_dev<T>(c, dir);
@@ -1523,6 +1805,8 @@ LineJob<T> job_of(const T* src, T* dst, const T* aux, double scale, int dirichle
   j.aux2 = aux2;
   j.scale = T(scale);
   j.dirichlet = dirichlet;
+  j.work = nullptr;
+  for (int m = 0; m < 2 * kMaxP; ++m) j.fac[m] = nullptr;
   return j;
 }
 
@@ -1542,6 +1826,7 @@ cudaError_t e_solve(Ctx& c, int half, T* const* R, T* const* out) {
     const int sd = kStiffDir[half - 1][i];
     LineJobs<T> js{};
     js.job[0] = job_of<T>(R[i], R[i], cf[2], 0.0, 1, reinterpret_cast<const T*>(c.pivots[sd]));
+    for (int m = 0; m < 2 * P; ++m) js.job[0].fac[m] = reinterpret_cast<T*>(c.stiff_fac[sd][m]);
     e = launch_line<T, P>(c, sd, LM_STIFF, js, 1, stiff_name[sd]);
     if (e != cudaSuccess) return e;
     int md[2], m = 0;
@@ -1745,9 +2030,12 @@ cudaError_t h_substep_uniform(Ctx& c, int half) {
   T* const* Ea = cur;     // alpha: E^n (half 1) or E^{n+1} (half 2)
   T* const* Eb = hlf;     // beta:  E^{n+1/2}
   const double d = c.d_uniform;
+  T** R = reinterpret_cast<T**>(c.rhs);  // free during the H half step: intermediates of y / z passes
   LineJobs<T> js{};
   js.job[0] = job_of<T>(Eb[1], H[0], nullptr, d, 0);
   js.job[1] = job_of<T>(Ea[0], H[1], nullptr, -d, 0);
+  js.job[0].work = R[0];
+  js.job[1].work = R[1];
   cudaError_t e = launch_line<T, P>(c, 2, LM_DERIV, js, 2, "line_z_deriv");
   if (e != cudaSuccess) return e;
   js.job[0] = job_of<T>(Eb[2], H[1], nullptr, d, 0);
@@ -1756,6 +2044,8 @@ cudaError_t h_substep_uniform(Ctx& c, int half) {
   if (e != cudaSuccess) return e;
   js.job[0] = job_of<T>(Ea[2], H[0], nullptr, -d, 0);
   js.job[1] = job_of<T>(Eb[0], H[2], nullptr, d, 0);
+  js.job[0].work = R[0];
+  js.job[1].work = R[1];
   e = launch_line<T, P>(c, 1, LM_DERIV, js, 2, "line_y_deriv");
   if (e != cudaSuccess) return e;
   if (half == 2) e = advance_clock(c);
@@ -1781,6 +2071,17 @@ cudaError_t pivots_tp(Ctx& c) {
     }
     LineJobs<T> js{};
     js.job[0] = job_of<T>(nullptr, reinterpret_cast<T*>(c.pivots[d]), cf[2], 0.0, 1);
+    if (d > 0) {  // y and z: the streaming stiffness solve reads the row factors
+      for (int m = 0; m < 2 * P; ++m) {
+        if (!c.stiff_fac[d][m]) {
+          cudaError_t e = cudaMalloc(&c.stiff_fac[d][m], c.Np * sizeof(T));
+          if (e != cudaSuccess) return e;
+          e = cudaMemsetAsync(c.stiff_fac[d][m], 0, c.Np * sizeof(T), c.stream);
+          if (e != cudaSuccess) return e;
+        }
+        js.job[0].fac[m] = reinterpret_cast<T*>(c.stiff_fac[d][m]);
+      }
+    }
     cudaError_t e = launch_line<T, P>(c, d, LM_PIVOT, js, 1, name[d]);
     if (e != cudaSuccess) return e;
   }

@@ -35,7 +35,7 @@ constexpr int kTY = 4;                    // x-lines (y rows) per convolution bl
 constexpr int kXBMax = 130;               // widest x segment of a block
 constexpr int kConvThreads = 256;
 constexpr int kWgThreads = 288;
-constexpr int kTmemCols = 256;
+constexpr int kTmemCols = 512;  // two accumulator buffers of 256 columns
 
 constexpr long long w_off(int l) {
   return l == 0 ? 0 : w_off(l - 1) + 27LL * kCI[l - 1] * kCO[l - 1] + kCO[l - 1];
@@ -239,32 +239,43 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv_kernel(const ConvArgs a)
     cp_commit();
   };
 
+  // MMAs of one block into accumulator buffer `buf` (two buffers of 256 columns):
+  // descriptors are built once and stepped by 16-byte units (rows); the start
+  // address field never leaves [0, 2^14) because every operand lies in the CTA's
+  // shared memory.
+  const uint64_t a_desc0 = sdesc(sA32 + (uint32_t)(g.rs * 16), (uint32_t)g.rows * 16u, 128u);
+  const uint64_t b_desc0 = sdesc(sW32, COUT * 16u, 128u);
+  auto issue = [&](uint32_t buf) {
+    tc_fence_after();
+    const int oy = g.Xh, oz = g.Xh * g.Yh;
+    for (int j = 0; j < g.ntiles; ++j) {
+      const uint32_t d = tmem + buf * 256u + (uint32_t)(j * COUT);
+      const uint64_t aj = a_desc0 + (uint64_t)(128 * j);
+#pragma unroll
+      for (int tap = 0; tap < 27; ++tap) {
+        const int off = (tap % 3 - 1) + oy * ((tap / 3) % 3 - 1) + oz * (tap / 9 - 1);
+#pragma unroll
+        for (int ks = 0; ks < CIN / 16; ++ks)
+          mma_bf16(d, aj + (uint64_t)(int64_t)(off + 2 * ks * g.rows),
+                   b_desc0 + (uint64_t)((tap * CH + 2 * ks) * COUT), IDESC, (tap | ks) != 0 ? 1u : 0u);
+      }
+    }
+    mma_commit(bar);
+  };
+
   uint32_t phase = 0;
   bool failed = false;
   int b = blockIdx.x;
-  if (b < g.nblocks) load_block(b);
-  while (b < g.nblocks) {
+  uint32_t it = 0;
+  if (b < g.nblocks) {
+    load_block(b);
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncthreads();
-    if (tid == 0) {
-      tc_fence_after();
-      for (int j = 0; j < g.ntiles; ++j) {
-        for (int tap = 0; tap < 27; ++tap) {
-          const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
-          const int off = (dx - 1) + g.Xh * ((dy - 1) + g.Yh * (dz - 1));
-          const int row0 = g.rs + 128 * j + off;
-#pragma unroll
-          for (int ks = 0; ks < CIN / 16; ++ks) {
-            const uint64_t ad = sdesc(sA32 + (uint32_t)((2 * ks * g.rows + row0) * 16), (uint32_t)g.rows * 16u, 128u);
-            const uint64_t bd = sdesc(sW32 + (uint32_t)((tap * CH + 2 * ks) * COUT * 16), COUT * 16u, 128u);
-            mma_bf16(tmem + (uint32_t)(j * COUT), ad, bd, IDESC, (tap | ks) != 0);
-          }
-        }
-      }
-      mma_commit(bar);
-    }
-    const bool ok = mbar_wait(bar, phase);
+    if (tid == 0) issue(0u);
+  }
+  while (b < g.nblocks) {
+    const bool ok = mbar_wait(bar, phase);  // MMAs of block b done: its staged inputs are free
     phase ^= 1u;
     if (!__syncthreads_and(ok)) {
       failed = true;
@@ -272,10 +283,19 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv_kernel(const ConvArgs a)
     }
     tc_fence_after();
     const int cur = b;
+    const uint32_t cur_buf = it & 1u;
     b += gridDim.x;
-    if (b < g.nblocks) load_block(b);  // the MMAs are done with the staged block
+    ++it;
+    if (b < g.nblocks) {  // stage the next block and start its MMAs in the other buffer
+      load_block(b);
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      tc_fence_before();
+      __syncthreads();
+      if (tid == 0) issue(it & 1u);
+    }
 
-    // epilogue of block `cur`
+    // epilogue of block `cur` (overlaps the MMAs of the next block)
     const int seg = cur % g.nseg;
     const int t = cur / g.nseg;
     const int y0 = (t % g.nyb) * kTY;
@@ -284,8 +304,9 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv_kernel(const ConvArgs a)
     const int q = warp & 3;
     for (int j = warp >> 2; j < g.ntiles; j += 2) {
       uint32_t r[32];
-      if (COUT == 32) tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(j * COUT), r);
-      else tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(j * COUT), r);
+      const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + cur_buf * 256u + (uint32_t)(j * COUT);
+      if (COUT == 32) tmem_ld32(taddr, r);
+      else tmem_ld16(taddr, r);
       tmem_wait_ld();
       const int row = g.rs + 128 * j + 32 * q + lane;
       const int zh = row / (g.Xh * g.Yh);
