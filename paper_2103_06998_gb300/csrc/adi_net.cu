@@ -4,15 +4,16 @@
 // definitions in the header.
 //
 // Convolutions (forward and input gradient) are implicit GEMMs on the 5th
-// generation tensor cores: per CTA a block of TY x-lines (one z plane) is
-// staged in shared memory in the no-swizzle K-major core-matrix layout
-// ([8-channel chunk][row] with 16-byte rows, row = haloed voxel), and for each
-// of the 27 taps a 128-row slice of that block -- the rows shifted by the
-// tap's linear offset -- is the A operand of tcgen05.mma (M = 128 voxels,
-// N = output channels, K = 16 input channels per instruction).  Accumulators
-// live in tensor memory and are read back with tcgen05.ld for the epilogue
-// (bias + ReLU, ReLU-mask, or FP32 output).  Weight gradients are reductions
-// over all voxels and run on the CUDA cores.
+// generation tensor cores.  A CTA owns a work unit (x segment, 2 y lines, a chunk
+// of z planes) and marches along z: each haloed z plane is one slot of a 4-slot
+// ring in shared memory, loaded by 5D TMA boxes straight into the no-swizzle
+// K-major core-matrix layout ([8-channel chunk][voxel row], 16-byte rows); for
+// each of the 27 taps the A operand of tcgen05.mma is the slot of plane z+dz-1
+// with its rows shifted by the tap's in-plane offset (M = 128 voxels, N = output
+// channels, K = 16 channels per instruction).  Warp 0 issues loads and MMAs
+// into two tensor-memory accumulator buffers; warps 4..7 read them back with
+// tcgen05.ld for the fused epilogue (bias + ReLU, ReLU mask, or FP32 output).
+// Weight gradients are reductions over all voxels on the CUDA cores.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -54,7 +55,6 @@ __device__ __forceinline__ void cp16(uint32_t dst, const void* src, int bytes) {
 __device__ __forceinline__ void cp_commit_wait() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 
 // Shared-memory matrix descriptor of tcgen05 (no swizzle): start address,
 // leading byte offset (between core matrices adjacent along K), stride byte
@@ -176,186 +176,264 @@ template <int CIN, int COUT>
 __host__ __device__ constexpr size_t conv_wbytes() {
   return 27ull * CIN * COUT * 2;
 }
+
+// Plane-ring geometry of the convolutions.  A work unit is (x segment, 2
+// consecutive y, a chunk of z); the CTA marches along z.  Each z plane of the
+// unit's haloed (X_b+2) x 4 voxel window is one ring slot in shared memory:
+// CIN/8 chunk planes of RS rows of 16 bytes (8 channels), row = xh + Xh yh,
+// exactly the box a 5D TMA load writes.  Output rows are rs .. rs+128 nt-1 of
+// a slot; tap (dz, dy, dx) reads plane z+dz-1 at row offset (dx-1) + Xh (dy-1).
+constexpr int kRTY = 2;     // y lines per unit
+constexpr int kSlots = 4;   // planes z-1, z, z+1 in use, z+2 loading
+struct Ring {
+  int X, Y, Z;
+  int XB, nseg, nyb, nzc, zc, units;
+  int Xh, Yh, rs, ntiles, RS;
+};
+
+inline Ring make_ring(int X, int Y, int Z, int sms) {
+  Ring r{};
+  r.X = X;
+  r.Y = Y;
+  r.Z = Z;
+  r.nseg = (X + kXBMax - 1) / kXBMax;
+  r.XB = (X + r.nseg - 1) / r.nseg;
+  r.nyb = (Y + kRTY - 1) / kRTY;
+  r.Xh = r.XB + 2;
+  r.Yh = kRTY + 2;
+  r.rs = 1 + r.Xh;
+  const int count = r.XB + r.Xh * (kRTY - 1);
+  r.ntiles = (count + 127) / 128;
+  r.RS = ((r.rs + 128 * r.ntiles + r.Xh + 1) + 7) / 8 * 8;  // 128-byte aligned chunk planes
+  const int cols = r.nseg * r.nyb;
+  int nzc = (8 * sms + cols - 1) / cols;  // about eight units per SM: a short last wave
+  if (nzc < 1) nzc = 1;
+  if (nzc > Z) nzc = Z;
+  r.zc = (Z + nzc - 1) / nzc;
+  r.nzc = (Z + r.zc - 1) / r.zc;
+  r.units = cols * r.nzc;
+  return r;
+}
 template <int CIN, int COUT>
-inline size_t conv_smem(const Geom& g) {
-  return 2048 + conv_wbytes<CIN, COUT>() + (size_t)(CIN / 8) * g.rows * 16;
+inline size_t ring_smem(const Ring& r) {  // worst-case alignment of the base and of the slots included
+  return 3072 + conv_wbytes<CIN, COUT>() + (size_t)kSlots * (CIN / 8) * r.RS * 16;
 }
 
 struct ConvArgs {
-  const bf16* in;     // [V][CIN]
   const bf16* w;      // packed [27][CIN/8][COUT][8]
   const float* bias;  // [COUT] (RELU, LINEAR)
   const bf16* mask;   // [V][COUT] (MASK): output kept where mask > 0
   void* out;          // bf16 [V][COUT] (RELU, MASK) or float [V][8] (LINEAR)
-  Geom g;
+  Ring r;
   int* err;
 };
 
+// 5D TMA load of one chunk plane: box (8 channels, 1 chunk, Xh, Yh, 1 plane)
+__device__ __forceinline__ void tma_plane(const CUtensorMap* map, uint32_t dst, uint64_t* bar, int c, int x, int y,
+                                          int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], "
+      "[%7];\n" ::"r"(dst),
+      "l"(map), "r"(0), "r"(c), "r"(x), "r"(y), "r"(z), "r"(su32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(su32(bar)), "r"(bytes) : "memory");
+}
+
+// Warp-specialised: warp 0 is the producer (lane 0 issues the TMA plane loads
+// and the MMAs of each output plane into one of two tensor-memory accumulator
+// buffers), warps 4..7 are the consumers (epilogue, one tensor-memory lane
+// quarter each).  Hand-offs use mbarriers only: plane loaded (per slot), MMAs of
+// a buffer done (tcgen05.commit), buffer read out (4 consumer arrivals).
 template <int CIN, int COUT, int EPI>
-__global__ void __launch_bounds__(kConvThreads, 1) conv_kernel(const ConvArgs a) {
+__global__ void __launch_bounds__(kConvThreads, 1) conv_kernel(const ConvArgs a, const __grid_constant__ CUtensorMap map) {
   constexpr int CH = CIN / 8;
   constexpr uint32_t IDESC = idesc_bf16_m128<COUT>();
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(base);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(base + 64);
+  uint64_t* lbar = reinterpret_cast<uint64_t*>(base);        // [kSlots] plane loaded
+  uint64_t* done = reinterpret_cast<uint64_t*>(base + 64);   // [2] MMAs of a buffer complete
+  uint64_t* freed = reinterpret_cast<uint64_t*>(base + 96);  // [2] buffer read out by the consumers
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(base + 128);
   uint8_t* sW = base + 1024;
-  uint8_t* sA = sW + conv_wbytes<CIN, COUT>();
+  uint8_t* sA = base + ((1024 + conv_wbytes<CIN, COUT>() + 1023) & ~(size_t)1023);
   const uint32_t sW32 = su32(sW), sA32 = su32(sA);
-  const Geom& g = a.g;
+  const Ring& g = a.r;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t slot_bytes = (uint32_t)(CH * g.RS * 16);
+  const uint32_t plane_tx = (uint32_t)(CH * g.Xh * g.Yh * 16);
 
   if (warp == 0) tmem_alloc(tslot);
-  if (tid == 0) mbar_init(bar);
-  // weights: a flat copy (the global array is already in the shared layout)
+  if (tid == 0) {
+    for (int s = 0; s < kSlots; ++s) mbar_init(&lbar[s]);
+    mbar_init(&done[0]);
+    mbar_init(&done[1]);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;\n" ::"r"(su32(&freed[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;\n" ::"r"(su32(&freed[1])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
   for (int i = tid; i < (int)(conv_wbytes<CIN, COUT>() / 16); i += kConvThreads)
     cp16(sW32 + 16 * i, reinterpret_cast<const uint8_t*>(a.w) + 16 * (size_t)i, 16);
-  cp_commit();
+  cp_commit_wait();
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // weights: generic writes, tensor-core reads
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
+  const int cols = g.nseg * g.nyb;
 
-  auto load_block = [&](int b) {
-    const int seg = b % g.nseg;
-    const int t = b / g.nseg;
-    const int y0 = (t % g.nyb) * kTY;
-    const int z0 = t / g.nyb;
-    const int x0 = seg * g.XB;
-    for (int line = 0; line < 3 * g.Yh; ++line) {
-      const int zh = line / g.Yh, yh = line - zh * g.Yh;
-      const int z = z0 - 1 + zh, y = y0 - 1 + yh;
-      const bool lin = z >= 0 && z < g.Z && y >= 0 && y < g.Y;
-      const bf16* src_line = a.in + ((size_t)z * g.Y + y) * (size_t)g.X * CIN;
-      const int rowbase = g.Xh * (yh + g.Yh * zh);
-      for (int i = tid; i < g.Xh * CH; i += kConvThreads) {
-        const int xh = i / CH, c = i - xh * CH;
-        const int x = x0 - 1 + xh;
-        const bool ok = lin && x >= 0 && x < g.X;
-        const void* src = ok ? (const void*)(src_line + (size_t)x * CIN + 8 * c) : (const void*)a.in;
-        cp16(sA32 + (uint32_t)((c * g.rows + rowbase + xh) * 16), src, ok ? 16 : 0);
-      }
-    }
-    cp_commit();
-  };
-
-  // MMAs of one block into accumulator buffer `buf` (two buffers of 256 columns):
-  // descriptors are built once and stepped by 16-byte units (rows); the start
-  // address field never leaves [0, 2^14) because every operand lies in the CTA's
-  // shared memory.
-  const uint64_t a_desc0 = sdesc(sA32 + (uint32_t)(g.rs * 16), (uint32_t)g.rows * 16u, 128u);
-  const uint64_t b_desc0 = sdesc(sW32, COUT * 16u, 128u);
-  auto issue = [&](uint32_t buf) {
-    tc_fence_after();
-    const int oy = g.Xh, oz = g.Xh * g.Yh;
-    for (int j = 0; j < g.ntiles; ++j) {
-      const uint32_t d = tmem + buf * 256u + (uint32_t)(j * COUT);
-      const uint64_t aj = a_desc0 + (uint64_t)(128 * j);
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      uint32_t lph[kSlots] = {0u, 0u, 0u, 0u};
+      bool lpend[kSlots] = {false, false, false, false};
+      uint32_t dph[2] = {0u, 0u}, fph[2] = {0u, 0u};
+      bool used[2] = {false, false};
+      bool ok = true;
+      // A descriptor offsets (16-byte units) of the nine (dy, dx) taps and of tile j / step ks
+      int off9[9];
 #pragma unroll
-      for (int tap = 0; tap < 27; ++tap) {
-        const int off = (tap % 3 - 1) + oy * ((tap / 3) % 3 - 1) + oz * (tap / 9 - 1);
-#pragma unroll
-        for (int ks = 0; ks < CIN / 16; ++ks)
-          mma_bf16(d, aj + (uint64_t)(int64_t)(off + 2 * ks * g.rows),
-                   b_desc0 + (uint64_t)((tap * CH + 2 * ks) * COUT), IDESC, (tap | ks) != 0 ? 1u : 0u);
-      }
-    }
-    mma_commit(bar);
-  };
-
-  uint32_t phase = 0;
-  bool failed = false;
-  int b = blockIdx.x;
-  uint32_t it = 0;
-  if (b < g.nblocks) {
-    load_block(b);
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    __syncthreads();
-    if (tid == 0) issue(0u);
-  }
-  while (b < g.nblocks) {
-    const bool ok = mbar_wait(bar, phase);  // MMAs of block b done: its staged inputs are free
-    phase ^= 1u;
-    if (!__syncthreads_and(ok)) {
-      failed = true;
-      break;
-    }
-    tc_fence_after();
-    const int cur = b;
-    const uint32_t cur_buf = it & 1u;
-    b += gridDim.x;
-    ++it;
-    if (b < g.nblocks) {  // stage the next block and start its MMAs in the other buffer
-      load_block(b);
-      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-      tc_fence_before();
-      __syncthreads();
-      if (tid == 0) issue(it & 1u);
-    }
-
-    // epilogue of block `cur` (overlaps the MMAs of the next block)
-    const int seg = cur % g.nseg;
-    const int t = cur / g.nseg;
-    const int y0 = (t % g.nyb) * kTY;
-    const int z0 = t / g.nyb;
-    const int x0 = seg * g.XB;
-    const int q = warp & 3;
-    for (int j = warp >> 2; j < g.ntiles; j += 2) {
-      uint32_t r[32];
-      const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + cur_buf * 256u + (uint32_t)(j * COUT);
-      if (COUT == 32) tmem_ld32(taddr, r);
-      else tmem_ld16(taddr, r);
-      tmem_wait_ld();
-      const int row = g.rs + 128 * j + 32 * q + lane;
-      const int zh = row / (g.Xh * g.Yh);
-      const int rem = row - zh * g.Xh * g.Yh;
-      const int yh = rem / g.Xh, xh = rem - yh * g.Xh;
-      const int x = x0 + xh - 1, y = y0 + yh - 1;
-      const bool valid = zh == 1 && yh >= 1 && yh <= kTY && xh >= 1 && xh <= g.XB && x < g.X && y < g.Y;
-      if (!valid) continue;
-      const size_t v = ((size_t)z0 * g.Y + y) * g.X + x;
-      if (EPI == EPI_LINEAR) {
-        float o[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) o[c] = c < 6 ? __uint_as_float(r[c]) + a.bias[c] : 0.0f;
-        float4* dst = reinterpret_cast<float4*>(static_cast<float*>(a.out) + v * 8);
-        dst[0] = make_float4(o[0], o[1], o[2], o[3]);
-        dst[1] = make_float4(o[4], o[5], o[6], o[7]);
-      } else {
-        uint32_t pk[COUT / 2];
-        if (EPI == EPI_RELU) {
-#pragma unroll
-          for (int c = 0; c < COUT / 2; ++c)
-            pk[c] = pack_bf16(fmaxf(__uint_as_float(r[2 * c]) + a.bias[2 * c], 0.0f),
-                              fmaxf(__uint_as_float(r[2 * c + 1]) + a.bias[2 * c + 1], 0.0f));
-        } else {
-          const uint4* mk = reinterpret_cast<const uint4*>(a.mask + v * COUT);
-#pragma unroll
-          for (int c8 = 0; c8 < COUT / 8; ++c8) {
-            const uint4 m = mk[c8];
-            const uint32_t mw[4] = {m.x, m.y, m.z, m.w};
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              const int c = 8 * c8 + 2 * k;
-              pk[c / 2] = pack_bf16(bf_lo(mw[k]) > 0.0f ? __uint_as_float(r[c]) : 0.0f,
-                                    bf_hi(mw[k]) > 0.0f ? __uint_as_float(r[c + 1]) : 0.0f);
+      for (int t = 0; t < 9; ++t) off9[t] = g.rs + (t % 3 - 1) + g.Xh * (t / 3 - 1);
+      const uint64_t a0 = sdesc(sA32, (uint32_t)g.RS * 16u, 128u);
+      const uint64_t b0 = sdesc(sW32, COUT * 16u, 128u);
+      for (int u = blockIdx.x; u < g.units && ok; u += gridDim.x) {
+        const int col = u % cols, zi = u / cols;
+        const int x0 = (col % g.nseg) * g.XB, y0 = (col / g.nseg) * kRTY;
+        const int za = zi * g.zc, zb = min(g.Z, za + g.zc);
+        auto load = [&](int p) {
+          const int s = (p - za + 1) & 3;
+          lpend[s] = true;
+          mbar_expect(&lbar[s], plane_tx);
+          for (int c = 0; c < CH; ++c)
+            tma_plane(&map, sA32 + (uint32_t)s * slot_bytes + (uint32_t)(c * g.RS * 16), &lbar[s], c, x0 - 1, y0 - 1, p);
+        };
+        for (int p = za - 1; p <= min(za + 2, zb); ++p) load(p);
+        for (int z = za; z < zb && ok; ++z) {
+          const int i = z - za;
+          const int buf = z & 1;
+          for (int d = i == 0 ? 0 : 2; d < 3 && ok; ++d) {  // new planes of this output plane
+            const int s = (i + d) & 3;
+            ok = mbar_wait(&lbar[s], lph[s]);
+            if (ok) {
+              lph[s] ^= 1u;
+              lpend[s] = false;
             }
           }
-        }
-        uint4* dst = reinterpret_cast<uint4*>(static_cast<bf16*>(a.out) + v * COUT);
+          if (ok && used[buf]) {  // the consumers have read this buffer's previous plane
+            ok = mbar_wait(&freed[buf], fph[buf]);
+            fph[buf] ^= 1u;
+          }
+          if (!ok) break;
+          used[buf] = true;
+          tc_fence_after();
+          uint64_t sd[3];
 #pragma unroll
-        for (int c8 = 0; c8 < COUT / 8; ++c8) dst[c8] = make_uint4(pk[4 * c8], pk[4 * c8 + 1], pk[4 * c8 + 2], pk[4 * c8 + 3]);
+          for (int dz = 0; dz < 3; ++dz) sd[dz] = a0 + (uint64_t)(((i + dz) & 3) * (int)(slot_bytes >> 4));
+          const uint32_t d0 = tmem + (uint32_t)buf * 256u;
+          for (int j = 0; j < g.ntiles; ++j) {
+#pragma unroll
+            for (int tap = 0; tap < 27; ++tap) {
+              const uint64_t ad = sd[tap / 9] + (uint64_t)(off9[tap % 9] + 128 * j);
+#pragma unroll
+              for (int ks = 0; ks < CIN / 16; ++ks)
+                mma_bf16(d0 + (uint32_t)(j * COUT), ad + (uint64_t)(2 * ks * g.RS),
+                         b0 + (uint64_t)((tap * CH + 2 * ks) * COUT), IDESC, (tap | ks) != 0 ? 1u : 0u);
+            }
+          }
+          mma_commit(&done[buf]);
+          if (i > 0) {  // MMAs of plane z-1 done: the slot of plane z-2 takes plane z+2
+            const int pb = buf ^ 1;
+            ok = mbar_wait(&done[pb], dph[pb]);
+            dph[pb] ^= 1u;
+            if (ok && z + 2 <= zb) load(z + 2);
+          }
+        }
+        if (ok) {  // the unit's last plane: its MMAs done before the slots are reused
+          const int lb = (zb - 1) & 1;
+          ok = mbar_wait(&done[lb], dph[lb]);
+          dph[lb] ^= 1u;
+        }
+      }
+      if (!ok) {
+        atomicOr(a.err, 2);
+        for (int s = 0; s < kSlots; ++s)  // copies still in flight land before the CTA leaves
+          if (lpend[s]) mbar_wait(&lbar[s], lph[s]);
+        mbar_wait(&done[0], dph[0]);
+        mbar_wait(&done[1], dph[1]);
       }
     }
-    tc_fence_before();
+    __syncwarp();
+  } else if (warp >= 4) {
+    // ------------------------------------------------------------ consumers
+    const int q = warp & 3;
+    uint32_t dph[2] = {0u, 0u};
+    bool ok = true;
+    for (int u = blockIdx.x; u < g.units && ok; u += gridDim.x) {
+      const int col = u % cols, zi = u / cols;
+      const int x0 = (col % g.nseg) * g.XB, y0 = (col / g.nseg) * kRTY;
+      const int za = zi * g.zc, zb = min(g.Z, za + g.zc);
+      for (int z = za; z < zb; ++z) {
+        const int buf = z & 1;
+        ok = mbar_wait(&done[buf], dph[buf]);
+        dph[buf] ^= 1u;
+        if (!__all_sync(0xffffffffu, ok)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        for (int j = 0; j < g.ntiles; ++j) {
+          uint32_t r[32];
+          const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)buf * 256u + (uint32_t)(j * COUT);
+          if (COUT == 32) tmem_ld32(taddr, r);
+          else tmem_ld16(taddr, r);
+          tmem_wait_ld();
+          const int row = g.rs + 128 * j + 32 * q + lane;
+          const int yh = row / g.Xh, xh = row - yh * g.Xh;
+          const int x = x0 + xh - 1, y = y0 + yh - 1;
+          if (!(yh >= 1 && yh <= kRTY && xh >= 1 && xh <= g.XB && x < g.X && y < g.Y)) continue;
+          const size_t v = ((size_t)z * g.Y + y) * g.X + x;
+          if (EPI == EPI_LINEAR) {
+            float o[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) o[c] = c < 6 ? __uint_as_float(r[c]) + a.bias[c] : 0.0f;
+            float4* dst = reinterpret_cast<float4*>(static_cast<float*>(a.out) + v * 8);
+            dst[0] = make_float4(o[0], o[1], o[2], o[3]);
+            dst[1] = make_float4(o[4], o[5], o[6], o[7]);
+          } else {
+            uint32_t pk[COUT / 2];
+            if (EPI == EPI_RELU) {
+#pragma unroll
+              for (int c = 0; c < COUT / 2; ++c)
+                pk[c] = pack_bf16(fmaxf(__uint_as_float(r[2 * c]) + a.bias[2 * c], 0.0f),
+                                  fmaxf(__uint_as_float(r[2 * c + 1]) + a.bias[2 * c + 1], 0.0f));
+            } else {
+              const uint4* mk = reinterpret_cast<const uint4*>(a.mask + v * COUT);
+#pragma unroll
+              for (int c8 = 0; c8 < COUT / 8; ++c8) {
+                const uint4 m = mk[c8];
+                const uint32_t mw[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                  const int c = 8 * c8 + 2 * k;
+                  pk[c / 2] = pack_bf16(bf_lo(mw[k]) > 0.0f ? __uint_as_float(r[c]) : 0.0f,
+                                        bf_hi(mw[k]) > 0.0f ? __uint_as_float(r[c + 1]) : 0.0f);
+                }
+              }
+            }
+            uint4* dst = reinterpret_cast<uint4*>(static_cast<bf16*>(a.out) + v * COUT);
+#pragma unroll
+            for (int c8 = 0; c8 < COUT / 8; ++c8)
+              dst[c8] = make_uint4(pk[4 * c8], pk[4 * c8 + 1], pk[4 * c8 + 2], pk[4 * c8 + 3]);
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(su32(&freed[buf])) : "memory");
+      }
+    }
+    if (!ok && lane == 0) atomicOr(a.err, 2);
   }
-  if (failed) {
-    if (tid == 0) atomicOr(a.err, 2);
-    mbar_wait(bar, phase ^ 1u);  // let MMAs still in flight finish (bounded)
-  }
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
@@ -659,7 +737,9 @@ inline unsigned blocks_for(size_t n, int t) { return (unsigned)((n + t - 1) / t)
 struct adi_net_ctx {
   int N[3] = {0, 0, 0};
   size_t V = 0;
-  Geom g{};
+  Geom g{};     // weight-gradient blocks
+  Ring ring{};  // convolution work units
+  void* encode = nullptr;  // cuTensorMapEncodeTiled (driver entry point)
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int device = 0, sms = 0;
@@ -706,17 +786,41 @@ Fields fields_of(adi_handle h) {
   return F;
 }
 
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// 5D view (8 channels, CIN/8 chunks, X, Y, Z) of a channels-last BF16 array; a
+// box (8, 1, Xh, Yh, 1) is one chunk plane of a ring slot.  Out-of-grid voxels
+// (x, y, z outside) arrive as zeros: the convolution's zero padding.
+cudaError_t encode_act(adi_net n, const bf16* act, int cin, CUtensorMap* out) {
+  if (((uintptr_t)act & 15u) != 0) return cudaErrorInvalidValue;
+  const Ring& r = n->ring;
+  cuuint64_t dims[5] = {8, (cuuint64_t)(cin / 8), (cuuint64_t)r.X, (cuuint64_t)r.Y, (cuuint64_t)r.Z};
+  cuuint64_t strides[4] = {16, (cuuint64_t)cin * 2, (cuuint64_t)r.X * cin * 2, (cuuint64_t)r.X * r.Y * cin * 2};
+  cuuint32_t box[5] = {8, 1, (cuuint32_t)r.Xh, (cuuint32_t)r.Yh, 1};
+  cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  CUresult res = reinterpret_cast<EncodeTiledFn>(n->encode)(
+      out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16*>(act), dims, strides, box, estr,
+      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return res == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <int CIN, int COUT, int EPI>
 cudaError_t launch_conv(adi_net n, const bf16* in, const bf16* w, const float* bias, const bf16* mask, void* out) {
-  // all of the opt-in shared memory: one CTA per SM, so the 256 tensor-memory
+  // all of the opt-in shared memory: one CTA per SM, so the 512 tensor-memory
   // columns of a CTA never wait for another CTA's
   const size_t smem = (size_t)n->optin;
   cudaError_t e = cudaFuncSetAttribute(conv_kernel<CIN, COUT, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  ConvArgs a{in, w, bias, mask, out, n->g, n->d_err};
-  const int grid = n->g.nblocks < n->sms ? n->g.nblocks : n->sms;
-  conv_kernel<CIN, COUT, EPI><<<grid, kConvThreads, smem, n->stream>>>(a);
+  CUtensorMap map;
+  e = encode_act(n, in, CIN, &map);
+  if (e != cudaSuccess) return e;
+  ConvArgs a{w, bias, mask, out, n->ring, n->d_err};
+  const int grid = n->ring.units < n->sms ? n->ring.units : n->sms;
+  conv_kernel<CIN, COUT, EPI><<<grid, kConvThreads, smem, n->stream>>>(a, map);
   return cudaGetLastError();
 }
 
@@ -816,6 +920,12 @@ adi_status adi_net_create(int Nx, int Ny, int Nz, adi_net* out) {
   n->g = make_geom(Nx, Ny, Nz);
   cudaError_t e = cudaGetDevice(&n->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n->sms, cudaDevAttrMultiProcessorCount, n->device);
+  if (e == cudaSuccess) {
+    n->ring = make_ring(Nx, Ny, Nz, n->sms);
+    cudaDriverEntryPointQueryResult q;
+    e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &n->encode, 12000, cudaEnableDefault, &q);
+    if (e == cudaSuccess && (q != cudaDriverEntryPointSuccess || !n->encode)) e = cudaErrorNotSupported;
+  }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&n->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) n->own_stream = true;
   auto alloc = [&](void** p, size_t bytes) {
@@ -839,7 +949,7 @@ adi_status adi_net_create(int Nx, int Ny, int Nz, adi_net* out) {
   alloc((void**)&n->scal, 8 * sizeof(double));
   alloc((void**)&n->d_err, sizeof(int));
   if (e == cudaSuccess) {
-    const size_t need = conv_smem<32, 32>(n->g);
+    const size_t need = ring_smem<32, 32>(n->ring);
     e = cudaDeviceGetAttribute(&n->optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, n->device);
     if (e == cudaSuccess && need > (size_t)n->optin) {
       adi_net_destroy(n);

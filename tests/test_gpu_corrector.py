@@ -120,9 +120,10 @@ def test_small_forward_matches_oracle():
     assert e_r < 2e-3 and e < 2e-2, (e_r, e)
 
 
-@pytest.mark.parametrize("n,p", [((38, 9, 4), 2), ((137, 5, 3), 3), ((62, 21, 6), 1)])
+@pytest.mark.parametrize("n,p", [((38, 9, 4), 2), ((137, 5, 3), 3), ((62, 21, 6), 1), ((14, 62, 38), 2)])
 def test_forward_multi_tile_and_segments(n, p):
-    # N_x = 40 (two MMA tiles per block), 140 (two x segments), 63 (ragged y blocks)
+    # N_x = 40, 140 (two x segments, two 128-row MMA tiles per plane), 63 (ragged y
+    # units), 16 x 64 x 40 (work units of several z planes: the plane ring is reused)
     e_r, e = _forward_case(n, p, 3)
     assert e_r < 2e-3 and e < 2e-2, (e_r, e)
 
