@@ -13,8 +13,11 @@ module only sequences the calls and keeps the device arrays (torch tensors).
   pairs: the gain of the corrected coarse step over the plain one.
 
 Command line: ``python -m paper_2103_06998_gb300.corrector --out weights.f32``
-trains on 2,000 pairs at 64^3 elements (p = 2, maps 10000 + i) and writes the
-FP32 parameter vector of include/adi_corrector.h.
+trains on 2,000 pairs at 64^3 elements (p = 2, maps 10000 + i, dipole carrier
+frequencies 2 and 1 alternating) and writes the FP32 parameter vector of
+include/adi_corrector.h.  At the same Courant number a field driven at f0 = 1
+on 64^3 has the wavelength in grid units of f0 = 2 on 128^3, the resolution the
+corrector runs at; without those maps the net over-corrects there.
 """
 import argparse
 import os
@@ -42,12 +45,15 @@ def cfl_tau(n, p, eps, mu, sigma, factor=4.0):
     return dt
 
 
-def solver_pair(n, p, k, seed, tau=None):
-    """Fine (tau) and coarse (k tau) FP32 solvers on map `seed` with its dipole."""
+def solver_pair(n, p, k, seed, tau=None, f0=None):
+    """Fine (tau) and coarse (k tau) FP32 solvers on map `seed` with its dipole
+    (carrier frequency f0 if given, else the dipole's own, with s = 1/f0, t0 = 3 s)."""
     eps, mu, sigma, _ = inputs.head_map(n, seed)
     if tau is None:
         tau = cfl_tau(n, p, eps, mu, sigma)
     src = inputs.dipole(seed)
+    if f0 is not None:
+        src = dict(src, f0=f0, s=1.0 / f0, t0=3.0 / f0)
     out = []
     for dt in (tau, k * tau):
         s = adi.Solver(n, p, dt, eps, mu, sigma)
@@ -57,14 +63,15 @@ def solver_pair(n, p, k, seed, tau=None):
     return out[0], out[1], tau
 
 
-def pairs(net, n, p, k, seeds, per_map, warm_time=0.5):
-    """List of (X, T) device tensors, `per_map` consecutive pairs per map."""
+def pairs(net, n, p, k, seeds, per_map, warm_time=0.5, f0s=(None,)):
+    """List of (X, T) device tensors, `per_map` consecutive pairs per map; map i
+    is driven at carrier frequency f0s[i % len(f0s)] (None: the dipole's own)."""
     torch = _torch()
     N = tuple(v + p for v in n)
     V = N[0] * N[1] * N[2]
     out = []
-    for sd in seeds:
-        fine, coarse, tau = solver_pair(n, p, k, sd)
+    for m, sd in enumerate(seeds):
+        fine, coarse, tau = solver_pair(n, p, k, sd, f0=f0s[m % len(f0s)])
         fine.step(max(1, int(round(warm_time / tau))))
         for _ in range(per_map):
             X = torch.zeros((V, 16), dtype=torch.bfloat16, device="cuda")
@@ -146,6 +153,9 @@ def main(argv=None):
     ap.add_argument("--per-map", type=int, default=25)
     ap.add_argument("--epochs", type=int, default=6)
     ap.add_argument("--test-maps", type=int, default=4)
+    ap.add_argument("--f0", default="2,1",
+                    help="carrier frequencies of the training maps, cycled (2 = the workloads' dipole; 1 at 64^3 "
+                         "has the grid-unit wavelength of 2 at 128^3, the inference resolution)")
     a = ap.parse_args(argv)
     log = lambda m: print(m, flush=True)
     n = (a.n,) * 3
@@ -153,7 +163,8 @@ def main(argv=None):
     net = adi.Net(N)
     net.set_params(adi.net_flatten(inputs.net_init(2103)))
     t0 = time.time()
-    data = pairs(net, n, a.p, a.k, range(10000, 10000 + a.maps), a.per_map)
+    f0s = tuple(float(v) for v in a.f0.split(","))
+    data = pairs(net, n, a.p, a.k, range(10000, 10000 + a.maps), a.per_map, f0s=f0s)
     held = pairs(net, n, a.p, a.k, range(20000, 20000 + a.test_maps), a.per_map)
     log("pairs: %d train, %d held out, %.1f s" % (len(data), len(held), time.time() - t0))
     b0, f0 = evaluate(net, held)
