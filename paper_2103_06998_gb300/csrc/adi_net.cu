@@ -367,6 +367,9 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv_kernel(const ConvArgs a,
   } else if (warp >= 4) {
     // ------------------------------------------------------------ consumers
     const int q = warp & 3;
+    float bias[COUT];  // in registers for the whole kernel
+#pragma unroll
+    for (int c = 0; c < COUT; ++c) bias[c] = EPI == EPI_MASK ? 0.0f : a.bias[c];
     uint32_t dph[2] = {0u, 0u};
     bool ok = true;
     for (int u = blockIdx.x; u < g.units && ok; u += gridDim.x) {
@@ -396,7 +399,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv_kernel(const ConvArgs a,
           if (EPI == EPI_LINEAR) {
             float o[8];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) o[c] = c < 6 ? __uint_as_float(r[c]) + a.bias[c] : 0.0f;
+            for (int c = 0; c < 8; ++c) o[c] = c < 6 ? __uint_as_float(r[c]) + bias[c] : 0.0f;
             float4* dst = reinterpret_cast<float4*>(static_cast<float*>(a.out) + v * 8);
             dst[0] = make_float4(o[0], o[1], o[2], o[3]);
             dst[1] = make_float4(o[4], o[5], o[6], o[7]);
@@ -405,8 +408,8 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv_kernel(const ConvArgs a,
             if (EPI == EPI_RELU) {
 #pragma unroll
               for (int c = 0; c < COUT / 2; ++c)
-                pk[c] = pack_bf16(fmaxf(__uint_as_float(r[2 * c]) + a.bias[2 * c], 0.0f),
-                                  fmaxf(__uint_as_float(r[2 * c + 1]) + a.bias[2 * c + 1], 0.0f));
+                pk[c] = pack_bf16(fmaxf(__uint_as_float(r[2 * c]) + bias[2 * c], 0.0f),
+                                  fmaxf(__uint_as_float(r[2 * c + 1]) + bias[2 * c + 1], 0.0f));
             } else {
               const uint4* mk = reinterpret_cast<const uint4*>(a.mask + v * COUT);
 #pragma unroll
