@@ -50,6 +50,7 @@ def parse():
                          "learned: guarded corrector at 128^3 against plain steps")
     ap.add_argument("--weights", default=None, help="learned: corrector parameter file (FP32)")
     ap.add_argument("--coarse-steps", type=int, default=400, help="learned: coarse steps of the guarded run")
+    ap.add_argument("--tol", type=float, default=1e-4, help="learned: guard tolerance (relative l2 per coarse step)")
     return ap.parse_args()
 
 
@@ -258,7 +259,7 @@ def run_learned(args, rank, world, local):
     from paper_2103_06998_gb300 import adi, corrector
     torch.cuda.set_device(local)
     n = args.n if args.n != N_ELEM else 128
-    k, every, tol, m = 8, 8, 1e-4, args.coarse_steps
+    k, every, tol, m = 8, 8, args.tol, args.coarse_steps
     N = (n + P,) * 3
     Nc = N[0] * N[1] * N[2]
     fine, coarse, tau = corrector.solver_pair((n, n, n), P, k, SEED)
