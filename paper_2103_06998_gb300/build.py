@@ -14,7 +14,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libadi_maxwell.so")
-SOURCES = ["adi_kernels.cu", "adi_capi.cpp", "setup_host.cpp", "adi_noalloc.cu", "adi_batch.cpp", "adi_net.cu"]
+# (source, object name, extra flags): the step kernels are compiled twice, one
+# element type per object, so the two halves build in parallel
+SOURCES = [("adi_kernels.cu", "adi_kernels_f32", []), ("adi_kernels.cu", "adi_kernels_f64", ["-DADI_KERNELS_F64"]),
+           ("adi_capi.cpp", "adi_capi", []), ("setup_host.cpp", "setup_host", []), ("adi_noalloc.cu", "adi_noalloc", []),
+           ("adi_batch.cpp", "adi_batch", []), ("adi_net.cu", "adi_net", [])]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -32,9 +36,10 @@ def build(verbose=False, extra_flags=()):
     common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
     common += list(extra_flags)
 
-    def compile_one(src):
-        obj = os.path.join(out_dir, src + ".o")
-        cmd = [nv, "-c", os.path.join(CSRC, src), "-o", obj] + common + ARCH
+    def compile_one(entry):
+        src, name, flags = entry
+        obj = os.path.join(out_dir, name + ".o")
+        cmd = [nv, "-c", os.path.join(CSRC, src), "-o", obj] + common + list(flags) + ARCH
         if src.endswith(".cu"):
             cmd += ["-Xptxas", "-v"] if verbose else []
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -2165,14 +2165,31 @@ cudaError_t pivots_t(Ctx& c) {
   }
 }
 
+// This file is compiled twice: with ADI_KERNELS_F64 it holds the FP64 step, else
+// the FP32 / mixed step and everything shared; the two halves build in parallel.
+// The element-type-specific entry points are named *_f32 / *_f64; the
+// dispatchers below pick one by c.precision.
+#ifdef ADI_KERNELS_F64
+cudaError_t upload_tables_f64(Ctx& c, int optin) {
+  cudaError_t e = prepare_t<double>(c.p, optin);
+  if (e == cudaSuccess) e = upload_tables_t<double>(c);
+  if (e == cudaSuccess) e = pivots_t<double>(c);
+  return e;
+}
+cudaError_t run_substep_f64(Ctx& c, int which) { return substep_t<double>(c, which); }
+#else
+cudaError_t upload_tables_f64(Ctx& c, int optin);
+cudaError_t run_substep_f64(Ctx& c, int which);
+
 cudaError_t upload_tables(Ctx& c) {
   int optin = 0;
   cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c.device);
   if (e != cudaSuccess) return e;
   c.smem_optin = optin;
-  e = c.precision == ADI_PREC_FP64 ? prepare_t<double>(c.p, optin) : prepare_t<float>(c.p, optin);
+  if (c.precision == ADI_PREC_FP64) return upload_tables_f64(c, optin);
+  e = prepare_t<float>(c.p, optin);
   if (e != cudaSuccess) return e;
-  e = c.precision == ADI_PREC_FP64 ? upload_tables_t<double>(c) : upload_tables_t<float>(c);
+  e = upload_tables_t<float>(c);
   if (e != cudaSuccess) return e;
   if (c.precision == ADI_PREC_MIXED) {  // FP64 bands for the residual: per axis M, S, A, B
     std::vector<double> h;
@@ -2189,11 +2206,11 @@ cudaError_t upload_tables(Ctx& c) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
     if (e != cudaSuccess) return e;
   }
-  return c.precision == ADI_PREC_FP64 ? pivots_t<double>(c) : pivots_t<float>(c);
+  return pivots_t<float>(c);
 }
 
 cudaError_t run_substep(Ctx& c, int which) {
-  return c.precision == ADI_PREC_FP64 ? substep_t<double>(c, which) : substep_t<float>(c, which);
+  return c.precision == ADI_PREC_FP64 ? run_substep_f64(c, which) : substep_t<float>(c, which);
 }
 
 cudaError_t set_fields_dev(Ctx& c, const double* d_src) {
@@ -2278,5 +2295,7 @@ cudaError_t compute_coefficients(Ctx& c) {
   }
   return e;
 }
+
+#endif  // ADI_KERNELS_F64
 
 }  // namespace adi
