@@ -23,7 +23,9 @@
  * predicted (fine - coarse) / s.  Correction: fields += s * out, constrained
  * (Dirichlet) coefficients untouched.
  *
- * Device arrays passed to these calls (caller-owned, on the net's device):
+ * Device arrays passed to these calls (caller-owned, on the net's device, each
+ * 16-byte aligned: the convolutions read them with TMA; ADI_EINVAL / ADI_ECUDA
+ * otherwise):
  *   features  X: BF16 [z][y][x][16]  (channels 9..15 are zero)
  *   targets   T: FP32 [z][y][x][8]   (channels 6, 7 are zero)
  *   outputs   Y: FP32 [z][y][x][8]

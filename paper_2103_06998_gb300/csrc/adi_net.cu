@@ -1053,6 +1053,8 @@ adi_status adi_net_target(adi_net n, adi_handle fine, adi_handle coarse, float* 
 adi_status adi_net_forward(adi_net n, const void* X, float* Y) {
   if (!n) return net_fail(nullptr, ADI_EINVAL, "adi_net_forward: NULL net");
   if (!X || !Y) return net_fail(n, ADI_EINVAL, "adi_net_forward: NULL array");
+  if (((uintptr_t)X & 15u) || ((uintptr_t)Y & 15u))
+    return net_fail(n, ADI_EINVAL, "adi_net_forward: X and Y must be 16-byte aligned");
   cudaError_t e = net_forward(n, static_cast<const bf16*>(X), Y);
   if (e != cudaSuccess) return net_cuda(n, e, "adi_net_forward");
   return ADI_OK;
@@ -1078,6 +1080,8 @@ adi_status adi_net_apply(adi_net n, adi_handle h, const float* Y) {
 adi_status adi_net_train_step(adi_net n, const void* X, const float* T, float lr) {
   if (!n) return net_fail(nullptr, ADI_EINVAL, "adi_net_train_step: NULL net");
   if (!X || !T) return net_fail(n, ADI_EINVAL, "adi_net_train_step: NULL array");
+  if (((uintptr_t)X & 15u) || ((uintptr_t)T & 15u))
+    return net_fail(n, ADI_EINVAL, "adi_net_train_step: X and T must be 16-byte aligned");
   if (!(lr > 0.0f) || !std::isfinite(lr)) return net_fail(n, ADI_EINVAL, "adi_net_train_step: lr must be > 0");
   cudaError_t e = net_backward(n, static_cast<const bf16*>(X), T);
   if (e == cudaSuccess) {

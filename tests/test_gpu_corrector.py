@@ -305,3 +305,28 @@ def test_guarded_loop_follows_its_rule():
     for s in (coarse, fine, ref, coarse2, fine2, plain):
         s.close()
     net.close()
+
+
+def test_net_rejects_bad_arguments():
+    adi = _adi()
+    N = (7, 6, 5)
+    net = adi.Net(N)
+    X = _X(N)
+    Y = _F(N)
+    with pytest.raises(adi.AdiError) as e:
+        net.forward(X.data_ptr() + 4, Y.data_ptr())  # not 16-byte aligned
+    assert e.value.status == adi.ADI_EINVAL
+    with pytest.raises(adi.AdiError) as e:
+        net.set_params(np.zeros(adi.NET_PARAMS - 1, dtype=np.float32))
+    assert e.value.status == adi.ADI_EINVAL
+    bad = np.zeros(adi.NET_PARAMS, dtype=np.float32)
+    bad[3] = np.nan
+    with pytest.raises(adi.AdiError) as e:
+        net.set_params(bad)
+    assert e.value.status == adi.ADI_ENUMERIC
+    s, _, _ = _solver((3, 3, 3), 2, 1)  # another grid
+    with pytest.raises(adi.AdiError) as e:
+        net.features(s, X.data_ptr())
+    assert e.value.status == adi.ADI_EINVAL
+    s.close()
+    net.close()
