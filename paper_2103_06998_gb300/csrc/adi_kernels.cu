@@ -767,11 +767,13 @@ __global__ void __launch_bounds__(64) line_kernel(const LineJobs<T> jobs, const 
 // a whole launch are resident at once.  The forward sweep writes y to dst (DERIV:
 // to job.work) and the backward sweep reads it back through the L2.  Loads of
 // the next block of rows are issued before the stores of the current block.
-//   LM_MASS : dst = M^-1 src (precomputed mass LU; mid-line rows use constants).
-//   LM_DERIV: dst += scale * M^-1 (A src)  (red.global.add).
 //   LM_STIFF: dst = (M + diag(c) S)^-1 src with the row factors precomputed per
 //             dt by the LM_PIVOT pass (job.fac: multipliers, normalised upper
-//             factors; job.aux2: inverse pivots).
+//             factors; job.aux2: inverse pivots).  This is the form launched.
+//   LM_MASS : dst = M^-1 src, and LM_DERIV: dst += scale * M^-1 (A src), also
+//             compile; launch_line keeps those lines on the staged kernel,
+//             which measured faster for them (1 KB of intermediate per line of
+//             a whole launch does not stay in L2).
 template <typename T, int P, int MODE>
 __global__ void __launch_bounds__(128) line_direct_kernel(const LineJobs<T> jobs, const LineParams lp,
                                                           const AxisDev<T> ax) {
