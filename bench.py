@@ -71,9 +71,15 @@ def peaks():
 
 
 def kernel_source_hash():
+    """Hash of the step kernels' source with comments and whitespace removed, so
+    that only code changes invalidate recorded counters."""
+    import re
     h = hashlib.sha256()
     for f in ("adi_kernels.cu", "adi_internal.h"):
-        h.update(open(os.path.join(ROOT, "paper_2103_06998_gb300", "csrc", f), "rb").read())
+        txt = open(os.path.join(ROOT, "paper_2103_06998_gb300", "csrc", f)).read()
+        txt = re.sub(r"/\*.*?\*/", " ", txt, flags=re.S)
+        txt = re.sub(r"//[^\n]*", " ", txt)
+        h.update(" ".join(txt.split()).encode())
     return h.hexdigest()[:12]
 
 
