@@ -1,0 +1,30 @@
+"""Host-side helpers of the bench and the corrector (no GPU)."""
+import os
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_kernel_hash_ignores_comments_and_matches_recorded_traffic():
+    import bench
+    h = bench.kernel_source_hash()
+    assert len(h) == 12
+    # the committed counters were taken on the current step kernels
+    assert bench.ncu_traffic("rhs_E", 256) is not None
+    assert bench.ncu_traffic("rhs_E", 128) is None
+    assert bench.ncu_traffic("line_x_mass", 256) is None
+
+
+def test_corrector_weights_roundtrip(tmp_path):
+    from paper_2103_06998_gb300 import adi, corrector, inputs
+    flat = adi.net_flatten(inputs.net_init(3))
+    path = str(tmp_path / "w.f32")
+    corrector.save(flat, path)
+    np.testing.assert_array_equal(corrector.load(path), flat)
+    # the committed weights have the documented size and are finite
+    w = corrector.load()
+    assert w.size == adi.NET_PARAMS and np.all(np.isfinite(w))
+    # their padding entries are zero (layer 0 ci >= 9, layer 3 co >= 6)
+    real = adi.net_flatten([(np.ones((3, 3, 3, ci, co)), np.ones(co)) for ci, co in adi.NET_REAL]) != 0
+    assert np.all(w[~real] == 0.0)
