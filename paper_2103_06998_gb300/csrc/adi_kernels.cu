@@ -1076,7 +1076,9 @@ struct Smem {
   static constexpr int HX = TX + 2 * P, HY = TY + 2 * P, HZ = TZ + 2 * P;
   static constexpr int BX = 40;       // tile row: x0-4 .. x0+35 (TMA box)
   static constexpr int XOFF = 4 - P;  // position of x0-P inside a tile row
-  static constexpr int HXP = HX + 1;  // odd row pitch of the y-pass results (bank-conflict free x pass)
+  // row pitch of the y-pass results: odd (bank-conflict free scalar x pass), or
+  // even for p = 2, whose passes move pairs of columns (8- / 16-byte accesses)
+  static constexpr int HXP = P == 2 ? HX + 2 : HX + 1;
   static constexpr int TILE = HZ * HY * BX, ZR = TZ * HY * HX, YR = TZ * TY * HXP;
   // dynamic shared memory: 128 bytes of alignment slack, the tiles (TMA
   // destinations, 128-byte aligned), the pass buffers, then two mbarriers
@@ -1154,6 +1156,125 @@ __device__ __forceinline__ void xpass(const RhsParams<T>& prm, const T* yr, int 
   }
 }
 
+// ---- p = 2: passes on pairs of adjacent columns (two-element vector loads and
+// stores, half the shared-memory instructions and address arithmetic per output)
+template <typename T>
+struct V2;
+template <>
+struct V2<float> {
+  using t = float2;
+};
+template <>
+struct V2<double> {
+  using t = double2;
+};
+
+// z pass of column pair i2 = (yy, xx/2) for one or two z operators (ZSHARE: one)
+template <typename T, int P, int OP0, int OP1, bool ZSHARE, bool INNER>
+__device__ __forceinline__ void zpass2(const RhsParams<T>& prm, const T* tl, T* zr0, T* zr1, int z0, int i2) {
+  using S = Smem<T, P>;
+  using v2 = typename V2<T>::t;
+  constexpr int W = 2 * P + 1;
+  const int yy = i2 / (S::HX / 2), xx = 2 * (i2 % (S::HX / 2));
+  const T* col = tl + yy * S::BX + S::XOFF + xx;
+  v2 w[S::HZ];
+#pragma unroll
+  for (int k = 0; k < S::HZ; ++k) w[k] = *reinterpret_cast<const v2*>(col + k * S::HY * S::BX);
+  const int o = yy * S::HX + xx;
+#pragma unroll
+  for (int zz = 0; zz < TZ; ++zz) {
+    T a0 = T(0), a1 = T(0), b0 = T(0), b1 = T(0);
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+      const T c = bandv<T, P, 2, OP0, INNER>(prm, z0 + zz, q);
+      a0 += c * w[zz + q].x;
+      a1 += c * w[zz + q].y;
+      if (!ZSHARE) {
+        const T d = bandv<T, P, 2, OP1, INNER>(prm, z0 + zz, q);
+        b0 += d * w[zz + q].x;
+        b1 += d * w[zz + q].y;
+      }
+    }
+    v2 ra, rb;
+    ra.x = a0;
+    ra.y = a1;
+    *reinterpret_cast<v2*>(zr0 + zz * S::HY * S::HX + o) = ra;
+    if (!ZSHARE) {
+      rb.x = b0;
+      rb.y = b1;
+      *reinterpret_cast<v2*>(zr1 + zz * S::HY * S::HX + o) = rb;
+    }
+  }
+}
+
+// y pass of column pair i2 = (zz, xx/2) for the field's two y operators
+template <typename T, int P, int OP0, int OP1, bool ZSHARE, bool INNER>
+__device__ __forceinline__ void ypass2(const RhsParams<T>& prm, const T* zr0, const T* zr1, T* yr0, T* yr1, int y0,
+                                       int i2) {
+  using S = Smem<T, P>;
+  using v2 = typename V2<T>::t;
+  constexpr int W = 2 * P + 1;
+  const int zz = i2 / (S::HX / 2), xx = 2 * (i2 % (S::HX / 2));
+  v2 w0[S::HY], w1[S::HY];
+#pragma unroll
+  for (int k = 0; k < S::HY; ++k) {
+    w0[k] = *reinterpret_cast<const v2*>(zr0 + zz * S::HY * S::HX + k * S::HX + xx);
+    w1[k] = ZSHARE ? w0[k] : *reinterpret_cast<const v2*>(zr1 + zz * S::HY * S::HX + k * S::HX + xx);
+  }
+#pragma unroll
+  for (int yy = 0; yy < TY; ++yy) {
+    T a0 = T(0), a1 = T(0), b0 = T(0), b1 = T(0);
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+      const T c = bandv<T, P, 1, OP0, INNER>(prm, y0 + yy, q);
+      const T d = bandv<T, P, 1, OP1, INNER>(prm, y0 + yy, q);
+      a0 += c * w0[yy + q].x;
+      a1 += c * w0[yy + q].y;
+      b0 += d * w1[yy + q].x;
+      b1 += d * w1[yy + q].y;
+    }
+    v2 ra, rb;
+    ra.x = a0;
+    ra.y = a1;
+    rb.x = b0;
+    rb.y = b1;
+    *reinterpret_cast<v2*>(yr0 + (zz * TY + yy) * S::HXP + xx) = ra;
+    *reinterpret_cast<v2*>(yr1 + (zz * TY + yy) * S::HXP + xx) = rb;
+  }
+}
+
+// x pass as xpass, with the six-value windows read as three pairs
+template <typename T, int P, int OP, bool INNER, int OUT, int CK>
+__device__ __forceinline__ void xpass2(const RhsParams<T>& prm, const T* yr, int gx, int xp, int rg, float sg,
+                                       T (&cf)[3][RPT][2], T (&acc)[3][RPT][2]) {
+  using S = Smem<T, P>;
+  using v2 = typename V2<T>::t;
+  constexpr int W = 2 * P + 1;
+  T bx[2][W];
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int q = 0; q < W; ++q) bx[j][q] = bandv<T, P, 0, OP, INNER>(prm, min(gx + j, prm.Nx - 1), q);
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    const T* src = yr + (r * RG + rg) * S::HXP + xp;
+    T w[W + 1];
+#pragma unroll
+    for (int q = 0; q < (W + 1) / 2; ++q) {
+      const v2 u = *reinterpret_cast<const v2*>(src + 2 * q);
+      w[2 * q] = u.x;
+      w[2 * q + 1] = u.y;
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      T s = T(0);
+#pragma unroll
+      for (int q = 0; q < W; ++q) s += bx[j][q] * w[j + q];
+      acc[OUT][r][j] += (T(sg) * cf[CK][r][j]) * s;
+    }
+  }
+}
+
 // TMA: one 3D box per field tile; x starts at x0 - 4 so that x * sizeof(T) is a
 // multiple of 16 bytes; out-of-domain elements arrive as zeros.
 constexpr int BOXX = 40;
@@ -1215,33 +1336,54 @@ __device__ __forceinline__ bool do_field(const RhsParams<T>& prm, const TmaMaps&
     __syncthreads();
   }
   constexpr bool zshare = PL::z0 == PL::z1;
-  for (int i = tid; i < S::HY * S::HX; i += NT) {
-    if (inZ) zpass<T, P, PL::z0, true>(prm, tl, s_zr, z0, i);
-    else zpass<T, P, PL::z0, false>(prm, tl, s_zr, z0, i);
-    if (!zshare) {
-      if (inZ) zpass<T, P, PL::z1, true>(prm, tl, s_zr + S::ZR, z0, i);
-      else zpass<T, P, PL::z1, false>(prm, tl, s_zr + S::ZR, z0, i);
+  if constexpr (P == 2) {  // pairs of columns
+    for (int i2 = tid; i2 < S::HY * S::HX / 2; i2 += NT) {
+      if (inZ) zpass2<T, P, PL::z0, PL::z1, zshare, true>(prm, tl, s_zr, s_zr + S::ZR, z0, i2);
+      else zpass2<T, P, PL::z0, PL::z1, zshare, false>(prm, tl, s_zr, s_zr + S::ZR, z0, i2);
     }
-  }
-  __syncthreads();
-  for (int i = tid; i < TZ * S::HX; i += NT) {
-    const int zz = i / S::HX, xx = i % S::HX;
-    T w[S::HY];
-    yload<T, P>(s_zr, zz, xx, w);
-    if (inY) yapply<T, P, PL::y0, true>(prm, w, s_yr, y0, zz, xx);
-    else yapply<T, P, PL::y0, false>(prm, w, s_yr, y0, zz, xx);
-    if (!zshare) yload<T, P>(s_zr + S::ZR, zz, xx, w);
-    if (inY) yapply<T, P, PL::y1, true>(prm, w, s_yr + S::YR, y0, zz, xx);
-    else yapply<T, P, PL::y1, false>(prm, w, s_yr + S::YR, y0, zz, xx);
-  }
-  __syncthreads();
-  const int gx = x0 + xp;  // band rows are clamped per output inside xpass
-  if (inX) {
-    xpass<T, P, PL::x0, true, PL::o0, PL::c0 - CF_A>(prm, s_yr, gx, xp, rg, PL::s0, cf, acc);
-    xpass<T, P, PL::x1, true, PL::o1, PL::c1 - CF_A>(prm, s_yr + S::YR, gx, xp, rg, PL::s1, cf, acc);
-  } else {
-    xpass<T, P, PL::x0, false, PL::o0, PL::c0 - CF_A>(prm, s_yr, gx, xp, rg, PL::s0, cf, acc);
-    xpass<T, P, PL::x1, false, PL::o1, PL::c1 - CF_A>(prm, s_yr + S::YR, gx, xp, rg, PL::s1, cf, acc);
+    __syncthreads();
+    for (int i2 = tid; i2 < TZ * S::HX / 2; i2 += NT) {
+      if (inY) ypass2<T, P, PL::y0, PL::y1, zshare, true>(prm, s_zr, s_zr + S::ZR, s_yr, s_yr + S::YR, y0, i2);
+      else ypass2<T, P, PL::y0, PL::y1, zshare, false>(prm, s_zr, s_zr + S::ZR, s_yr, s_yr + S::YR, y0, i2);
+    }
+    __syncthreads();
+    const int gx = x0 + xp;
+    if (inX) {
+      xpass2<T, P, PL::x0, true, PL::o0, PL::c0 - CF_A>(prm, s_yr, gx, xp, rg, PL::s0, cf, acc);
+      xpass2<T, P, PL::x1, true, PL::o1, PL::c1 - CF_A>(prm, s_yr + S::YR, gx, xp, rg, PL::s1, cf, acc);
+    } else {
+      xpass2<T, P, PL::x0, false, PL::o0, PL::c0 - CF_A>(prm, s_yr, gx, xp, rg, PL::s0, cf, acc);
+      xpass2<T, P, PL::x1, false, PL::o1, PL::c1 - CF_A>(prm, s_yr + S::YR, gx, xp, rg, PL::s1, cf, acc);
+    }
+  } else {  // p = 1, 3: one column per thread
+    for (int i = tid; i < S::HY * S::HX; i += NT) {
+      if (inZ) zpass<T, P, PL::z0, true>(prm, tl, s_zr, z0, i);
+      else zpass<T, P, PL::z0, false>(prm, tl, s_zr, z0, i);
+      if (!zshare) {
+        if (inZ) zpass<T, P, PL::z1, true>(prm, tl, s_zr + S::ZR, z0, i);
+        else zpass<T, P, PL::z1, false>(prm, tl, s_zr + S::ZR, z0, i);
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < TZ * S::HX; i += NT) {
+      const int zz = i / S::HX, xx = i % S::HX;
+      T w[S::HY];
+      yload<T, P>(s_zr, zz, xx, w);
+      if (inY) yapply<T, P, PL::y0, true>(prm, w, s_yr, y0, zz, xx);
+      else yapply<T, P, PL::y0, false>(prm, w, s_yr, y0, zz, xx);
+      if (!zshare) yload<T, P>(s_zr + S::ZR, zz, xx, w);
+      if (inY) yapply<T, P, PL::y1, true>(prm, w, s_yr + S::YR, y0, zz, xx);
+      else yapply<T, P, PL::y1, false>(prm, w, s_yr + S::YR, y0, zz, xx);
+    }
+    __syncthreads();
+    const int gx = x0 + xp;  // band rows are clamped per output inside xpass
+    if (inX) {
+      xpass<T, P, PL::x0, true, PL::o0, PL::c0 - CF_A>(prm, s_yr, gx, xp, rg, PL::s0, cf, acc);
+      xpass<T, P, PL::x1, true, PL::o1, PL::c1 - CF_A>(prm, s_yr + S::YR, gx, xp, rg, PL::s1, cf, acc);
+    } else {
+      xpass<T, P, PL::x0, false, PL::o0, PL::c0 - CF_A>(prm, s_yr, gx, xp, rg, PL::s0, cf, acc);
+      xpass<T, P, PL::x1, false, PL::o1, PL::c1 - CF_A>(prm, s_yr + S::YR, gx, xp, rg, PL::s1, cf, acc);
+    }
   }
   __syncthreads();
   if (S::NBUF == 1 && F + 1 < 6 && tid == 0)  // single buffer: load the next field now
