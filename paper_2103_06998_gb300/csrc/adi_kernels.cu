@@ -464,6 +464,10 @@ __global__ void __launch_bounds__(64) line_kernel(const LineJobs<T> jobs, const 
   cp_async_wait_all();
   __syncthreads();
 
+  // y / z lines (one line per thread, own column): the backward sweep stores each
+  // result row directly (coalesced across the warp) instead of a write-back pass
+  constexpr bool FUSED = !XDIR && MODE != LM_PIVOT;
+  T* gdst = job.dst + off;
   if (t < cnt) {
     const int lo = dch ? 1 : 0, hi = dch ? N - 2 : N - 1;
     T* col = sr + t;
@@ -575,7 +579,8 @@ __global__ void __launch_bounds__(64) line_kernel(const LineJobs<T> jobs, const 
           T x = yk;
 #pragma unroll
           for (int e = 1; e <= P; ++e) x -= uk[e - 1] * xq[e - 1];
-          col[k * LP] = x;
+          if (FUSED) gdst[k * stride] = x;  // y / z lines: straight to global memory
+          else col[k * LP] = x;
 #pragma unroll
           for (int m = P - 1; m >= 1; --m) xq[m] = xq[m - 1];
           xq[0] = x;
@@ -669,7 +674,12 @@ __global__ void __launch_bounds__(64) line_kernel(const LineJobs<T> jobs, const 
         T x = (cst ? ax.luc[f][P] : tb[P]) * yk;
 #pragma unroll
         for (int e = 1; e <= P; ++e) x -= (cst ? ax.luc[f][P + e] : tb[P + e]) * xq[e - 1];
-        col[k * LP] = x;
+        if (FUSED) {  // y / z lines: straight to global memory
+          if (MODE == LM_DERIV) red_add(gdst + k * stride, job.scale * x);
+          else gdst[k * stride] = x;
+        } else {
+          col[k * LP] = x;
+        }
 #pragma unroll
         for (int m = P - 1; m >= 1; --m) xq[m] = xq[m - 1];
         xq[0] = x;
@@ -687,9 +697,17 @@ __global__ void __launch_bounds__(64) line_kernel(const LineJobs<T> jobs, const 
       for (; k >= b0; --k) bwd(k, true, col[k * LP]);
       for (; k >= lo; --k) bwd(k, false, col[k * LP]);
     }
-    for (int k = 0; k < lo; ++k) col[k * LP] = T(0);
-    for (int k = hi + 1; k < N; ++k) col[k * LP] = T(0);
+    if (FUSED) {
+      if (MODE != LM_DERIV) {  // fixed coefficients
+        for (int k = 0; k < lo; ++k) gdst[k * stride] = T(0);
+        for (int k = hi + 1; k < N; ++k) gdst[k * stride] = T(0);
+      }
+    } else {
+      for (int k = 0; k < lo; ++k) col[k * LP] = T(0);
+      for (int k = hi + 1; k < N; ++k) col[k * LP] = T(0);
+    }
   }
+  if (FUSED) return;  // y / z results are already in global memory
   __syncthreads();
 
   // ---- write back (LM_DERIV: dst += scale * x, done by the L2)
