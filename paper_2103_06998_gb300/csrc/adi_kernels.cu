@@ -1097,7 +1097,12 @@ struct Smem {
   // row pitch of the y-pass results: odd (bank-conflict free scalar x pass), or
   // even for p = 2, whose passes move pairs of columns (8- / 16-byte accesses)
   static constexpr int HXP = P == 2 ? HX + 2 : HX + 1;
-  static constexpr int TILE = HZ * HY * BX, ZR = TZ * HY * HX, YR = TZ * TY * HXP;
+  // plane strides of the z- and y-pass results (SZ per z' of [y'][x'], SY per z'
+  // of [y][x']); p = 2 pads both to 4 (mod 32) banks, so a half-warp of pair
+  // accesses that straddles two planes touches 32 distinct banks
+  static constexpr int SZ = P == 2 ? HY * HX + ((36 - (HY * HX) % 32) % 32) : HY * HX;
+  static constexpr int SY = P == 2 ? TY * HXP + ((36 - (TY * HXP) % 32) % 32) : TY * HXP;
+  static constexpr int TILE = HZ * HY * BX, ZR = TZ * SZ, YR = TZ * SY;
   // dynamic shared memory: 128 bytes of alignment slack, the tiles (TMA
   // destinations, 128-byte aligned), the pass buffers, then two mbarriers
   static constexpr size_t DATA2 = sizeof(T) * (2 * (size_t)TILE + 2 * (size_t)ZR + 2 * (size_t)YR);
@@ -1120,7 +1125,7 @@ __device__ __forceinline__ void zpass(const RhsParams<T>& prm, const T* tl, T* z
     T s = T(0);
 #pragma unroll
     for (int q = 0; q < W; ++q) s += bandv<T, P, 2, OP, INNER>(prm, z0 + zz, q) * w[zz + q];
-    zr[zz * S::HY * S::HX + i] = s;
+    zr[zz * S::SZ + i] = s;
   }
 }
 
@@ -1135,14 +1140,14 @@ __device__ __forceinline__ void yapply(const RhsParams<T>& prm, const T (&w)[Sme
     T s = T(0);
 #pragma unroll
     for (int q = 0; q < W; ++q) s += bandv<T, P, 1, OP, INNER>(prm, y0 + yy, q) * w[yy + q];
-    yr[(zz * TY + yy) * S::HXP + xx] = s;
+    yr[zz * S::SY + yy * S::HXP + xx] = s;
   }
 }
 
 template <typename T, int P>
 __device__ __forceinline__ void yload(const T* zr, int zz, int xx, T (&w)[Smem<T, P>::HY]) {
   using S = Smem<T, P>;
-  const T* src = zr + zz * S::HY * S::HX + xx;
+  const T* src = zr + zz * S::SZ + xx;
 #pragma unroll
   for (int k = 0; k < S::HY; ++k) w[k] = src[k * S::HX];
 }
@@ -1160,7 +1165,8 @@ __device__ __forceinline__ void xpass(const RhsParams<T>& prm, const T* yr, int 
     for (int q = 0; q < W; ++q) bx[j][q] = bandv<T, P, 0, OP, INNER>(prm, min(gx + j, prm.Nx - 1), q);
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
-    const T* src = yr + (r * RG + rg) * S::HXP + xp;  // half-warps read adjacent rows
+    const int row = r * RG + rg;  // half-warps read adjacent rows
+    const T* src = yr + (row / TY) * S::SY + (row % TY) * S::HXP + xp;
     T w[W + 1];
 #pragma unroll
     for (int q = 0; q < W + 1; ++q) w[q] = src[q];
@@ -1193,7 +1199,12 @@ __device__ __forceinline__ void zpass2(const RhsParams<T>& prm, const T* tl, T* 
   using S = Smem<T, P>;
   using v2 = typename V2<T>::t;
   constexpr int W = 2 * P + 1;
-  const int yy = i2 / (S::HX / 2), xx = 2 * (i2 % (S::HX / 2));
+  // pairs 0..15 of every row first (a half-warp reads 32 consecutive floats of
+  // one tile row), then the remaining pairs of every row
+  constexpr int NPR = S::HX / 2, NR = NPR - 16;
+  static_assert(NR > 0, "a tile row holds more than 16 column pairs");
+  const int j = i2 - S::HY * 16;
+  const int yy = j < 0 ? i2 >> 4 : j / NR, xx = 2 * (j < 0 ? i2 & 15 : 16 + j % NR);
   const T* col = tl + yy * S::BX + S::XOFF + xx;
   v2 w[S::HZ];
 #pragma unroll
@@ -1216,11 +1227,11 @@ __device__ __forceinline__ void zpass2(const RhsParams<T>& prm, const T* tl, T* 
     v2 ra, rb;
     ra.x = a0;
     ra.y = a1;
-    *reinterpret_cast<v2*>(zr0 + zz * S::HY * S::HX + o) = ra;
+    *reinterpret_cast<v2*>(zr0 + zz * S::SZ + o) = ra;
     if (!ZSHARE) {
       rb.x = b0;
       rb.y = b1;
-      *reinterpret_cast<v2*>(zr1 + zz * S::HY * S::HX + o) = rb;
+      *reinterpret_cast<v2*>(zr1 + zz * S::SZ + o) = rb;
     }
   }
 }
@@ -1236,8 +1247,8 @@ __device__ __forceinline__ void ypass2(const RhsParams<T>& prm, const T* zr0, co
   v2 w0[S::HY], w1[S::HY];
 #pragma unroll
   for (int k = 0; k < S::HY; ++k) {
-    w0[k] = *reinterpret_cast<const v2*>(zr0 + zz * S::HY * S::HX + k * S::HX + xx);
-    w1[k] = ZSHARE ? w0[k] : *reinterpret_cast<const v2*>(zr1 + zz * S::HY * S::HX + k * S::HX + xx);
+    w0[k] = *reinterpret_cast<const v2*>(zr0 + zz * S::SZ + k * S::HX + xx);
+    w1[k] = ZSHARE ? w0[k] : *reinterpret_cast<const v2*>(zr1 + zz * S::SZ + k * S::HX + xx);
   }
 #pragma unroll
   for (int yy = 0; yy < TY; ++yy) {
@@ -1256,8 +1267,8 @@ __device__ __forceinline__ void ypass2(const RhsParams<T>& prm, const T* zr0, co
     ra.y = a1;
     rb.x = b0;
     rb.y = b1;
-    *reinterpret_cast<v2*>(yr0 + (zz * TY + yy) * S::HXP + xx) = ra;
-    *reinterpret_cast<v2*>(yr1 + (zz * TY + yy) * S::HXP + xx) = rb;
+    *reinterpret_cast<v2*>(yr0 + zz * S::SY + yy * S::HXP + xx) = ra;
+    *reinterpret_cast<v2*>(yr1 + zz * S::SY + yy * S::HXP + xx) = rb;
   }
 }
 
@@ -1275,7 +1286,8 @@ __device__ __forceinline__ void xpass2(const RhsParams<T>& prm, const T* yr, int
     for (int q = 0; q < W; ++q) bx[j][q] = bandv<T, P, 0, OP, INNER>(prm, min(gx + j, prm.Nx - 1), q);
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
-    const T* src = yr + (r * RG + rg) * S::HXP + xp;
+    const int row = r * RG + rg;
+    const T* src = yr + (row / TY) * S::SY + (row % TY) * S::HXP + xp;
     T w[W + 1];
 #pragma unroll
     for (int q = 0; q < (W + 1) / 2; ++q) {
