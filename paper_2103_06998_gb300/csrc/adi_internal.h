@@ -148,6 +148,7 @@ struct Ctx {
   int use_graph = 1;
   int line_tile = 0;  // lines per line-solve CTA (0: largest that leaves two CTAs per SM)
   bool line_stream = true;  // y / z stiffness solves on the streaming kernel (precomputed factors)
+  bool line_xw = true;      // FP32 x mass / derivative solves on the warp-per-32-lines kernel
   double dt = 0.0;
   size_t Nc = 0;      // coefficients per component (N_x N_y N_z)
   int pitch = 0;      // device row pitch in elements: N_x rounded up to a multiple of 4

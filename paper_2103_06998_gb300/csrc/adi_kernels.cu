@@ -1026,6 +1026,206 @@ __global__ void __launch_bounds__(128) line_direct_kernel(const LineJobs<T> jobs
   }
 }
 
+// 16-byte asynchronous global -> shared copy (both addresses 16-byte aligned)
+__device__ __forceinline__ void cp_async16(float* smem, const float* gmem) {
+  unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+// four fire-and-forget global adds in one request (16-byte aligned address)
+__device__ __forceinline__ void red_add4(float* p, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
+               : "memory");
+}
+
+// Banded solves along x (rows contiguous in memory), one warp per 32 lines and
+// no block-wide synchronisation (Appendix, eqs. split1/split2).  Each line is
+// staged whole into shared memory as row [line][k] by 16-byte cp.async; the row
+// pitch lpk is a multiple of 4 with lpk / 4 odd, so the 16-byte accesses of
+// eight lanes to eight lines fall into 32 distinct banks.  Each lane runs its
+// line's recurrence in place, four rows per shared access, and the warp writes
+// the lines back with 16-byte stores.
+//   LM_MASS : dst = M^-1 src (full or Dirichlet-reduced mass LU)
+//   LM_DERIV: dst += scale * M^-1 (A src) (red.global.add)
+// Blocks of four rows whose factors (and A rows) all equal the mid-line
+// constants use registers; the other rows read the 1D tables, whose rows in the
+// constant range hold the same values.
+template <int P, int MODE>
+__global__ void __launch_bounds__(32) line_xw_kernel(const LineJobs<float> jobs, const LineParams lp,
+                                                     const AxisDev<float> ax, int lpk) {
+  constexpr int W = 2 * P + 1;
+  extern __shared__ __align__(16) float xw_plane[];  // [32][lpk]
+  const LineJob<float> job = blockIdx.y == 0 ? jobs.job[0] : (blockIdx.y == 1 ? jobs.job[1] : jobs.job[2]);
+  const int lane = threadIdx.x;
+  const long long L0 = (long long)blockIdx.x * 32;
+  const int cnt = (int)min(32LL, lp.nlines - L0);
+  const int N = lp.N, NC = (N + 3) >> 2;  // 16-byte chunks per line (the pitch holds 4 NC elements)
+  const long long pitch = lp.pitch;
+
+  // ---- stage the warp's lines
+  const float* src = job.src + L0 * pitch;
+  for (int i = 0; i < cnt; ++i)
+    for (int c = lane; c < NC; c += 32) cp_async16(xw_plane + i * lpk + 4 * c, src + i * pitch + 4 * c);
+  cp_async_wait_all();
+  __syncwarp();
+
+  if (lane < cnt) {
+    float* row = xw_plane + lane * lpk;
+    for (int k = N; k < 4 * NC; ++k) row[k] = 0.f;  // pitch padding copied with the last chunk
+    const int dch = job.dirichlet;
+    const int lo = dch ? 1 : 0, hi = dch ? N - 2 : N - 1;
+    const int llo = dch ? ax.lu_lo[1] : ax.lu_lo[0], lhi = dch ? ax.lu_hi[1] : ax.lu_hi[0];
+    const float* Lt = dch ? ax.luL[1] : ax.luL[0];
+    const float* It = dch ? ax.luInv[1] : ax.luInv[0];
+    const float* Ut = dch ? ax.luU[1] : ax.luU[0];
+    const float* At = ax.band[OP_A];
+    float lc[P], uc[P], ac[W];
+#pragma unroll
+    for (int m = 0; m < P; ++m) {
+      lc[m] = dch ? ax.luc[1][m] : ax.luc[0][m];
+      uc[m] = dch ? ax.luc[1][P + 1 + m] : ax.luc[0][P + 1 + m];
+    }
+    const float ic = dch ? ax.luc[1][P] : ax.luc[0][P];
+#pragma unroll
+    for (int d = 0; d < W; ++d) ac[d] = ax.inner[OP_A][d];
+    int c0 = max(lo, llo), c1 = min(hi, lhi);
+    if (MODE == LM_DERIV) {
+      c0 = max(c0, ax.inner_lo);
+      c1 = min(c1, ax.inner_hi);
+    }
+
+    // ---- forward sweep (DERIV: right-hand side (A u)_k from a window u[k-P .. k+P])
+    float yq[P];
+#pragma unroll
+    for (int m = 0; m < P; ++m) yq[m] = 0.f;
+    float win[W];
+#pragma unroll
+    for (int d = 0; d < W; ++d) win[d] = (MODE == LM_DERIV && d >= P && d - P < N) ? row[d - P] : 0.f;
+    float4 cv = *reinterpret_cast<const float4*>(row);
+    for (int b = 0; b < NC; ++b) {
+      const int k0 = 4 * b;
+      // the next block is read before this block's results are stored
+      const float4 nv = b + 1 < NC ? *reinterpret_cast<const float4*>(row + k0 + 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float cur[8] = {cv.x, cv.y, cv.z, cv.w, nv.x, nv.y, nv.z, nv.w};  // DERIV: u[k0 .. k0+7]
+      cv = nv;
+      float out[4];
+      if (k0 >= c0 && k0 + 3 <= c1) {  // constant block (warp-uniform)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          float y;
+          if (MODE == LM_DERIV) {
+            y = 0.f;
+#pragma unroll
+            for (int d = 0; d < W; ++d) y += ac[d] * win[d];
+#pragma unroll
+            for (int d = 0; d < W - 1; ++d) win[d] = win[d + 1];
+            win[W - 1] = cur[u + P + 1];
+          } else {
+            y = cur[u];
+          }
+#pragma unroll
+          for (int m = P - 1; m >= 0; --m) y -= lc[m] * yq[m];  // nearest term last: one FMA per row on the chain
+          out[u] = y;
+#pragma unroll
+          for (int m = P - 1; m >= 1; --m) yq[m] = yq[m - 1];
+          yq[0] = y;
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int k = k0 + u;
+          const bool live = k >= lo && k <= hi;
+          float y = 0.f;
+          if (MODE == LM_DERIV) {
+            if (live) {
+#pragma unroll
+              for (int d = 0; d < W; ++d) y += At[k * W + d] * win[d];
+            }
+#pragma unroll
+            for (int d = 0; d < W - 1; ++d) win[d] = win[d + 1];
+            win[W - 1] = cur[u + P + 1];
+          } else {
+            y = cur[u];
+          }
+          if (live) {
+#pragma unroll
+            for (int m = P - 1; m >= 0; --m) y -= Lt[k * P + m] * yq[m];
+#pragma unroll
+            for (int m = P - 1; m >= 1; --m) yq[m] = yq[m - 1];
+            yq[0] = y;
+          }
+          out[u] = live ? y : 0.f;
+        }
+      }
+      *reinterpret_cast<float4*>(row + k0) = make_float4(out[0], out[1], out[2], out[3]);
+    }
+
+    // ---- backward sweep
+    const int b0 = max(lo, llo), b1 = min(hi, lhi);
+    float xq[P];
+#pragma unroll
+    for (int m = 0; m < P; ++m) xq[m] = 0.f;
+    float4 yv = *reinterpret_cast<const float4*>(row + 4 * (NC - 1));
+    for (int b = NC - 1; b >= 0; --b) {
+      const int k0 = 4 * b;
+      const float yy[4] = {yv.x, yv.y, yv.z, yv.w};
+      if (b > 0) yv = *reinterpret_cast<const float4*>(row + k0 - 4);  // next block ahead of the stores
+      float out[4];
+      if (k0 >= b0 && k0 + 3 <= b1) {
+#pragma unroll
+        for (int u = 3; u >= 0; --u) {
+          float x = ic * yy[u];
+#pragma unroll
+          for (int e = P - 1; e >= 0; --e) x -= uc[e] * xq[e];
+          out[u] = x;
+#pragma unroll
+          for (int m = P - 1; m >= 1; --m) xq[m] = xq[m - 1];
+          xq[0] = x;
+        }
+      } else {
+#pragma unroll
+        for (int u = 3; u >= 0; --u) {
+          const int k = k0 + u;
+          if (k >= lo && k <= hi) {
+            float x = It[k] * yy[u];
+#pragma unroll
+            for (int e = P - 1; e >= 0; --e) x -= Ut[k * P + e] * xq[e];
+            out[u] = x;
+#pragma unroll
+            for (int m = P - 1; m >= 1; --m) xq[m] = xq[m - 1];
+            xq[0] = x;
+          } else {
+            out[u] = 0.f;
+          }
+        }
+      }
+      *reinterpret_cast<float4*>(row + k0) = make_float4(out[0], out[1], out[2], out[3]);
+    }
+  }
+  __syncwarp();
+
+  // ---- write back (MASS: dst = x; DERIV: dst += scale * x)
+  float* dst = job.dst + L0 * pitch;
+  const float s = job.scale;
+  for (int i = 0; i < cnt; ++i) {
+    for (int c = lane; c < NC; c += 32) {
+      const float4 v = *reinterpret_cast<const float4*>(xw_plane + i * lpk + 4 * c);
+      float* g = dst + i * pitch + 4 * c;
+      if (4 * c + 3 < N) {
+        if (MODE == LM_DERIV) red_add4(g, s * v.x, s * v.y, s * v.z, s * v.w);
+        else *reinterpret_cast<float4*>(g) = v;
+      } else {
+        const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (4 * c + u < N) {
+            if (MODE == LM_DERIV) red_add(g + u, s * vv[u]);
+            else g[u] = vv[u];
+          }
+      }
+    }
+  }
+}
+
 // ------------------------------------------------- E right-hand side (v2)
 // One CTA per 32 x 8 x 8 output tile (256 threads).  For each of the six input
 // fields a (8+2P) x (8+2P) x (32+2P) tile with halo is staged by cp.async
@@ -1932,6 +2132,24 @@ cudaError_t launch_line(Ctx& c, int dir, int mode, const LineJobs<T>& jobs, int 
     prof_end(c);
     return cudaGetLastError();
   }
+  if constexpr (sizeof(T) == 4) {
+    // x mass and derivative lines (FP32): one warp per 32 lines, 16-byte staging
+    bool xw = dir == 0 && (mode == LM_MASS || mode == LM_DERIV) && c.line_xw;
+    for (int j = 0; j < njobs; ++j)  // 16-byte aligned line starts (pitch is a multiple of 4)
+      xw = xw && ((reinterpret_cast<uintptr_t>(jobs.job[j].src) | reinterpret_cast<uintptr_t>(jobs.job[j].dst)) & 15) == 0;
+    int lpk = (lp.N + 3) & ~3;
+    if (((lpk >> 2) & 1) == 0) lpk += 4;  // lpk / 4 odd: conflict-free 16-byte lane accesses
+    const size_t smw = sizeof(float) * 32 * (size_t)lpk;
+    if (xw && smw <= (size_t)c.smem_optin) {
+      const AxisDev<T> axw = axis_dev<T>(c, 0);
+      dim3 gw((unsigned)((lp.nlines + 31) / 32), njobs);
+      prof_begin(c, name, per_job * njobs);
+      if (mode == LM_MASS) line_xw_kernel<P, LM_MASS><<<gw, 32, smw, c.stream>>>(jobs, lp, axw, lpk);
+      else line_xw_kernel<P, LM_DERIV><<<gw, 32, smw, c.stream>>>(jobs, lp, axw, lpk);
+      prof_end(c);
+      return cudaGetLastError();
+    }
+  }
   const int W = 2 * P + 1;
   const bool fact = mode == LM_STIFF || mode == LM_PIVOT;
   const int tabw = fact ? 2 * W : (mode == LM_DERIV ? 3 * P + 1 + W : 3 * P + 1);
@@ -2297,6 +2515,8 @@ cudaError_t prepare_tp(int optin) {
   if (e == cudaSuccess) e = opt_in(rhs_e_kernel<T, P, 1, false>, optin);
   if (e == cudaSuccess) e = opt_in(rhs_e_kernel<T, P, 2, false>, optin);
   if constexpr (sizeof(T) == 4) {
+    if (e == cudaSuccess) e = opt_in(line_xw_kernel<P, LM_MASS>, optin);
+    if (e == cudaSuccess) e = opt_in(line_xw_kernel<P, LM_DERIV>, optin);
     if (e == cudaSuccess) e = opt_in(rhs_e_kernel<T, P, 1, true>, optin);
     if (e == cudaSuccess) e = opt_in(rhs_e_kernel<T, P, 2, true>, optin);
     if (e == cudaSuccess) e = opt_in(resid_kernel<P>, optin);
