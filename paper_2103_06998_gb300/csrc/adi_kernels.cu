@@ -1226,6 +1226,177 @@ __global__ void __launch_bounds__(32) line_xw_kernel(const LineJobs<float> jobs,
   }
 }
 
+// Stiffness solves along x (FP32), one warp per 32 lines, with the row factors
+// of M + diag(c) S precomputed per dt by the LM_PIVOT pass (multipliers
+// fac[0..P-1], normalised upper factors fac[P..2P-1], inverse pivots aux2):
+//   forward  y_k = r_k - sum_m l_m[k] y_{k-m},
+//   backward x_k = y_k / pivot_k - sum_e u_e[k] x_{k+e},   k in lo .. hi,
+// the arithmetic of the streaming y / z form.  The right-hand side and y stay
+// in shared memory as rows [line][k]; the factor rows stream through a
+// two-stage ring of 16-row chunks (cp.async, one group per chunk), so the next
+// chunk is in flight while this one is solved.
+template <int P>
+__global__ void __launch_bounds__(32) line_xws_kernel(const LineJobs<float> jobs, const LineParams lp, int lpk) {
+  constexpr int CH = 16, CHP = CH + 4, NA = P + 1;  // rows per chunk, chunk row pitch (CHP / 4 odd), arrays per stage
+  static_assert(((CHP / 4) & 1) == 1, "conflict-free 16-byte lane accesses");
+  extern __shared__ __align__(16) float xs_smem[];
+  float* plane = xs_smem;           // [32][lpk]: r, then y, then x
+  float* ring = xs_smem + 32 * lpk;  // [2][NA][32][CHP]
+  const LineJob<float> job = blockIdx.y == 0 ? jobs.job[0] : (blockIdx.y == 1 ? jobs.job[1] : jobs.job[2]);
+  const int lane = threadIdx.x;
+  const long long L0 = (long long)blockIdx.x * 32;
+  const int cnt = (int)min(32LL, lp.nlines - L0);
+  const int N = lp.N, N4 = (N + 3) & ~3, nch = (N + CH - 1) / CH;
+  const long long pitch = lp.pitch, base = L0 * pitch;
+  const int dch = job.dirichlet;
+  const int lo = dch ? 1 : 0, hi = dch ? N - 2 : N - 1;
+  auto slot = [&](int st, int a, int i) { return ring + ((st * NA + a) * 32 + i) * CHP; };
+  // chunk ch: 32 lines x CH / 4 pieces of 16 bytes, four pieces per line per instruction group
+  auto issue = [&](int ch, int st, bool fwd) {
+    const int k0 = ch * CH;
+#pragma unroll
+    for (int q = 0; q < CH / 4; ++q) {
+      const int t = q * 32 + lane, i = t / (CH / 4), j = t % (CH / 4), k = k0 + 4 * j;
+      if (i < cnt && k < N4) {
+        const long long g = base + i * pitch + k;
+        if (fwd) {
+          cp_async16(plane + i * lpk + k, job.src + g);
+#pragma unroll
+          for (int m = 0; m < P; ++m) cp_async16(slot(st, m, i) + 4 * j, job.fac[m] + g);
+        } else {
+          cp_async16(slot(st, 0, i) + 4 * j, job.aux2 + g);
+#pragma unroll
+          for (int e = 0; e < P; ++e) cp_async16(slot(st, 1 + e, i) + 4 * j, job.fac[P + e] + g);
+        }
+      }
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  float* row = plane + lane * lpk;
+  const bool mine = lane < cnt;
+
+  // ---- forward sweep
+  float yq[P];
+#pragma unroll
+  for (int m = 0; m < P; ++m) yq[m] = 0.f;
+  issue(0, 0, true);
+  for (int ch = 0; ch < nch; ++ch) {
+    if (ch + 1 < nch) {
+      issue(ch + 1, (ch + 1) & 1, true);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    }
+    __syncwarp();
+    if (mine) {
+      const int st = ch & 1;
+#pragma unroll
+      for (int bb = 0; bb < CH / 4; ++bb) {
+        const int k0 = ch * CH + 4 * bb;
+        if (k0 >= N4) break;
+        const float4 rv = *reinterpret_cast<const float4*>(row + k0);
+        const float r[4] = {rv.x, rv.y, rv.z, rv.w};
+        float l[P][4];
+#pragma unroll
+        for (int m = 0; m < P; ++m) {
+          const float4 v = *reinterpret_cast<const float4*>(slot(st, m, lane) + 4 * bb);
+          l[m][0] = v.x;
+          l[m][1] = v.y;
+          l[m][2] = v.z;
+          l[m][3] = v.w;
+        }
+        float out[4];
+        const bool all = k0 >= lo && k0 + 3 <= hi;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const bool live = all || (k0 + u >= lo && k0 + u <= hi);
+          float y = r[u];
+#pragma unroll
+          for (int m = P - 1; m >= 0; --m) y -= l[m][u] * yq[m];
+          if (live) {
+#pragma unroll
+            for (int m = P - 1; m >= 1; --m) yq[m] = yq[m - 1];
+            yq[0] = y;
+          }
+          out[u] = live ? y : 0.f;
+        }
+        *reinterpret_cast<float4*>(row + k0) = make_float4(out[0], out[1], out[2], out[3]);
+      }
+    }
+    __syncwarp();  // this stage is refilled two chunks on
+  }
+
+  // ---- backward sweep
+  float xq[P];
+#pragma unroll
+  for (int m = 0; m < P; ++m) xq[m] = 0.f;
+  issue(nch - 1, (nch - 1) & 1, false);
+  for (int ch = nch - 1; ch >= 0; --ch) {
+    if (ch > 0) {
+      issue(ch - 1, (ch - 1) & 1, false);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    }
+    __syncwarp();
+    if (mine) {
+      const int st = ch & 1;
+#pragma unroll
+      for (int bb = CH / 4 - 1; bb >= 0; --bb) {
+        const int k0 = ch * CH + 4 * bb;
+        if (k0 >= N4) continue;
+        const float4 yv = *reinterpret_cast<const float4*>(row + k0);
+        const float y[4] = {yv.x, yv.y, yv.z, yv.w};
+        const float4 iv = *reinterpret_cast<const float4*>(slot(st, 0, lane) + 4 * bb);
+        const float inv[4] = {iv.x, iv.y, iv.z, iv.w};
+        float uu[P][4];
+#pragma unroll
+        for (int e = 0; e < P; ++e) {
+          const float4 v = *reinterpret_cast<const float4*>(slot(st, 1 + e, lane) + 4 * bb);
+          uu[e][0] = v.x;
+          uu[e][1] = v.y;
+          uu[e][2] = v.z;
+          uu[e][3] = v.w;
+        }
+        float out[4];
+        const bool all = k0 >= lo && k0 + 3 <= hi;
+#pragma unroll
+        for (int u = 3; u >= 0; --u) {
+          const bool live = all || (k0 + u >= lo && k0 + u <= hi);
+          float x = inv[u] * y[u];
+#pragma unroll
+          for (int e = P - 1; e >= 0; --e) x -= uu[e][u] * xq[e];
+          if (live) {
+#pragma unroll
+            for (int m = P - 1; m >= 1; --m) xq[m] = xq[m - 1];
+            xq[0] = x;
+          }
+          out[u] = live ? x : 0.f;
+        }
+        *reinterpret_cast<float4*>(row + k0) = make_float4(out[0], out[1], out[2], out[3]);
+      }
+    }
+    __syncwarp();
+  }
+
+  // ---- write back
+  float* dst = job.dst + base;
+  for (int i = 0; i < cnt; ++i) {
+    for (int c = lane; 4 * c < N4; c += 32) {
+      const float4 v = *reinterpret_cast<const float4*>(plane + i * lpk + 4 * c);
+      float* g = dst + i * pitch + 4 * c;
+      if (4 * c + 3 < N) {
+        *reinterpret_cast<float4*>(g) = v;
+      } else {
+        const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (4 * c + u < N) g[u] = vv[u];
+      }
+    }
+  }
+}
+
 // ------------------------------------------------- E right-hand side (v2)
 // One CTA per 32 x 8 x 8 output tile (256 threads).  For each of the six input
 // fields a (8+2P) x (8+2P) x (32+2P) tile with halo is staged by cp.async
@@ -2140,6 +2311,22 @@ cudaError_t launch_line(Ctx& c, int dir, int mode, const LineJobs<T>& jobs, int 
     int lpk = (lp.N + 3) & ~3;
     if (((lpk >> 2) & 1) == 0) lpk += 4;  // lpk / 4 odd: conflict-free 16-byte lane accesses
     const size_t smw = sizeof(float) * 32 * (size_t)lpk;
+    // x stiffness lines with precomputed row factors: plane plus a two-stage ring
+    const size_t sms = smw + sizeof(float) * 2 * (P + 1) * 32 * 20;
+    bool xs = dir == 0 && mode == LM_STIFF && c.line_xw && jobs.job[0].fac[0] != nullptr;
+    for (int j = 0; j < njobs && xs; ++j) {
+      uintptr_t a = reinterpret_cast<uintptr_t>(jobs.job[j].src) | reinterpret_cast<uintptr_t>(jobs.job[j].dst) |
+                    reinterpret_cast<uintptr_t>(jobs.job[j].aux2);
+      for (int m = 0; m < 2 * P; ++m) a |= reinterpret_cast<uintptr_t>(jobs.job[j].fac[m]);
+      xs = (a & 15) == 0 && jobs.job[j].aux2 != nullptr;
+    }
+    if (xs && sms <= (size_t)c.smem_optin) {
+      dim3 gs((unsigned)((lp.nlines + 31) / 32), njobs);
+      prof_begin(c, name, per_job * njobs);
+      line_xws_kernel<P><<<gs, 32, sms, c.stream>>>(jobs, lp, lpk);
+      prof_end(c);
+      return cudaGetLastError();
+    }
     if (xw && smw <= (size_t)c.smem_optin) {
       const AxisDev<T> axw = axis_dev<T>(c, 0);
       dim3 gw((unsigned)((lp.nlines + 31) / 32), njobs);
@@ -2463,7 +2650,7 @@ cudaError_t pivots_tp(Ctx& c) {
     }
     LineJobs<T> js{};
     js.job[0] = job_of<T>(nullptr, reinterpret_cast<T*>(c.pivots[d]), cf[2], 0.0, 1);
-    if (d > 0) {  // y and z: the streaming stiffness solve reads the row factors
+    if (d > 0 || sizeof(T) == 4) {  // streaming (y, z) and FP32 x stiffness solves read the row factors
       for (int m = 0; m < 2 * P; ++m) {
         if (!c.stiff_fac[d][m]) {
           cudaError_t e = cudaMalloc(&c.stiff_fac[d][m], c.Np * sizeof(T));
@@ -2517,6 +2704,7 @@ cudaError_t prepare_tp(int optin) {
   if constexpr (sizeof(T) == 4) {
     if (e == cudaSuccess) e = opt_in(line_xw_kernel<P, LM_MASS>, optin);
     if (e == cudaSuccess) e = opt_in(line_xw_kernel<P, LM_DERIV>, optin);
+    if (e == cudaSuccess) e = opt_in(line_xws_kernel<P>, optin);
     if (e == cudaSuccess) e = opt_in(rhs_e_kernel<T, P, 1, true>, optin);
     if (e == cudaSuccess) e = opt_in(rhs_e_kernel<T, P, 2, true>, optin);
     if (e == cudaSuccess) e = opt_in(resid_kernel<P>, optin);
