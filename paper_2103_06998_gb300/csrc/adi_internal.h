@@ -109,6 +109,7 @@ struct LineParams {
   long long nlines;
   int Nx, Ny, Nz;
   int pitch;      // elements between consecutive x rows
+  int* err;       // device status word: bit 0 = a bounded wait gave up
 };
 
 enum LineMode : int { LM_MASS = 0, LM_STIFF = 1, LM_DERIV = 2, LM_PIVOT = 3 };

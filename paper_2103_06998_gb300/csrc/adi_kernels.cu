@@ -1037,13 +1037,66 @@ __device__ __forceinline__ void red_add4(float* p, float a, float b, float c, fl
                : "memory");
 }
 
+// Whole-line bulk copies (TMA, no tensor map): global -> shared completing on an
+// mbarrier, shared -> global as a store or an FP32 add.  Addresses and sizes are
+// multiples of 16 bytes.
+__device__ __forceinline__ void xw_bar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"((unsigned)__cvta_generic_to_shared(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void xw_bar_expect(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(
+                   (unsigned)__cvta_generic_to_shared(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_load(float* smem, const float* gmem, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   (unsigned)__cvta_generic_to_shared(smem)),
+               "l"(gmem), "r"(bytes), "r"((unsigned)__cvta_generic_to_shared(bar))
+               : "memory");
+}
+// the issuing thread's own shared writes before the copy (generic -> async proxy)
+__device__ __forceinline__ void bulk_store(float* gmem, const float* smem, unsigned bytes, bool add) {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  if (add)
+    asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;\n" ::"l"(gmem),
+                 "r"((unsigned)__cvta_generic_to_shared(smem)), "r"(bytes)
+                 : "memory");
+  else
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(gmem),
+                 "r"((unsigned)__cvta_generic_to_shared(smem)), "r"(bytes)
+                 : "memory");
+  asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+}
+// shared memory may be released once the issuing thread's bulk stores have read it
+__device__ __forceinline__ void bulk_store_drain() {
+  asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+}
+// Wait for phase `parity` of the barrier with an iteration limit; false if it gave up.
+__device__ __forceinline__ bool xw_bar_wait(unsigned long long* bar, unsigned parity) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+  for (int it = 0; it < (1 << 22); ++it) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
 // Banded solves along x (rows contiguous in memory), one warp per 32 lines and
-// no block-wide synchronisation (Appendix, eqs. split1/split2).  Each line is
-// staged whole into shared memory as row [line][k] by 16-byte cp.async; the row
-// pitch lpk is a multiple of 4 with lpk / 4 odd, so the 16-byte accesses of
-// eight lanes to eight lines fall into 32 distinct banks.  Each lane runs its
-// line's recurrence in place, four rows per shared access, and the warp writes
-// the lines back with 16-byte stores.
+// no block-wide synchronisation (Appendix, eqs. split1/split2).  Each lane
+// stages its line whole into shared memory as row [line][k] with one bulk copy
+// (the row pitch lpk is a multiple of 4 with lpk / 4 odd, so the 16-byte
+// accesses of eight lanes to eight lines fall into 32 distinct banks), runs
+// the line's recurrence in place, four rows per shared access, and writes the
+// row back with one bulk store (DERIV: a bulk FP32 add).  Rows are copied to
+// the pitch (a multiple of 4): the padding of dst receives zeros (MASS) or an
+// added zero (DERIV).
 //   LM_MASS : dst = M^-1 src (full or Dirichlet-reduced mass LU)
 //   LM_DERIV: dst += scale * M^-1 (A src) (red.global.add)
 // Blocks of four rows whose factors (and A rows) all equal the mid-line
@@ -1061,16 +1114,23 @@ __global__ void __launch_bounds__(32) line_xw_kernel(const LineJobs<float> jobs,
   const int N = lp.N, NC = (N + 3) >> 2;  // 16-byte chunks per line (the pitch holds 4 NC elements)
   const long long pitch = lp.pitch;
 
-  // ---- stage the warp's lines
-  const float* src = job.src + L0 * pitch;
-  for (int i = 0; i < cnt; ++i)
-    for (int c = lane; c < NC; c += 32) cp_async16(xw_plane + i * lpk + 4 * c, src + i * pitch + 4 * c);
-  cp_async_wait_all();
+  __shared__ __align__(8) unsigned long long bar;
+  // ---- stage: one bulk copy per line
+  if (lane == 0) {
+    xw_bar_init(&bar);
+    xw_bar_expect(&bar, (unsigned)(cnt * 16 * NC));
+  }
   __syncwarp();
+  if (lane < cnt) bulk_load(xw_plane + lane * lpk, job.src + (L0 + lane) * pitch, 16u * NC, &bar);
+  if (!xw_bar_wait(&bar, 0)) {  // give up: report, give the copies a bounded time, leave
+    if (lane == 0) atomicOr(lp.err, 1);
+    xw_bar_wait(&bar, 0);
+    return;
+  }
 
   if (lane < cnt) {
     float* row = xw_plane + lane * lpk;
-    for (int k = N; k < 4 * NC; ++k) row[k] = 0.f;  // pitch padding copied with the last chunk
+    for (int k = N; k < lpk; ++k) row[k] = 0.f;  // pitch padding (and slack) reads as zeros
     const int dch = job.dirichlet;
     const int lo = dch ? 1 : 0, hi = dch ? N - 2 : N - 1;
     const int llo = dch ? ax.lu_lo[1] : ax.lu_lo[0], lhi = dch ? ax.lu_hi[1] : ax.lu_hi[0];
@@ -1104,7 +1164,7 @@ __global__ void __launch_bounds__(32) line_xw_kernel(const LineJobs<float> jobs,
     for (int b = 0; b < NC; ++b) {
       const int k0 = 4 * b;
       // the next block is read before this block's results are stored
-      const float4 nv = b + 1 < NC ? *reinterpret_cast<const float4*>(row + k0 + 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 nv = *reinterpret_cast<const float4*>(row + k0 + 4);  // lpk >= 4 NC + 4
       const float cur[8] = {cv.x, cv.y, cv.z, cv.w, nv.x, nv.y, nv.z, nv.w};  // DERIV: u[k0 .. k0+7]
       cv = nv;
       float out[4];
@@ -1176,7 +1236,7 @@ __global__ void __launch_bounds__(32) line_xw_kernel(const LineJobs<float> jobs,
           float x = ic * yy[u];
 #pragma unroll
           for (int e = P - 1; e >= 0; --e) x -= uc[e] * xq[e];
-          out[u] = x;
+          out[u] = MODE == LM_DERIV ? job.scale * x : x;
 #pragma unroll
           for (int m = P - 1; m >= 1; --m) xq[m] = xq[m - 1];
           xq[0] = x;
@@ -1189,7 +1249,7 @@ __global__ void __launch_bounds__(32) line_xw_kernel(const LineJobs<float> jobs,
             float x = It[k] * yy[u];
 #pragma unroll
             for (int e = P - 1; e >= 0; --e) x -= Ut[k * P + e] * xq[e];
-            out[u] = x;
+            out[u] = MODE == LM_DERIV ? job.scale * x : x;
 #pragma unroll
             for (int m = P - 1; m >= 1; --m) xq[m] = xq[m - 1];
             xq[0] = x;
@@ -1200,29 +1260,9 @@ __global__ void __launch_bounds__(32) line_xw_kernel(const LineJobs<float> jobs,
       }
       *reinterpret_cast<float4*>(row + k0) = make_float4(out[0], out[1], out[2], out[3]);
     }
-  }
-  __syncwarp();
-
-  // ---- write back (MASS: dst = x; DERIV: dst += scale * x)
-  float* dst = job.dst + L0 * pitch;
-  const float s = job.scale;
-  for (int i = 0; i < cnt; ++i) {
-    for (int c = lane; c < NC; c += 32) {
-      const float4 v = *reinterpret_cast<const float4*>(xw_plane + i * lpk + 4 * c);
-      float* g = dst + i * pitch + 4 * c;
-      if (4 * c + 3 < N) {
-        if (MODE == LM_DERIV) red_add4(g, s * v.x, s * v.y, s * v.z, s * v.w);
-        else *reinterpret_cast<float4*>(g) = v;
-      } else {
-        const float vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (4 * c + u < N) {
-            if (MODE == LM_DERIV) red_add(g + u, s * vv[u]);
-            else g[u] = vv[u];
-          }
-      }
-    }
+    // ---- write back (MASS: dst = x; DERIV: dst += scale * x, scaled above)
+    bulk_store(job.dst + (L0 + lane) * pitch, row, 16u * NC, MODE == LM_DERIV);
+    bulk_store_drain();
   }
 }
 
@@ -1234,7 +1274,8 @@ __global__ void __launch_bounds__(32) line_xw_kernel(const LineJobs<float> jobs,
 // the arithmetic of the streaming y / z form.  The right-hand side and y stay
 // in shared memory as rows [line][k]; the factor rows stream through a
 // two-stage ring of 16-row chunks (cp.async, one group per chunk), so the next
-// chunk is in flight while this one is solved.
+// chunk is in flight while this one is solved.  Each lane stores its row back
+// with one bulk copy.
 template <int P>
 __global__ void __launch_bounds__(32) line_xws_kernel(const LineJobs<float> jobs, const LineParams lp, int lpk) {
   constexpr int CH = 16, CHP = CH + 4, NA = P + 1;  // rows per chunk, chunk row pitch (CHP / 4 odd), arrays per stage
@@ -1379,21 +1420,10 @@ __global__ void __launch_bounds__(32) line_xws_kernel(const LineJobs<float> jobs
     __syncwarp();
   }
 
-  // ---- write back
-  float* dst = job.dst + base;
-  for (int i = 0; i < cnt; ++i) {
-    for (int c = lane; 4 * c < N4; c += 32) {
-      const float4 v = *reinterpret_cast<const float4*>(plane + i * lpk + 4 * c);
-      float* g = dst + i * pitch + 4 * c;
-      if (4 * c + 3 < N) {
-        *reinterpret_cast<float4*>(g) = v;
-      } else {
-        const float vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (4 * c + u < N) g[u] = vv[u];
-      }
-    }
+  // ---- write back: one bulk store per line (rows to the pitch; zeros outside lo .. hi)
+  if (mine) {
+    bulk_store(job.dst + base + lane * pitch, row, 4u * N4, false);
+    bulk_store_drain();
   }
 }
 
@@ -2285,6 +2315,7 @@ cudaError_t launch_line(Ctx& c, int dir, int mode, const LineJobs<T>& jobs, int 
   lp.Ny = c.N[1];
   lp.Nz = c.N[2];
   lp.pitch = c.pitch;
+  lp.err = c.d_err;
   lp.nlines = (long long)c.N[0] * c.N[1] * c.N[2] / c.N[dir];
   const double per_job = (double)c.Nc * sizeof(T) *
                          (mode == LM_MASS || mode == LM_PIVOT ? 2.0 : (mode == LM_STIFF ? 4.0 : 3.0));
@@ -2308,7 +2339,7 @@ cudaError_t launch_line(Ctx& c, int dir, int mode, const LineJobs<T>& jobs, int 
     bool xw = dir == 0 && (mode == LM_MASS || mode == LM_DERIV) && c.line_xw;
     for (int j = 0; j < njobs; ++j)  // 16-byte aligned line starts (pitch is a multiple of 4)
       xw = xw && ((reinterpret_cast<uintptr_t>(jobs.job[j].src) | reinterpret_cast<uintptr_t>(jobs.job[j].dst)) & 15) == 0;
-    int lpk = (lp.N + 3) & ~3;
+    int lpk = ((lp.N + 3) & ~3) + 4;      // a line, padded to 16 bytes, plus one 16-byte slack
     if (((lpk >> 2) & 1) == 0) lpk += 4;  // lpk / 4 odd: conflict-free 16-byte lane accesses
     const size_t smw = sizeof(float) * 32 * (size_t)lpk;
     // x stiffness lines with precomputed row factors: plane plus a two-stage ring
