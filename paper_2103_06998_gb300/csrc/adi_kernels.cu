@@ -1276,9 +1276,10 @@ __global__ void __launch_bounds__(32) line_xw_kernel(const LineJobs<float> jobs,
 // two-stage ring of 16-row chunks (cp.async, one group per chunk), so the next
 // chunk is in flight while this one is solved.  Each lane stores its row back
 // with one bulk copy.
+constexpr int kXwsRows = 32;  // factor rows per ring chunk
 template <int P>
 __global__ void __launch_bounds__(32) line_xws_kernel(const LineJobs<float> jobs, const LineParams lp, int lpk) {
-  constexpr int CH = 16, CHP = CH + 4, NA = P + 1;  // rows per chunk, chunk row pitch (CHP / 4 odd), arrays per stage
+  constexpr int CH = kXwsRows, CHP = CH + 4, NA = P + 1;  // rows per chunk, chunk row pitch (CHP / 4 odd), arrays per stage
   static_assert(((CHP / 4) & 1) == 1, "conflict-free 16-byte lane accesses");
   extern __shared__ __align__(16) float xs_smem[];
   float* plane = xs_smem;           // [32][lpk]: r, then y, then x
@@ -2343,7 +2344,7 @@ cudaError_t launch_line(Ctx& c, int dir, int mode, const LineJobs<T>& jobs, int 
     if (((lpk >> 2) & 1) == 0) lpk += 4;  // lpk / 4 odd: conflict-free 16-byte lane accesses
     const size_t smw = sizeof(float) * 32 * (size_t)lpk;
     // x stiffness lines with precomputed row factors: plane plus a two-stage ring
-    const size_t sms = smw + sizeof(float) * 2 * (P + 1) * 32 * 20;
+    const size_t sms = smw + sizeof(float) * 2 * (P + 1) * 32 * (kXwsRows + 4);
     bool xs = dir == 0 && mode == LM_STIFF && c.line_xw && jobs.job[0].fac[0] != nullptr;
     for (int j = 0; j < njobs && xs; ++j) {
       uintptr_t a = reinterpret_cast<uintptr_t>(jobs.job[j].src) | reinterpret_cast<uintptr_t>(jobs.job[j].dst) |
