@@ -1031,12 +1031,6 @@ __device__ __forceinline__ void cp_async16(float* smem, const float* gmem) {
   unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
-// four fire-and-forget global adds in one request (16-byte aligned address)
-__device__ __forceinline__ void red_add4(float* p, float a, float b, float c, float d) {
-  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
-               : "memory");
-}
-
 // Whole-line bulk copies (TMA, no tensor map): global -> shared completing on an
 // mbarrier, shared -> global as a store or an FP32 add.  Addresses and sizes are
 // multiples of 16 bytes.
@@ -1098,7 +1092,7 @@ __device__ __forceinline__ bool xw_bar_wait(unsigned long long* bar, unsigned pa
 // the pitch (a multiple of 4): the padding of dst receives zeros (MASS) or an
 // added zero (DERIV).
 //   LM_MASS : dst = M^-1 src (full or Dirichlet-reduced mass LU)
-//   LM_DERIV: dst += scale * M^-1 (A src) (red.global.add)
+//   LM_DERIV: dst += scale * M^-1 (A src) (the bulk add performs the update)
 // Blocks of four rows whose factors (and A rows) all equal the mid-line
 // constants use registers; the other rows read the 1D tables, whose rows in the
 // constant range hold the same values.
