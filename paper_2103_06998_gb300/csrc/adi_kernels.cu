@@ -1823,9 +1823,9 @@ __global__ void __launch_bounds__(rhs2::NT, sizeof(T) == 4 ? ADI_RHS_MINB : 1)
     rhs_e_kernel(const RhsParams<T> prm, const __grid_constant__ TmaMaps maps) {
   using namespace rhs2;
   using S = Smem<T, P>;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char rhs_smem[];
   // TMA writes need a 128-byte aligned shared address: align at run time
-  unsigned char* sbase = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
+  unsigned char* sbase = rhs_smem + ((128u - (smem_addr(rhs_smem) & 127u)) & 127u);
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(sbase + S::DATA);  // 8-byte aligned
   T* s_tile = reinterpret_cast<T*>(sbase);     // NBUF x TILE (TMA destinations)
   T* s_zr = s_tile + S::NBUF * S::TILE;         // 2 x ZR
