@@ -1740,19 +1740,19 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
   return false;
 }
 
+// The passes of one field, as three stages.  The kernel software-pipelines
+// them across fields: [z(F) and x(F-1)] | [y(F)], so each field costs two
+// block barriers (plus its tile wait) instead of three.
+// Stage z: wait for the field's tile (every thread; the give-up decision is
+// block-wide), optional BF16 rounding, z pass into s_zr.
 template <typename T, int P, int H, int F, bool BFT>
-__device__ __forceinline__ bool do_field(const RhsParams<T>& prm, const TmaMaps& maps, T* s_tile, T* s_zr,
-                                         T* s_yr, unsigned long long* bars, int x0, int y0, int z0, bool inZ,
-                                         bool inY, bool inX, int xp, int rg, T (&cf)[3][RPT][2],
-                                         T (&acc)[3][RPT][2]) {
+__device__ __forceinline__ bool zstage(const RhsParams<T>& prm, T* s_tile, T* s_zr, unsigned long long* bars, int z0,
+                                       bool inZ) {
   using S = Smem<T, P>;
   using PL = Plan<H, F>;
   const int tid = threadIdx.x;
-  constexpr int B = S::NBUF == 2 ? (F & 1) : 0;          // buffer of this field
+  constexpr int B = S::NBUF == 2 ? (F & 1) : 0;                 // buffer of this field
   constexpr unsigned PAR = S::NBUF == 2 ? (F / 2) & 1 : F & 1;  // its barrier phase
-  if (S::NBUF == 2 && F + 1 < 6 && tid == 0)  // prefetch the next field into the other buffer
-    tma_tile<T, P>(&maps.m[F + 1], s_tile + ((F + 1) & 1) * S::TILE, &bars[(F + 1) & 1], x0 - 4, y0 - P, z0 - P);
-  // every thread waits for the tile; the give-up decision is made block-wide
   if (!__syncthreads_and(mbar_wait(&bars[B], PAR))) return false;
   const T* tl = s_tile + B * S::TILE;
   if (BFT) {  // mixed precision: the field tile rounded to BF16 (FP32 accumulation below)
@@ -1767,20 +1767,6 @@ __device__ __forceinline__ bool do_field(const RhsParams<T>& prm, const TmaMaps&
       if (inZ) zpass2<T, P, PL::z0, PL::z1, zshare, true>(prm, tl, s_zr, s_zr + S::ZR, z0, i2);
       else zpass2<T, P, PL::z0, PL::z1, zshare, false>(prm, tl, s_zr, s_zr + S::ZR, z0, i2);
     }
-    __syncthreads();
-    for (int i2 = tid; i2 < TZ * S::HX / 2; i2 += NT) {
-      if (inY) ypass2<T, P, PL::y0, PL::y1, zshare, true>(prm, s_zr, s_zr + S::ZR, s_yr, s_yr + S::YR, y0, i2);
-      else ypass2<T, P, PL::y0, PL::y1, zshare, false>(prm, s_zr, s_zr + S::ZR, s_yr, s_yr + S::YR, y0, i2);
-    }
-    __syncthreads();
-    const int gx = x0 + xp;
-    if (inX) {
-      xpass2<T, P, PL::x0, true, PL::o0, PL::c0 - CF_A>(prm, s_yr, gx, xp, rg, PL::s0, cf, acc);
-      xpass2<T, P, PL::x1, true, PL::o1, PL::c1 - CF_A>(prm, s_yr + S::YR, gx, xp, rg, PL::s1, cf, acc);
-    } else {
-      xpass2<T, P, PL::x0, false, PL::o0, PL::c0 - CF_A>(prm, s_yr, gx, xp, rg, PL::s0, cf, acc);
-      xpass2<T, P, PL::x1, false, PL::o1, PL::c1 - CF_A>(prm, s_yr + S::YR, gx, xp, rg, PL::s1, cf, acc);
-    }
   } else {  // p = 1, 3: one column per thread
     for (int i = tid; i < S::HY * S::HX; i += NT) {
       if (inZ) zpass<T, P, PL::z0, true>(prm, tl, s_zr, z0, i);
@@ -1790,7 +1776,23 @@ __device__ __forceinline__ bool do_field(const RhsParams<T>& prm, const TmaMaps&
         else zpass<T, P, PL::z1, false>(prm, tl, s_zr + S::ZR, z0, i);
       }
     }
-    __syncthreads();
+  }
+  return true;
+}
+
+// Stage y: s_zr -> s_yr for the field's two y operators.
+template <typename T, int P, int H, int F>
+__device__ __forceinline__ void ystage(const RhsParams<T>& prm, const T* s_zr, T* s_yr, int y0, bool inY) {
+  using S = Smem<T, P>;
+  using PL = Plan<H, F>;
+  const int tid = threadIdx.x;
+  constexpr bool zshare = PL::z0 == PL::z1;
+  if constexpr (P == 2) {
+    for (int i2 = tid; i2 < TZ * S::HX / 2; i2 += NT) {
+      if (inY) ypass2<T, P, PL::y0, PL::y1, zshare, true>(prm, s_zr, s_zr + S::ZR, s_yr, s_yr + S::YR, y0, i2);
+      else ypass2<T, P, PL::y0, PL::y1, zshare, false>(prm, s_zr, s_zr + S::ZR, s_yr, s_yr + S::YR, y0, i2);
+    }
+  } else {
     for (int i = tid; i < TZ * S::HX; i += NT) {
       const int zz = i / S::HX, xx = i % S::HX;
       T w[S::HY];
@@ -1801,8 +1803,25 @@ __device__ __forceinline__ bool do_field(const RhsParams<T>& prm, const TmaMaps&
       if (inY) yapply<T, P, PL::y1, true>(prm, w, s_yr + S::YR, y0, zz, xx);
       else yapply<T, P, PL::y1, false>(prm, w, s_yr + S::YR, y0, zz, xx);
     }
-    __syncthreads();
-    const int gx = x0 + xp;  // band rows are clamped per output inside xpass
+  }
+}
+
+// Stage x: s_yr -> the field's two terms accumulated into the output registers.
+template <typename T, int P, int H, int F>
+__device__ __forceinline__ void xstage(const RhsParams<T>& prm, const T* s_yr, int x0, bool inX, int xp, int rg,
+                                       T (&cf)[3][RPT][2], T (&acc)[3][RPT][2]) {
+  using S = Smem<T, P>;
+  using PL = Plan<H, F>;
+  const int gx = x0 + xp;  // band rows are clamped per output inside the x pass
+  if constexpr (P == 2) {
+    if (inX) {
+      xpass2<T, P, PL::x0, true, PL::o0, PL::c0 - CF_A>(prm, s_yr, gx, xp, rg, PL::s0, cf, acc);
+      xpass2<T, P, PL::x1, true, PL::o1, PL::c1 - CF_A>(prm, s_yr + S::YR, gx, xp, rg, PL::s1, cf, acc);
+    } else {
+      xpass2<T, P, PL::x0, false, PL::o0, PL::c0 - CF_A>(prm, s_yr, gx, xp, rg, PL::s0, cf, acc);
+      xpass2<T, P, PL::x1, false, PL::o1, PL::c1 - CF_A>(prm, s_yr + S::YR, gx, xp, rg, PL::s1, cf, acc);
+    }
+  } else {
     if (inX) {
       xpass<T, P, PL::x0, true, PL::o0, PL::c0 - CF_A>(prm, s_yr, gx, xp, rg, PL::s0, cf, acc);
       xpass<T, P, PL::x1, true, PL::o1, PL::c1 - CF_A>(prm, s_yr + S::YR, gx, xp, rg, PL::s1, cf, acc);
@@ -1811,9 +1830,28 @@ __device__ __forceinline__ bool do_field(const RhsParams<T>& prm, const TmaMaps&
       xpass<T, P, PL::x1, false, PL::o1, PL::c1 - CF_A>(prm, s_yr + S::YR, gx, xp, rg, PL::s1, cf, acc);
     }
   }
+}
+
+// Field F of the pipeline: prefetch tile F+1, [z(F) and x(F-1)], y(F).  The
+// tile buffer refilled here held field F-1, whose z pass ended before the
+// previous barrier (one buffer: the tile is reloaded after z(F)); x(F-1) reads
+// s_yr, which y(F) overwrites only after the barrier that follows it.
+template <typename T, int P, int H, int F, bool BFT>
+__device__ __forceinline__ bool pipe_field(const RhsParams<T>& prm, const TmaMaps& maps, T* s_tile, T* s_zr,
+                                           T* s_yr, unsigned long long* bars, int x0, int y0, int z0, bool inZ,
+                                           bool inY, bool inX, int xp, int rg, T (&cf)[3][RPT][2],
+                                           T (&acc)[3][RPT][2]) {
+  using S = Smem<T, P>;
+  const int tid = threadIdx.x;
+  if (S::NBUF == 2 && F + 1 < 6 && tid == 0)
+    tma_tile<T, P>(&maps.m[F + 1], s_tile + ((F + 1) & 1) * S::TILE, &bars[(F + 1) & 1], x0 - 4, y0 - P, z0 - P);
+  if (!zstage<T, P, H, F, BFT>(prm, s_tile, s_zr, bars, z0, inZ)) return false;
+  if (F > 0) xstage<T, P, H, (F > 0 ? F - 1 : 0)>(prm, s_yr, x0, inX, xp, rg, cf, acc);
   __syncthreads();
-  if (S::NBUF == 1 && F + 1 < 6 && tid == 0)  // single buffer: load the next field now
+  if (S::NBUF == 1 && F + 1 < 6 && tid == 0)  // single buffer (FP64): load the next tile during the y pass
     tma_tile<T, P>(&maps.m[F + 1], s_tile, &bars[0], x0 - 4, y0 - P, z0 - P);
+  ystage<T, P, H, F>(prm, s_zr, s_yr, y0, inY);
+  __syncthreads();
   return true;
 }
 }  // namespace rhs2
@@ -1864,12 +1902,13 @@ __global__ void __launch_bounds__(rhs2::NT, sizeof(T) == 4 ? ADI_RHS_MINB : 1)
   }
   __syncthreads();
   if (tid == 0) tma_tile<T, P>(&maps.m[0], s_tile, &bars[0], x0 - 4, y0 - P, z0 - P);
-  bool ok = do_field<T, P, H, 0, BFT>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
-  if (ok) ok = do_field<T, P, H, 1, BFT>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
-  if (ok) ok = do_field<T, P, H, 2, BFT>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
-  if (ok) ok = do_field<T, P, H, 3, BFT>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
-  if (ok) ok = do_field<T, P, H, 4, BFT>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
-  if (ok) ok = do_field<T, P, H, 5, BFT>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+  bool ok = pipe_field<T, P, H, 0, BFT>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+  if (ok) ok = pipe_field<T, P, H, 1, BFT>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+  if (ok) ok = pipe_field<T, P, H, 2, BFT>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+  if (ok) ok = pipe_field<T, P, H, 3, BFT>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+  if (ok) ok = pipe_field<T, P, H, 4, BFT>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+  if (ok) ok = pipe_field<T, P, H, 5, BFT>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+  if (ok) xstage<T, P, H, 5>(prm, s_yr, x0, inX, xp, rg, cf, acc);
   if (!ok) {
     // a tile never arrived: report, give the copies in flight a bounded time, leave
     if (tid == 0) atomicOr(prm.err, 1);
