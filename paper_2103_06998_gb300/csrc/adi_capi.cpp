@@ -35,7 +35,7 @@ void free_ctx(Ctx* c0) {
   adi_ctx* c = static_cast<adi_ctx*>(c0);
   if (c->graph) cudaGraphExecDestroy(c->graph);
   for (auto* l : c->pending) delete l;
-  void* ptrs[] = {c->d_eps, c->d_mu, c->d_sigma, c->stage, c->tab, c->tab64, c->d_clock_t0, c->d_clock_step, c->d_err};
+  void* ptrs[] = {c->d_eps, c->d_mu, c->d_sigma, c->stage, c->tab, c->tab64, c->d_clock_t0, c->d_clock_step, c->d_err, c->d_bad};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int i = 0; i < 6; ++i) {
@@ -53,12 +53,6 @@ void free_ctx(Ctx* c0) {
   }
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
-}
-
-bool finite_all(const double* v, size_t n) {
-  for (size_t i = 0; i < n; ++i)
-    if (!std::isfinite(v[i])) return false;
-  return true;
 }
 
 void drop_graph(Ctx* c) {
@@ -208,6 +202,7 @@ adi_status adi_create(int nx, int ny, int nz, int p, double dt, const double* ep
   alloc((void**)&c->d_clock_t0, sizeof(double));
   alloc((void**)&c->d_clock_step, sizeof(long long));
   alloc((void**)&c->d_err, sizeof(int));
+  alloc((void**)&c->d_bad, sizeof(int));
   if (!ok) {
     cudaGetLastError();
     free_ctx(c);
@@ -296,9 +291,18 @@ adi_status adi_set_fields(adi_handle h, const double* EH, double t) {
   if (!h) return fail(nullptr, ADI_EINVAL, "adi_set_fields: NULL handle");
   if (!EH) return fail(h, ADI_EINVAL, "adi_set_fields: EH is NULL");
   if (!std::isfinite(t)) return fail(h, ADI_EINVAL, "adi_set_fields: t must be finite");
-  if (!finite_all(EH, 6 * h->Nc)) return fail(h, ADI_ENUMERIC, "adi_set_fields: NaN or Inf in EH");
-  cudaError_t e = cudaMemcpyAsync(h->stage, EH, 6 * h->Nc * sizeof(double), cudaMemcpyHostToDevice, h->stream);
-  if (e == cudaSuccess) e = adi::set_fields_dev(*h, (const double*)h->stage);
+  // copy, then check on the device (a host scan of 6 N_c doubles would dominate the call);
+  // the state is written only when every value is finite
+  const long long n6 = 6LL * (long long)h->Nc;
+  cudaError_t e = cudaMemsetAsync(h->d_bad, 0, sizeof(int), h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->stage, EH, n6 * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = adi::check_finite_dev(*h, (const double*)h->stage, n6, h->d_bad);
+  int bad = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, h->d_bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "adi_set_fields");
+  if (bad) return fail(h, ADI_ENUMERIC, "adi_set_fields: NaN or Inf in EH");
+  e = adi::set_fields_dev(*h, (const double*)h->stage);
   if (e == cudaSuccess) e = adi::set_clock(*h, t);
   if (e != cudaSuccess) return cuda_fail(h, e, "adi_set_fields");
   h->t_host = t;
@@ -394,16 +398,13 @@ static adi_status check_device_status(adi_handle h, const char* where) {
 adi_status adi_fields(adi_handle h, double* EH, double* t) {
   if (!h) return fail(nullptr, ADI_EINVAL, "adi_fields: NULL handle");
   if (!EH) return fail(h, ADI_EINVAL, "adi_fields: EH is NULL");
-  int* d_bad = nullptr;
-  cudaError_t e = cudaMalloc(&d_bad, sizeof(int));
-  if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, sizeof(int), h->stream);
-  if (e == cudaSuccess) e = adi::get_fields_dev(*h, (double*)h->stage, d_bad);
+  cudaError_t e = cudaMemsetAsync(h->d_bad, 0, sizeof(int), h->stream);
+  if (e == cudaSuccess) e = adi::get_fields_dev(*h, (double*)h->stage, h->d_bad);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(EH, h->stage, 6 * h->Nc * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
   int bad = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, h->d_bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  if (d_bad) cudaFree(d_bad);
   if (e != cudaSuccess) return cuda_fail(h, e, "adi_fields");
   if (t) *t = h->t_host + (double)h->steps_host * h->dt;
   adi_status ds = check_device_status(h, "adi_fields");

@@ -207,6 +207,7 @@ struct Ctx {
   CUtensorMap tmap_half[3];
   bool tmaps_ok = false;
   int* d_err = nullptr;  // device status word written by bounded waits
+  int* d_bad = nullptr;  // device flag: a value that is not finite (field checks)
 
   // graph of one step
   cudaGraphExec_t graph = nullptr;
@@ -223,6 +224,8 @@ cudaError_t compute_coefficients(Ctx& c);
 cudaError_t run_substep(Ctx& c, int which);
 cudaError_t set_fields_dev(Ctx& c, const double* d_src);
 cudaError_t get_fields_dev(Ctx& c, double* d_dst, int* d_bad);
+// d_bad |= 1 if any of the n doubles at d_src is NaN or Inf
+cudaError_t check_finite_dev(Ctx& c, const double* d_src, long long n, int* d_bad);
 cudaError_t set_clock(Ctx& c, double t0);
 cudaError_t make_tensor_maps(Ctx& c);
 

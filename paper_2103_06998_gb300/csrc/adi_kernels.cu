@@ -1976,6 +1976,13 @@ __global__ void set_fields_kernel(const double* __restrict__ src, T* d0, T* d1, 
   }
 }
 
+__global__ void finite_kernel(const double* __restrict__ src, long long n, int* bad) {
+  int local_bad = 0;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < n; g += (long long)gridDim.x * blockDim.x)
+    if (!isfinite(src[g])) local_bad = 1;
+  if (__syncthreads_or(local_bad) && threadIdx.x == 0) atomicOr(bad, 1);
+}
+
 template <typename T>
 __global__ void get_fields_kernel(double* __restrict__ dst, const T* s0, const T* s1, const T* s2, const T* s3,
                                   const T* s4, const T* s5, int Nx, int Ny, int Nz, int pitch, int* bad) {
@@ -2869,6 +2876,11 @@ cudaError_t set_fields_dev(Ctx& c, const double* d_src) {
     float** d = reinterpret_cast<float**>(c.cur);
     set_fields_kernel<float><<<g, 256, 0, c.stream>>>(d_src, d[0], d[1], d[2], d[3], d[4], d[5], c.N[0], c.N[1], c.N[2], c.pitch);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t check_finite_dev(Ctx& c, const double* d_src, long long n, int* d_bad) {
+  finite_kernel<<<grid_for(n, 256), 256, 0, c.stream>>>(d_src, n, d_bad);
   return cudaGetLastError();
 }
 
