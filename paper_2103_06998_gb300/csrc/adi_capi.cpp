@@ -55,6 +55,18 @@ void free_ctx(Ctx* c0) {
   delete c;
 }
 
+// Device address of a page-locked (pinned or registered) host buffer, else null:
+// kernels then read or write the caller's array directly over the host link
+// instead of staging it through a copy.
+const void* mapped_host(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 void drop_graph(Ctx* c) {
   if (c->graph) {
     cudaGraphExecDestroy(c->graph);
@@ -291,18 +303,32 @@ adi_status adi_set_fields(adi_handle h, const double* EH, double t) {
   if (!h) return fail(nullptr, ADI_EINVAL, "adi_set_fields: NULL handle");
   if (!EH) return fail(h, ADI_EINVAL, "adi_set_fields: EH is NULL");
   if (!std::isfinite(t)) return fail(h, ADI_EINVAL, "adi_set_fields: t must be finite");
-  // copy, then check on the device (a host scan of 6 N_c doubles would dominate the call);
-  // the state is written only when every value is finite
+  // check on the device (a host scan of 6 N_c doubles would dominate the call); the
+  // state is written only when every value is finite.  A page-locked EH is converted
+  // in one pass straight from host memory into scratch arrays (the right-hand side
+  // and half-step buffers, free between steps; a partial step is discarded), then
+  // copied into the state; other memory is copied to the staging buffer first.
   const long long n6 = 6LL * (long long)h->Nc;
+  const double* mapped = static_cast<const double*>(mapped_host(EH));
+  void* scratch[6] = {h->rhs[0], h->rhs[1], h->rhs[2], h->half[0], h->half[1], h->half[2]};
   cudaError_t e = cudaMemsetAsync(h->d_bad, 0, sizeof(int), h->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h->stage, EH, n6 * sizeof(double), cudaMemcpyHostToDevice, h->stream);
-  if (e == cudaSuccess) e = adi::check_finite_dev(*h, (const double*)h->stage, n6, h->d_bad);
+  if (mapped) {
+    if (e == cudaSuccess) e = adi::set_fields_into(*h, mapped, scratch, h->d_bad);
+  } else {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->stage, EH, n6 * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = adi::check_finite_dev(*h, (const double*)h->stage, n6, h->d_bad);
+  }
   int bad = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, h->d_bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "adi_set_fields");
   if (bad) return fail(h, ADI_ENUMERIC, "adi_set_fields: NaN or Inf in EH");
-  e = adi::set_fields_dev(*h, (const double*)h->stage);
+  if (mapped) {
+    for (int i = 0; i < 6 && e == cudaSuccess; ++i)
+      e = cudaMemcpyAsync(h->cur[i], scratch[i], h->Np * h->esize, cudaMemcpyDeviceToDevice, h->stream);
+  } else {
+    e = adi::set_fields_dev(*h, (const double*)h->stage);
+  }
   if (e == cudaSuccess) e = adi::set_clock(*h, t);
   if (e != cudaSuccess) return cuda_fail(h, e, "adi_set_fields");
   h->t_host = t;
@@ -398,9 +424,11 @@ static adi_status check_device_status(adi_handle h, const char* where) {
 adi_status adi_fields(adi_handle h, double* EH, double* t) {
   if (!h) return fail(nullptr, ADI_EINVAL, "adi_fields: NULL handle");
   if (!EH) return fail(h, ADI_EINVAL, "adi_fields: EH is NULL");
+  // a page-locked EH is written directly by the kernel, other memory through the staging buffer
+  double* mapped = const_cast<double*>(static_cast<const double*>(mapped_host(EH)));
   cudaError_t e = cudaMemsetAsync(h->d_bad, 0, sizeof(int), h->stream);
-  if (e == cudaSuccess) e = adi::get_fields_dev(*h, (double*)h->stage, h->d_bad);
-  if (e == cudaSuccess)
+  if (e == cudaSuccess) e = adi::get_fields_dev(*h, mapped ? mapped : (double*)h->stage, h->d_bad);
+  if (e == cudaSuccess && !mapped)
     e = cudaMemcpyAsync(EH, h->stage, 6 * h->Nc * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
   int bad = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, h->d_bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream);

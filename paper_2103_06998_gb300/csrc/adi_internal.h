@@ -223,6 +223,9 @@ cudaError_t upload_tables(Ctx& c);
 cudaError_t compute_coefficients(Ctx& c);
 cudaError_t run_substep(Ctx& c, int which);
 cudaError_t set_fields_dev(Ctx& c, const double* d_src);
+// convert 6 N_c doubles at d_src (device memory or mapped host memory) into the six
+// arrays dst (state layout, constrained coefficients zero); d_bad (optional) |= 1 on NaN/Inf
+cudaError_t set_fields_into(Ctx& c, const double* d_src, void* const* dst, int* d_bad);
 cudaError_t get_fields_dev(Ctx& c, double* d_dst, int* d_bad);
 // d_bad |= 1 if any of the n doubles at d_src is NaN or Inf
 cudaError_t check_finite_dev(Ctx& c, const double* d_src, long long n, int* d_bad);

@@ -1961,19 +1961,24 @@ __device__ __forceinline__ bool constrained(int comp, int i, int j, int k, int N
   }
 }
 
+// src may be host memory mapped into the device address space; bad (optional)
+// receives 1 if any source value is NaN or Inf
 template <typename T>
 __global__ void set_fields_kernel(const double* __restrict__ src, T* d0, T* d1, T* d2, T* d3, T* d4, T* d5,
-                                  int Nx, int Ny, int Nz, int pitch) {
+                                  int Nx, int Ny, int Nz, int pitch, int* bad) {
   const long long Nc = (long long)Nx * Ny * Nz;
   T* dst[6] = {d0, d1, d2, d3, d4, d5};
+  int local_bad = 0;
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < 6 * Nc;
        g += (long long)gridDim.x * blockDim.x) {
     int comp = (int)(g / Nc);
     long long r = g % Nc;
     int i = (int)(r % Nx), j = (int)((r / Nx) % Ny), k = (int)(r / ((long long)Nx * Ny));
     double v = src[g];
+    if (!isfinite(v)) local_bad = 1;
     dst[comp][((long long)k * Ny + j) * pitch + i] = constrained(comp, i, j, k, Nx, Ny, Nz) ? T(0) : T(v);
   }
+  if (bad && __syncthreads_or(local_bad) && threadIdx.x == 0) atomicOr(bad, 1);
 }
 
 __global__ void finite_kernel(const double* __restrict__ src, long long n, int* bad) {
@@ -2867,17 +2872,21 @@ cudaError_t run_substep(Ctx& c, int which) {
   return c.precision == ADI_PREC_FP64 ? run_substep_f64(c, which) : substep_t<float>(c, which);
 }
 
-cudaError_t set_fields_dev(Ctx& c, const double* d_src) {
+cudaError_t set_fields_into(Ctx& c, const double* d_src, void* const* dst, int* d_bad) {
   unsigned g = grid_for(6LL * (long long)c.Nc, 256);
   if (c.precision == ADI_PREC_FP64) {
-    double** d = reinterpret_cast<double**>(c.cur);
-    set_fields_kernel<double><<<g, 256, 0, c.stream>>>(d_src, d[0], d[1], d[2], d[3], d[4], d[5], c.N[0], c.N[1], c.N[2], c.pitch);
+    double* const* d = reinterpret_cast<double* const*>(dst);
+    set_fields_kernel<double><<<g, 256, 0, c.stream>>>(d_src, d[0], d[1], d[2], d[3], d[4], d[5], c.N[0], c.N[1], c.N[2],
+                                                        c.pitch, d_bad);
   } else {
-    float** d = reinterpret_cast<float**>(c.cur);
-    set_fields_kernel<float><<<g, 256, 0, c.stream>>>(d_src, d[0], d[1], d[2], d[3], d[4], d[5], c.N[0], c.N[1], c.N[2], c.pitch);
+    float* const* d = reinterpret_cast<float* const*>(dst);
+    set_fields_kernel<float><<<g, 256, 0, c.stream>>>(d_src, d[0], d[1], d[2], d[3], d[4], d[5], c.N[0], c.N[1], c.N[2],
+                                                       c.pitch, d_bad);
   }
   return cudaGetLastError();
 }
+
+cudaError_t set_fields_dev(Ctx& c, const double* d_src) { return set_fields_into(c, d_src, c.cur, nullptr); }
 
 cudaError_t check_finite_dev(Ctx& c, const double* d_src, long long n, int* d_bad) {
   finite_kernel<<<grid_for(n, 256), 256, 0, c.stream>>>(d_src, n, d_bad);
