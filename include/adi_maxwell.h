@@ -108,7 +108,11 @@ adi_status adi_set_stream(adi_handle h, void* cuda_stream);
 /* Copy 6 N_c doubles (host) into the state and set the time to t.  The
  * coefficients that the boundary conditions fix to zero (E_i in the two
  * directions other than i, H_i in direction i: first and last B-spline) are
- * set to zero.  NaN/Inf in EH gives ADI_ENUMERIC. */
+ * set to zero.  NaN/Inf in EH gives ADI_ENUMERIC and leaves the state and the
+ * time unchanged (the check runs on the device; the call synchronises the
+ * handle's stream to read it).  A page-locked EH (pinned or registered) is read
+ * by the device directly; other memory is copied to a staging buffer first.  A
+ * partial step (adi_substep) in progress is discarded. */
 adi_status adi_set_fields(adi_handle h, const double* EH, double t);
 
 /* Point dipole J = amp g(t) delta(x - x0) e_comp (comp 0, 1, 2 = E1, E2, E3),
@@ -129,7 +133,8 @@ adi_status adi_substep(adi_handle h, int which);
 
 /* Copy the state to 6 N_c host doubles (working precision widened) and the
  * current time to *t (t may be NULL).  Synchronises the stream.  Returns
- * ADI_ENUMERIC if any value is NaN/Inf (the data are still copied). */
+ * ADI_ENUMERIC if any value is NaN/Inf (the data are still copied).  A
+ * page-locked EH is written by the device directly. */
 adi_status adi_fields(adi_handle h, double* EH, double* t);
 
 /* Copy the state, in the working precision (float or double as created), to
