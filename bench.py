@@ -453,9 +453,12 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": traffic, "kernel": dom["name"], "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"
                 if peak_kind == "measured" else "fallback 6.8 TB/s"}
-    if dom["name"] == "resid_E64":
-        # FP64-ALU bound: 18 Kronecker terms x 3 passes x (2p+1) FMAs per point
-        flops = 18 * 3 * (2 * P + 1) * 2 * Nc
+    fp64_terms = 18 if dom["name"] == "resid_E64" else (12 if args.precision == "fp64" and dom["name"] == "rhs_E"
+                                                         else 0)
+    if fp64_terms:
+        # FP64-ALU bound (GB300's FP64 rate is 1/64 of FP32): Kronecker terms x 3 passes x (2p+1) FMAs per
+        # point (18 terms in the mixed-mode residual, the 12 of the E right-hand side in the FP64 step)
+        flops = fp64_terms * 3 * (2 * P + 1) * 2 * Nc
         roofline.update({"bound": "alu", "achieved": flops / (avg_ms * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": flops / (avg_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
                          "peak_source": "nominal FP64 of GB300 (no measured FP64 peak)"})
