@@ -1027,7 +1027,7 @@ __global__ void __launch_bounds__(128) line_direct_kernel(const LineJobs<T> jobs
 }
 
 // 16-byte asynchronous global -> shared copy (both addresses 16-byte aligned)
-__device__ __forceinline__ void cp_async16(float* smem, const float* gmem) {
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
@@ -1051,7 +1051,7 @@ __device__ __forceinline__ void bulk_load(float* smem, const float* gmem, unsign
                : "memory");
 }
 // the issuing thread's own shared writes before the copy (generic -> async proxy)
-__device__ __forceinline__ void bulk_store(float* gmem, const float* smem, unsigned bytes, bool add) {
+__device__ __forceinline__ void bulk_store(void* gmem, const void* smem, unsigned bytes, bool add) {
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
   if (add)
     asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;\n" ::"l"(gmem),
@@ -1270,15 +1270,41 @@ __global__ void __launch_bounds__(32) line_xw_kernel(const LineJobs<float> jobs,
 // two-stage ring of 16-row chunks (cp.async, one group per chunk), so the next
 // chunk is in flight while this one is solved.  Each lane stores its row back
 // with one bulk copy.
-constexpr int kXwsRows = 32;  // factor rows per ring chunk
-template <int P>
-__global__ void __launch_bounds__(32) line_xws_kernel(const LineJobs<float> jobs, const LineParams lp, int lpk) {
-  constexpr int CH = kXwsRows, CHP = CH + 4, NA = P + 1;  // rows per chunk, chunk row pitch (CHP / 4 odd), arrays per stage
-  static_assert(((CHP / 4) & 1) == 1, "conflict-free 16-byte lane accesses");
-  extern __shared__ __align__(16) float xs_smem[];
-  float* plane = xs_smem;           // [32][lpk]: r, then y, then x
-  float* ring = xs_smem + 32 * lpk;  // [2][NA][32][CHP]
-  const LineJob<float> job = blockIdx.y == 0 ? jobs.job[0] : (blockIdx.y == 1 ? jobs.job[1] : jobs.job[2]);
+// four consecutive elements (16 bytes of FP32, 32 of FP64) from / to shared memory
+__device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = a.z;
+  v[3] = a.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
+  const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = b.x;
+  v[3] = b.y;
+}
+__device__ __forceinline__ void st4(float* p, const float (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double (&v)[4]) {
+  *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
+}
+
+// factor rows per ring chunk: 32 (FP32), 16 (FP64, so that two warps fit per SM)
+template <typename T>
+__host__ __device__ constexpr int xws_rows() { return sizeof(T) == 4 ? 32 : 16; }
+template <typename T, int P>
+__global__ void __launch_bounds__(32) line_xws_kernel(const LineJobs<T> jobs, const LineParams lp, int lpk) {
+  constexpr int CH = xws_rows<T>(), CHP = CH + 4, NA = P + 1;  // rows per chunk, chunk row pitch, arrays per stage
+  constexpr int EP = 16 / sizeof(T), PPL = CH / EP;          // elements per 16-byte piece, pieces per chunk row
+  static_assert(sizeof(T) != 4 || ((CHP / 4) & 1) == 1, "conflict-free 16-byte lane accesses");
+  extern __shared__ __align__(16) unsigned char xs_raw[];
+  T* plane = reinterpret_cast<T*>(xs_raw);  // [32][lpk]: r, then y, then x
+  T* ring = plane + 32 * lpk;               // [2][NA][32][CHP]
+  const LineJob<T> job = blockIdx.y == 0 ? jobs.job[0] : (blockIdx.y == 1 ? jobs.job[1] : jobs.job[2]);
   const int lane = threadIdx.x;
   const long long L0 = (long long)blockIdx.x * 32;
   const int cnt = (int)min(32LL, lp.nlines - L0);
@@ -1287,34 +1313,34 @@ __global__ void __launch_bounds__(32) line_xws_kernel(const LineJobs<float> jobs
   const int dch = job.dirichlet;
   const int lo = dch ? 1 : 0, hi = dch ? N - 2 : N - 1;
   auto slot = [&](int st, int a, int i) { return ring + ((st * NA + a) * 32 + i) * CHP; };
-  // chunk ch: 32 lines x CH / 4 pieces of 16 bytes, four pieces per line per instruction group
+  // chunk ch: 32 lines x PPL pieces of 16 bytes
   auto issue = [&](int ch, int st, bool fwd) {
     const int k0 = ch * CH;
 #pragma unroll
-    for (int q = 0; q < CH / 4; ++q) {
-      const int t = q * 32 + lane, i = t / (CH / 4), j = t % (CH / 4), k = k0 + 4 * j;
+    for (int q = 0; q < PPL; ++q) {
+      const int t = q * 32 + lane, i = t / PPL, j = t % PPL, k = k0 + EP * j;
       if (i < cnt && k < N4) {
         const long long g = base + i * pitch + k;
         if (fwd) {
           cp_async16(plane + i * lpk + k, job.src + g);
 #pragma unroll
-          for (int m = 0; m < P; ++m) cp_async16(slot(st, m, i) + 4 * j, job.fac[m] + g);
+          for (int m = 0; m < P; ++m) cp_async16(slot(st, m, i) + EP * j, job.fac[m] + g);
         } else {
-          cp_async16(slot(st, 0, i) + 4 * j, job.aux2 + g);
+          cp_async16(slot(st, 0, i) + EP * j, job.aux2 + g);
 #pragma unroll
-          for (int e = 0; e < P; ++e) cp_async16(slot(st, 1 + e, i) + 4 * j, job.fac[P + e] + g);
+          for (int e = 0; e < P; ++e) cp_async16(slot(st, 1 + e, i) + EP * j, job.fac[P + e] + g);
         }
       }
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   };
-  float* row = plane + lane * lpk;
+  T* row = plane + lane * lpk;
   const bool mine = lane < cnt;
 
   // ---- forward sweep
-  float yq[P];
+  T yq[P];
 #pragma unroll
-  for (int m = 0; m < P; ++m) yq[m] = 0.f;
+  for (int m = 0; m < P; ++m) yq[m] = T(0);
   issue(0, 0, true);
   for (int ch = 0; ch < nch; ++ch) {
     if (ch + 1 < nch) {
@@ -1330,23 +1356,15 @@ __global__ void __launch_bounds__(32) line_xws_kernel(const LineJobs<float> jobs
       for (int bb = 0; bb < CH / 4; ++bb) {
         const int k0 = ch * CH + 4 * bb;
         if (k0 >= N4) break;
-        const float4 rv = *reinterpret_cast<const float4*>(row + k0);
-        const float r[4] = {rv.x, rv.y, rv.z, rv.w};
-        float l[P][4];
+        T r[4], l[P][4], out[4];
+        ld4(row + k0, r);
 #pragma unroll
-        for (int m = 0; m < P; ++m) {
-          const float4 v = *reinterpret_cast<const float4*>(slot(st, m, lane) + 4 * bb);
-          l[m][0] = v.x;
-          l[m][1] = v.y;
-          l[m][2] = v.z;
-          l[m][3] = v.w;
-        }
-        float out[4];
+        for (int m = 0; m < P; ++m) ld4(slot(st, m, lane) + 4 * bb, l[m]);
         const bool all = k0 >= lo && k0 + 3 <= hi;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const bool live = all || (k0 + u >= lo && k0 + u <= hi);
-          float y = r[u];
+          T y = r[u];
 #pragma unroll
           for (int m = P - 1; m >= 0; --m) y -= l[m][u] * yq[m];
           if (live) {
@@ -1354,18 +1372,18 @@ __global__ void __launch_bounds__(32) line_xws_kernel(const LineJobs<float> jobs
             for (int m = P - 1; m >= 1; --m) yq[m] = yq[m - 1];
             yq[0] = y;
           }
-          out[u] = live ? y : 0.f;
+          out[u] = live ? y : T(0);
         }
-        *reinterpret_cast<float4*>(row + k0) = make_float4(out[0], out[1], out[2], out[3]);
+        st4(row + k0, out);
       }
     }
     __syncwarp();  // this stage is refilled two chunks on
   }
 
   // ---- backward sweep
-  float xq[P];
+  T xq[P];
 #pragma unroll
-  for (int m = 0; m < P; ++m) xq[m] = 0.f;
+  for (int m = 0; m < P; ++m) xq[m] = T(0);
   issue(nch - 1, (nch - 1) & 1, false);
   for (int ch = nch - 1; ch >= 0; --ch) {
     if (ch > 0) {
@@ -1381,25 +1399,16 @@ __global__ void __launch_bounds__(32) line_xws_kernel(const LineJobs<float> jobs
       for (int bb = CH / 4 - 1; bb >= 0; --bb) {
         const int k0 = ch * CH + 4 * bb;
         if (k0 >= N4) continue;
-        const float4 yv = *reinterpret_cast<const float4*>(row + k0);
-        const float y[4] = {yv.x, yv.y, yv.z, yv.w};
-        const float4 iv = *reinterpret_cast<const float4*>(slot(st, 0, lane) + 4 * bb);
-        const float inv[4] = {iv.x, iv.y, iv.z, iv.w};
-        float uu[P][4];
+        T y[4], inv[4], uu[P][4], out[4];
+        ld4(row + k0, y);
+        ld4(slot(st, 0, lane) + 4 * bb, inv);
 #pragma unroll
-        for (int e = 0; e < P; ++e) {
-          const float4 v = *reinterpret_cast<const float4*>(slot(st, 1 + e, lane) + 4 * bb);
-          uu[e][0] = v.x;
-          uu[e][1] = v.y;
-          uu[e][2] = v.z;
-          uu[e][3] = v.w;
-        }
-        float out[4];
+        for (int e = 0; e < P; ++e) ld4(slot(st, 1 + e, lane) + 4 * bb, uu[e]);
         const bool all = k0 >= lo && k0 + 3 <= hi;
 #pragma unroll
         for (int u = 3; u >= 0; --u) {
           const bool live = all || (k0 + u >= lo && k0 + u <= hi);
-          float x = inv[u] * y[u];
+          T x = inv[u] * y[u];
 #pragma unroll
           for (int e = P - 1; e >= 0; --e) x -= uu[e][u] * xq[e];
           if (live) {
@@ -1407,9 +1416,9 @@ __global__ void __launch_bounds__(32) line_xws_kernel(const LineJobs<float> jobs
             for (int m = P - 1; m >= 1; --m) xq[m] = xq[m - 1];
             xq[0] = x;
           }
-          out[u] = live ? x : 0.f;
+          out[u] = live ? x : T(0);
         }
-        *reinterpret_cast<float4*>(row + k0) = make_float4(out[0], out[1], out[2], out[3]);
+        st4(row + k0, out);
       }
     }
     __syncwarp();
@@ -1417,7 +1426,7 @@ __global__ void __launch_bounds__(32) line_xws_kernel(const LineJobs<float> jobs
 
   // ---- write back: one bulk store per line (rows to the pitch; zeros outside lo .. hi)
   if (mine) {
-    bulk_store(job.dst + base + lane * pitch, row, 4u * N4, false);
+    bulk_store(job.dst + base + lane * pitch, row, (unsigned)(sizeof(T) * N4), false);
     bulk_store_drain();
   }
 }
@@ -2380,30 +2389,32 @@ cudaError_t launch_line(Ctx& c, int dir, int mode, const LineJobs<T>& jobs, int 
     prof_end(c);
     return cudaGetLastError();
   }
+  // x lines on one warp per 32 lines: rows [line][k] of shared memory with a pitch lpk of a
+  // multiple of 4 elements, lpk / 4 odd (conflict-free 16-byte lane accesses in FP32)
+  int lpk = ((lp.N + 3) & ~3) + 4;      // a line padded to 4 elements, plus 4 elements of slack
+  if (((lpk >> 2) & 1) == 0) lpk += 4;
+  const size_t smw = sizeof(T) * 32 * (size_t)lpk;
+  // x stiffness lines with precomputed row factors (FP32 and FP64): plane plus a two-stage ring
+  const size_t sms = smw + sizeof(T) * 2 * (P + 1) * 32 * (xws_rows<T>() + 4);
+  bool xs = dir == 0 && mode == LM_STIFF && c.line_xw && jobs.job[0].fac[0] != nullptr;
+  for (int j = 0; j < njobs && xs; ++j) {  // 16-byte aligned line starts (pitch is a multiple of 4)
+    uintptr_t a = reinterpret_cast<uintptr_t>(jobs.job[j].src) | reinterpret_cast<uintptr_t>(jobs.job[j].dst) |
+                  reinterpret_cast<uintptr_t>(jobs.job[j].aux2);
+    for (int m = 0; m < 2 * P; ++m) a |= reinterpret_cast<uintptr_t>(jobs.job[j].fac[m]);
+    xs = (a & 15) == 0 && jobs.job[j].aux2 != nullptr;
+  }
+  if (xs && sms <= (size_t)c.smem_optin) {
+    dim3 gs((unsigned)((lp.nlines + 31) / 32), njobs);
+    prof_begin(c, name, per_job * njobs);
+    line_xws_kernel<T, P><<<gs, 32, sms, c.stream>>>(jobs, lp, lpk);
+    prof_end(c);
+    return cudaGetLastError();
+  }
   if constexpr (sizeof(T) == 4) {
-    // x mass and derivative lines (FP32): one warp per 32 lines, 16-byte staging
+    // x mass and derivative lines (FP32): whole-line bulk copies
     bool xw = dir == 0 && (mode == LM_MASS || mode == LM_DERIV) && c.line_xw;
-    for (int j = 0; j < njobs; ++j)  // 16-byte aligned line starts (pitch is a multiple of 4)
+    for (int j = 0; j < njobs; ++j)
       xw = xw && ((reinterpret_cast<uintptr_t>(jobs.job[j].src) | reinterpret_cast<uintptr_t>(jobs.job[j].dst)) & 15) == 0;
-    int lpk = ((lp.N + 3) & ~3) + 4;      // a line, padded to 16 bytes, plus one 16-byte slack
-    if (((lpk >> 2) & 1) == 0) lpk += 4;  // lpk / 4 odd: conflict-free 16-byte lane accesses
-    const size_t smw = sizeof(float) * 32 * (size_t)lpk;
-    // x stiffness lines with precomputed row factors: plane plus a two-stage ring
-    const size_t sms = smw + sizeof(float) * 2 * (P + 1) * 32 * (kXwsRows + 4);
-    bool xs = dir == 0 && mode == LM_STIFF && c.line_xw && jobs.job[0].fac[0] != nullptr;
-    for (int j = 0; j < njobs && xs; ++j) {
-      uintptr_t a = reinterpret_cast<uintptr_t>(jobs.job[j].src) | reinterpret_cast<uintptr_t>(jobs.job[j].dst) |
-                    reinterpret_cast<uintptr_t>(jobs.job[j].aux2);
-      for (int m = 0; m < 2 * P; ++m) a |= reinterpret_cast<uintptr_t>(jobs.job[j].fac[m]);
-      xs = (a & 15) == 0 && jobs.job[j].aux2 != nullptr;
-    }
-    if (xs && sms <= (size_t)c.smem_optin) {
-      dim3 gs((unsigned)((lp.nlines + 31) / 32), njobs);
-      prof_begin(c, name, per_job * njobs);
-      line_xws_kernel<P><<<gs, 32, sms, c.stream>>>(jobs, lp, lpk);
-      prof_end(c);
-      return cudaGetLastError();
-    }
     if (xw && smw <= (size_t)c.smem_optin) {
       const AxisDev<T> axw = axis_dev<T>(c, 0);
       dim3 gw((unsigned)((lp.nlines + 31) / 32), njobs);
@@ -2727,16 +2738,14 @@ cudaError_t pivots_tp(Ctx& c) {
     }
     LineJobs<T> js{};
     js.job[0] = job_of<T>(nullptr, reinterpret_cast<T*>(c.pivots[d]), cf[2], 0.0, 1);
-    if (d > 0 || sizeof(T) == 4) {  // streaming (y, z) and FP32 x stiffness solves read the row factors
-      for (int m = 0; m < 2 * P; ++m) {
-        if (!c.stiff_fac[d][m]) {
-          cudaError_t e = cudaMalloc(&c.stiff_fac[d][m], c.Np * sizeof(T));
-          if (e != cudaSuccess) return e;
-          e = cudaMemsetAsync(c.stiff_fac[d][m], 0, c.Np * sizeof(T), c.stream);
-          if (e != cudaSuccess) return e;
-        }
-        js.job[0].fac[m] = reinterpret_cast<T*>(c.stiff_fac[d][m]);
+    for (int m = 0; m < 2 * P; ++m) {  // the stiffness solves of every axis read the row factors
+      if (!c.stiff_fac[d][m]) {
+        cudaError_t e = cudaMalloc(&c.stiff_fac[d][m], c.Np * sizeof(T));
+        if (e != cudaSuccess) return e;
+        e = cudaMemsetAsync(c.stiff_fac[d][m], 0, c.Np * sizeof(T), c.stream);
+        if (e != cudaSuccess) return e;
       }
+      js.job[0].fac[m] = reinterpret_cast<T*>(c.stiff_fac[d][m]);
     }
     cudaError_t e = launch_line<T, P>(c, d, LM_PIVOT, js, 1, name[d]);
     if (e != cudaSuccess) return e;
@@ -2776,12 +2785,12 @@ cudaError_t opt_in(K kern, int optin) {
 template <typename T, int P>
 cudaError_t prepare_tp(int optin) {
   cudaError_t e = opt_in(rhs_kernel<T, P, 32, 8, 8>, optin);
+  if (e == cudaSuccess) e = opt_in(line_xws_kernel<T, P>, optin);
   if (e == cudaSuccess) e = opt_in(rhs_e_kernel<T, P, 1, false>, optin);
   if (e == cudaSuccess) e = opt_in(rhs_e_kernel<T, P, 2, false>, optin);
   if constexpr (sizeof(T) == 4) {
     if (e == cudaSuccess) e = opt_in(line_xw_kernel<P, LM_MASS>, optin);
     if (e == cudaSuccess) e = opt_in(line_xw_kernel<P, LM_DERIV>, optin);
-    if (e == cudaSuccess) e = opt_in(line_xws_kernel<P>, optin);
     if (e == cudaSuccess) e = opt_in(rhs_e_kernel<T, P, 1, true>, optin);
     if (e == cudaSuccess) e = opt_in(rhs_e_kernel<T, P, 2, true>, optin);
     if (e == cudaSuccess) e = opt_in(resid_kernel<P>, optin);
