@@ -32,8 +32,12 @@ eigenvalue of M_D^{-1} S_D on axis d (Dirichlet-reduced), c_max =
 
 Pins (tests/test_oracle_material.py): uniform data give the uniform value; the
 hat equals a brute-force 3D quadrature of int eps B_rst / int B_rst; sigma = 0
-reduces a, b, c, d to the paper's constants; lambda h^2 tends to 10 for p = 2
-(the Fourier symbol of S / M at theta = pi).
+reduces a, b, c, d to the paper's constants; for sigma > 0, one E half step in
+uniform material reproduces, mode by mode, the closed-form amplification
+(1 - alpha) / (1 + alpha + beta lam) and curl response (tau / 2 eps) /
+(1 + alpha + beta lam) of the time-discrete model (a missing (1 + alpha) in a,
+b or c fails it); lambda h^2 tends to 10 for p = 2 (the Fourier symbol of S / M
+at theta = pi).
 """
 import numpy as np
 import scipy.linalg
