@@ -150,10 +150,10 @@ double adi_cfl_dt(adi_handle h);
 
 /* Allocation-free variant of adi_cfl_dt for callers that cannot allocate
  * device memory (the paper has no counterpart; this is a library service).
- * Who needs it: code that is recording a CUDA graph (cudaMalloc is not allowed
- * while a stream is being captured), services that give all device memory to
- * their own pool at start-up and forbid later cudaMalloc/cudaFree, and
- * real-time loops that must not block in the allocator.  adi_create allocates
+ * Who needs it: services that give all device memory to their own pool at
+ * start-up and forbid later cudaMalloc/cudaFree, real-time loops that must not
+ * block in the allocator, and plug-ins of a host application that owns every
+ * device allocation.  adi_create allocates
  * the whole state, so such callers cannot get the explicit time-step limit
  * from a handle at that point; this call computes the same value as
  * adi_cfl_dt of a handle created from the same nx, ny, nz, p, eps and mu.
@@ -171,7 +171,8 @@ double adi_cfl_dt(adi_handle h);
  * array and each call re-initialises what it reads, so calls that overlap on
  * the GPU (different streams, or host threads on the same device) race and
  * must be serialised by the caller.  Errors: ADI_EINVAL (NULL pointer, sizes),
- * ADI_ECUDA, ADI_ENUMERIC (eps or mu <= 0); message via adi_last_error(NULL). */
+ * ADI_ECUDA, ADI_ENUMERIC (some eps or mu element negative, zero, NaN or Inf:
+ * every element is checked on the device); message via adi_last_error(NULL). */
 adi_status adi_cfl_dt_noalloc(int nx, int ny, int nz, int p, const double* d_eps, const double* d_mu,
                               void* cuda_stream, double* dt_out);
 
@@ -221,8 +222,21 @@ adi_status adi_batch_autotune(adi_batch b, const char* cache_path);
 /* Release the batch and all its instances.  NULL is ignored. */
 void adi_batch_destroy(adi_batch b);
 
-/* Block until all work on the handle's stream is done. */
+/* Block until all work on the handle's stream is done.  Returns ADI_ETIMEOUT
+ * when a bounded device wait of a kernel gave up since the last report (an
+ * asynchronous copy was not delivered within its iteration limit; the kernel
+ * left its results unwritten and returned instead of hanging); the status is
+ * reported once and then cleared.  adi_fields reports it the same way. */
 adi_status adi_sync(adi_handle h);
+
+/* Diagnostic (not in the paper): run one of the kernels' bounded waits on a
+ * barrier that never completes, asynchronously on the handle's stream, so the
+ * time-out path can be tested without a fault.  which: 0 = the E right-hand
+ * side's tile wait, 1 = the x line solves' bulk-copy wait; budget: iterations
+ * before giving up (0 .. 2^22).  No copy is issued, so nothing is in flight when
+ * the wait gives up.  The next adi_sync returns ADI_ETIMEOUT, the one after it
+ * ADI_OK; the handle stays usable.  Errors: ADI_EINVAL (which, budget). */
+adi_status adi_wait_selftest(adi_handle h, int which, int budget);
 
 /* Per-kernel timing.  With profiling on, every kernel launch of adi_step /
  * adi_substep is bracketed by CUDA events on the handle's stream (graphs are

@@ -20,7 +20,7 @@ _PREC = {"fp64": PREC_FP64, "fp32": PREC_FP32, "mixed": PREC_MIXED}
 # every symbol declared in include/adi_maxwell.h
 EXPORTS = ("adi_create", "adi_factor", "adi_set_dt", "adi_set_stream", "adi_set_fields",
            "adi_set_source", "adi_step", "adi_substep", "adi_fields", "adi_fields_device",
-           "adi_cfl_dt", "adi_cfl_dt_noalloc", "adi_sync", "adi_set_profiling", "adi_kernel_stats", "adi_dims",
+           "adi_cfl_dt", "adi_cfl_dt_noalloc", "adi_sync", "adi_wait_selftest", "adi_set_profiling", "adi_kernel_stats", "adi_dims",
            "adi_destroy", "adi_last_error", "adi_status_string", "adi_set_line_tile",
            "adi_batch_create", "adi_batch_set_stream", "adi_batch_handle", "adi_batch_factor", "adi_batch_step", "adi_batch_sync",
            "adi_batch_autotune", "adi_batch_destroy",
@@ -75,6 +75,7 @@ def load_library(path=LIB_PATH):
         "adi_cfl_dt": (D, [H]),
         "adi_cfl_dt_noalloc": (I, [I, I, I, I, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, P(D)]),
         "adi_sync": (I, [H]),
+        "adi_wait_selftest": (I, [H, I, I]),
         "adi_set_profiling": (I, [H, I]),
         "adi_kernel_stats": (I, [H, P(AdiKernelStat), I, P(I)]),
         "adi_dims": (I, [H, P(I), P(I), P(I), P(I)]),
@@ -221,6 +222,9 @@ class Solver:
 
     def sync(self):
         self._check(self._lib.adi_sync(self.h))
+
+    def wait_selftest(self, which, budget):
+        self._check(self._lib.adi_wait_selftest(self.h, int(which), int(budget)))
 
     def set_profiling(self, on):
         self._check(self._lib.adi_set_profiling(self.h, 1 if on else 0))

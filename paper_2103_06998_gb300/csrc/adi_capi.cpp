@@ -140,8 +140,22 @@ const char* adi_last_error(adi_handle h) {
   return h->err.c_str();
 }
 
+static adi_status create_impl(int nx, int ny, int nz, int p, double dt, const double* eps, const double* mu,
+                              const double* sigma, const adi_options* opt, adi_handle* out);
+
 adi_status adi_create(int nx, int ny, int nz, int p, double dt, const double* eps, const double* mu,
                       const double* sigma, const adi_options* opt, adi_handle* out) {
+  // no exception crosses the C-ABI: a failed host allocation is ADI_ENOMEM
+  try {
+    return create_impl(nx, ny, nz, p, dt, eps, mu, sigma, opt, out);
+  } catch (const std::bad_alloc&) {
+    if (out) *out = nullptr;
+    return fail(nullptr, ADI_ENOMEM, "adi_create: host allocation failed");
+  }
+}
+
+static adi_status create_impl(int nx, int ny, int nz, int p, double dt, const double* eps, const double* mu,
+                              const double* sigma, const adi_options* opt, adi_handle* out) {
   if (!out) return fail(nullptr, ADI_EINVAL, "adi_create: out is NULL");
   *out = nullptr;
   if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, ADI_EINVAL, "adi_create: element counts must be >= 1");
@@ -221,7 +235,13 @@ adi_status adi_create(int nx, int ny, int nz, int p, double dt, const double* ep
     return fail(nullptr, ADI_ENOMEM, "adi_create: device allocation failed");
   }
   // material: NULL -> 1, 1, 0
-  std::vector<double> tmp(ne);
+  std::vector<double> tmp;
+  try {
+    tmp.resize(ne);
+  } catch (const std::bad_alloc&) {
+    free_ctx(c);
+    return fail(nullptr, ADI_ENOMEM, "adi_create: host allocation failed");
+  }
   const double* srcs[3] = {eps, mu, sigma};
   double* dsts[3] = {c->d_eps, c->d_mu, c->d_sigma};
   const double defaults[3] = {1.0, 1.0, 0.0};
@@ -412,12 +432,28 @@ adi_status adi_substep(adi_handle h, int which) {
   return ADI_OK;
 }
 
+// Read and clear the device status word: a bounded wait that gave up is
+// reported once, by the first call that synchronises after it.
 static adi_status check_device_status(adi_handle h, const char* where) {
   int err = 0;
   cudaError_t e = cudaMemcpyAsync(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, where);
-  if (err) return fail(h, ADI_ETIMEOUT, std::string(where) + ": a bounded device wait gave up (TMA tile not delivered)");
+  if (err) {
+    e = cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, where);
+    return fail(h, ADI_ETIMEOUT, std::string(where) + ": a bounded device wait gave up (TMA tile not delivered)");
+  }
+  return ADI_OK;
+}
+
+adi_status adi_wait_selftest(adi_handle h, int which, int budget) {
+  if (!h) return fail(nullptr, ADI_EINVAL, "adi_wait_selftest: NULL handle");
+  if (which < 0 || which > 1) return fail(h, ADI_EINVAL, "adi_wait_selftest: which must be 0 or 1");
+  if (budget < 0 || budget > (1 << 22)) return fail(h, ADI_EINVAL, "adi_wait_selftest: budget must be in 0..2^22");
+  cudaError_t e = adi::wait_selftest(*h, which, budget);
+  if (e != cudaSuccess) return cuda_fail(h, e, "adi_wait_selftest");
   return ADI_OK;
 }
 

@@ -230,6 +230,9 @@ cudaError_t get_fields_dev(Ctx& c, double* d_dst, int* d_bad);
 // d_bad |= 1 if any of the n doubles at d_src is NaN or Inf
 cudaError_t check_finite_dev(Ctx& c, const double* d_src, long long n, int* d_bad);
 cudaError_t set_clock(Ctx& c, double t0);
+// one bounded wait (0: E right-hand side tile wait, 1: x line bulk-copy wait) on a
+// barrier that never completes, with an iteration budget; gives up into c.d_err
+cudaError_t wait_selftest(Ctx& c, int which, int budget);
 cudaError_t make_tensor_maps(Ctx& c);
 
 // record a failure that has no handle (readable through adi_last_error(NULL))

@@ -1068,9 +1068,9 @@ __device__ __forceinline__ void bulk_store_drain() {
   asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
 }
 // Wait for phase `parity` of the barrier with an iteration limit; false if it gave up.
-__device__ __forceinline__ bool xw_bar_wait(unsigned long long* bar, unsigned parity) {
+__device__ __forceinline__ bool xw_bar_wait(unsigned long long* bar, unsigned parity, int budget = 1 << 22) {
   const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
-  for (int it = 0; it < (1 << 22); ++it) {
+  for (int it = 0; it < budget; ++it) {
     unsigned ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -1735,9 +1735,9 @@ __device__ __forceinline__ void tma_tile(const CUtensorMap* map, T* dst, unsigne
 }
 
 // Wait for phase `parity` of the barrier with an iteration limit; false if it gave up.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, int budget = 1 << 22) {
   const unsigned a = smem_addr(bar);
-  for (int it = 0; it < (1 << 22); ++it) {
+  for (int it = 0; it < budget; ++it) {
     unsigned ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -1954,6 +1954,23 @@ __global__ void __launch_bounds__(rhs2::NT, sizeof(T) == 4 ? ADI_RHS_MINB : 1)
       }
     }
   }
+}
+
+// ------------------------------------------------- bounded-wait self-test
+// Runs one of the kernels' bounded waits (which = 0: the E right-hand side's
+// tile wait, 1: the x line solves' bulk-copy wait) on a barrier that expects
+// bytes no copy will ever deliver: nothing is issued, so nothing is in flight
+// when the wait gives up.  On give-up the kernel records it in the device status
+// word exactly as the step kernels do (bit 0), which the host reports as
+// ADI_ETIMEOUT.
+__global__ void wait_selftest_kernel(int which, int budget, int* err) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x != 0) return;
+  rhs2::mbar_init(&bar);
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  xw_bar_expect(&bar, 16);  // one arrival, 16 bytes that never come
+  const bool ok = which == 0 ? rhs2::mbar_wait(&bar, 0, budget) : xw_bar_wait(&bar, 0, budget);
+  if (!ok) atomicOr(err, 1);
 }
 
 // ------------------------------------------------------------ conversions
@@ -2925,6 +2942,11 @@ cudaError_t make_tensor_maps(Ctx& c) {
   for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = encode_map(c, enc, c.half[i], &c.tmap_half[i]);
   c.tmaps_ok = e == cudaSuccess;
   return e;
+}
+
+cudaError_t wait_selftest(Ctx& c, int which, int budget) {
+  wait_selftest_kernel<<<1, 32, 0, c.stream>>>(which, budget, c.d_err);
+  return cudaGetLastError();
 }
 
 cudaError_t set_clock(Ctx& c, double t0) {

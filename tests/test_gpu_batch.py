@@ -9,6 +9,7 @@ import pytest
 
 from oracle import maxwell_adi as ma
 from paper_2103_06998_gb300 import inputs
+from parity_check import assert_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -51,14 +52,14 @@ def test_batch_equals_instances_alone(prec):
         a.close()
         assert np.array_equal(got[i][0], ref), i
         assert abs(got[i][1] - t) < 1e-12
-    # instance 0 against the FP64 oracle
-    inst = insts[0]
-    prob = ma.make_problem(inst["n"], inst["p"], inst["dt"], inst["eps"], inst["mu"], inst["sigma"])
-    src = inst["source"]
-    ma.set_source(prob, src["x0"], src["comp"], src["amp"], src["f0"], src["t0"], src["s"])
-    ref, _ = ma.run(prob, ma.apply_dirichlet(list(states[0])), 1.3, 3)
-    err = np.sqrt(sum(np.sum((got[0][0][c] - ref[c]) ** 2) for c in range(6)) / sum(np.sum(r ** 2) for r in ref))
-    assert err < (3e-5 if prec == "fp32" else 3e-11)
+    # every instance (p = 2 and p = 3) against the FP64 oracle, element by element
+    from test_gpu_parity import tol
+    for i, inst in enumerate(insts):
+        prob = ma.make_problem(inst["n"], inst["p"], inst["dt"], inst["eps"], inst["mu"], inst["sigma"])
+        src = inst["source"]
+        ma.set_source(prob, src["x0"], src["comp"], src["amp"], src["f0"], src["t0"], src["s"])
+        ref, _ = ma.run(prob, ma.apply_dirichlet(list(states[i])), 1.3, 3)
+        assert_parity(list(got[i][0]), ref, 3 * tol(prec, inst["p"]), what="batch instance %d" % i)
     b.close()
 
 
