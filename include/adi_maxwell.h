@@ -142,6 +142,32 @@ adi_status adi_fields(adi_handle h, double* EH, double* t);
  * handle's stream).  Asynchronous. */
 adi_status adi_fields_device(adi_handle h, void* dev_ptr, void* cuda_stream);
 
+/* Norms of the current state as functions on the unit cube: the paper plots the
+ * L2 and H1 norms of E and H over time for the head simulation (section
+ * "Incorporating non-regular material data", Figure head_norms) and measures the
+ * manufactured-solution errors in the L2 and H(curl) norms (section "Numerical
+ * code verification with manufactured solution").
+ *  out[6] (host) = { ||E||_L2, ||H||_L2, ||E||_H1, ||H||_H1, ||E||_Hcurl, ||H||_Hcurl },
+ *  ||u||_H1^2 = ||u||_L2^2 + sum_i ||grad u_i||^2, ||u||_Hcurl^2 = ||u||_L2^2 + ||curl u||^2.
+ * Computed on the device as quadratic forms of the 1D matrices (c . (M(x)M(x)M) c
+ * and the like; exact integrals of the B-spline fields), summed in FP64 from
+ * the working precision; uses the right-hand-side scratch arrays, so it runs
+ * in stream order between steps.  Synchronises the handle's stream.
+ * Errors: ADI_EINVAL, ADI_ECUDA, ADI_ENUMERIC (NaN or Inf in the state). */
+adi_status adi_norms(adi_handle h, double* out);
+
+/* Values of one state component on a uniform grid of a coordinate plane (the
+ * paper's field pictures are cross sections along an OYZ plane, Figures head2
+ * and head3), written headless to a host buffer.
+ *  comp: 0..5 = E1, E2, E3, H1, H2, H3; axis: 0 (plane x = pos), 1 (y), 2 (z);
+ *  pos in [0, 1]; the grid points are u_j = j / (nu - 1), v_k = k / (nv - 1) over
+ *  the two other axes in x, y, z order (axis 0: u = y, v = z);
+ *  out (host, caller-owned): nu * nv doubles, out[k * nu + j].
+ * nu, nv >= 2 and (1 + nu + nv)(p + 2) + nu nv <= 6 N_c (the handle's staging
+ * buffer holds the point tables and the result).  Synchronises the handle's
+ * stream.  Errors: ADI_EINVAL, ADI_ECUDA. */
+adi_status adi_plane(adi_handle h, int comp, int axis, double pos, int nu, int nv, double* out);
+
 /* Explicit-scheme stability limit used to choose dt (not in the paper):
  * 2 / (c_max sqrt(lambda_x + lambda_y + lambda_z)), lambda_d the largest
  * eigenvalue of M^-1 S on axis d (Dirichlet-reduced), c_max =

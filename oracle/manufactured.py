@@ -142,10 +142,3 @@ def errors(state, n, p, t, exact=u_A):
         cl = sum(np.sum(W * (curl_h[i] - curl_ex[i]) ** 2) for i in range(3))
         res.append((np.sqrt(l2), np.sqrt(l2 + cl)))
     return res[0][0], res[1][0], res[0][1], res[1][1]
-
-
-def l2_norm(state, n, p, comps=range(6)):
-    grid = quad_grid(n, p)
-    gx, gy, gz = grid
-    W = np.einsum("k,j,i->kji", gz[1], gy[1], gx[1])
-    return np.sqrt(sum(np.sum(W * evaluate(state[i], grid) ** 2) for i in comps))

@@ -20,7 +20,7 @@ _PREC = {"fp64": PREC_FP64, "fp32": PREC_FP32, "mixed": PREC_MIXED}
 # every symbol declared in include/adi_maxwell.h
 EXPORTS = ("adi_create", "adi_factor", "adi_set_dt", "adi_set_stream", "adi_set_fields",
            "adi_set_source", "adi_step", "adi_substep", "adi_fields", "adi_fields_device",
-           "adi_cfl_dt", "adi_cfl_dt_noalloc", "adi_sync", "adi_wait_selftest", "adi_set_profiling", "adi_kernel_stats", "adi_dims",
+           "adi_cfl_dt", "adi_cfl_dt_noalloc", "adi_sync", "adi_wait_selftest", "adi_norms", "adi_plane", "adi_set_profiling", "adi_kernel_stats", "adi_dims",
            "adi_destroy", "adi_last_error", "adi_status_string", "adi_set_line_tile",
            "adi_batch_create", "adi_batch_set_stream", "adi_batch_handle", "adi_batch_factor", "adi_batch_step", "adi_batch_sync",
            "adi_batch_autotune", "adi_batch_destroy",
@@ -76,6 +76,8 @@ def load_library(path=LIB_PATH):
         "adi_cfl_dt_noalloc": (I, [I, I, I, I, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, P(D)]),
         "adi_sync": (I, [H]),
         "adi_wait_selftest": (I, [H, I, I]),
+        "adi_norms": (I, [H, P(D)]),
+        "adi_plane": (I, [H, I, I, D, I, I, P(D)]),
         "adi_set_profiling": (I, [H, I]),
         "adi_kernel_stats": (I, [H, P(AdiKernelStat), I, P(I)]),
         "adi_dims": (I, [H, P(I), P(I), P(I), P(I)]),
@@ -222,6 +224,18 @@ class Solver:
 
     def sync(self):
         self._check(self._lib.adi_sync(self.h))
+
+    def norms(self):
+        """[L2(E), L2(H), H1(E), H1(H), Hcurl(E), Hcurl(H)] of the current state."""
+        out = np.zeros(6)
+        self._check(self._lib.adi_norms(self.h, _dptr(out)))
+        return out
+
+    def plane(self, comp, axis, pos, nu, nv):
+        """Component ``comp`` on the plane x_axis = pos, an (nv, nu) array."""
+        out = np.zeros((nv, nu))
+        self._check(self._lib.adi_plane(self.h, int(comp), int(axis), float(pos), int(nu), int(nv), _dptr(out)))
+        return out
 
     def wait_selftest(self, which, budget):
         self._check(self._lib.adi_wait_selftest(self.h, int(which), int(budget)))

@@ -35,7 +35,8 @@ void free_ctx(Ctx* c0) {
   adi_ctx* c = static_cast<adi_ctx*>(c0);
   if (c->graph) cudaGraphExecDestroy(c->graph);
   for (auto* l : c->pending) delete l;
-  void* ptrs[] = {c->d_eps, c->d_mu, c->d_sigma, c->stage, c->tab, c->tab64, c->d_clock_t0, c->d_clock_step, c->d_err, c->d_bad};
+  void* ptrs[] = {c->d_eps,        c->d_mu,  c->d_sigma, c->stage,  c->tab,   c->tab64,
+                  c->d_clock_t0,   c->d_clock_step, c->d_err, c->d_bad, c->d_diag};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int i = 0; i < 6; ++i) {
@@ -229,6 +230,7 @@ static adi_status create_impl(int nx, int ny, int nz, int p, double dt, const do
   alloc((void**)&c->d_clock_step, sizeof(long long));
   alloc((void**)&c->d_err, sizeof(int));
   alloc((void**)&c->d_bad, sizeof(int));
+  alloc((void**)&c->d_diag, 8 * sizeof(double));
   if (!ok) {
     cudaGetLastError();
     free_ctx(c);
@@ -491,6 +493,60 @@ adi_status adi_fields_device(adi_handle h, void* dev_ptr, void* stream) {
                                       h->N[0] * h->esize, (size_t)h->N[1] * h->N[2], cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "adi_fields_device");
   }
+  return ADI_OK;
+}
+
+adi_status adi_norms(adi_handle h, double* out) {
+  if (!h) return fail(nullptr, ADI_EINVAL, "adi_norms: NULL handle");
+  if (!out) return fail(h, ADI_EINVAL, "adi_norms: out is NULL");
+  double acc[6] = {};
+  cudaError_t e = adi::field_norms_dev(*h, h->d_diag);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(acc, h->d_diag, sizeof(acc), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "adi_norms");
+  // rounding can leave a tiny negative sum for a zero field
+  for (double& v : acc) v = v > 0.0 ? v : 0.0;
+  out[0] = std::sqrt(acc[0]);
+  out[1] = std::sqrt(acc[1]);
+  out[2] = std::sqrt(acc[0] + acc[2]);
+  out[3] = std::sqrt(acc[1] + acc[3]);
+  out[4] = std::sqrt(acc[0] + acc[4]);
+  out[5] = std::sqrt(acc[1] + acc[5]);
+  for (int i = 0; i < 6; ++i)
+    if (!std::isfinite(out[i])) return fail(h, ADI_ENUMERIC, "adi_norms: NaN or Inf in the state");
+  return ADI_OK;
+}
+
+adi_status adi_plane(adi_handle h, int comp, int axis, double pos, int nu, int nv, double* out) {
+  if (!h) return fail(nullptr, ADI_EINVAL, "adi_plane: NULL handle");
+  if (!out) return fail(h, ADI_EINVAL, "adi_plane: out is NULL");
+  if (comp < 0 || comp > 5 || axis < 0 || axis > 2) return fail(h, ADI_EINVAL, "adi_plane: comp 0..5, axis 0..2");
+  if (!(pos >= 0.0 && pos <= 1.0)) return fail(h, ADI_EINVAL, "adi_plane: pos must lie in [0, 1]");
+  if (nu < 2 || nv < 2) return fail(h, ADI_EINVAL, "adi_plane: nu, nv must be >= 2");
+  const int rec = h->p + 2;
+  const long long ntab = (long long)rec * (1 + nu + nv);
+  const long long nout = (long long)nu * nv;
+  if (ntab + nout > 6LL * (long long)h->Nc)
+    return fail(h, ADI_EINVAL, "adi_plane: nu * nv exceeds the handle's staging buffer (6 N_c doubles)");
+  // 1D point records (first B-spline index, p + 1 values): the plane's coordinate, then the u and v points
+  const int o0 = axis == 0 ? 1 : 0, o1 = axis == 2 ? 1 : 2;
+  std::vector<double> tab((size_t)ntab, 0.0);
+  auto put = [&](long long slot, int d, double x) {
+    double v[adi::kMaxP + 1] = {};
+    const int e = adi::point_basis(h->n[d], h->p, x, v);
+    tab[(size_t)(slot * rec)] = (double)e;
+    for (int q = 0; q <= h->p; ++q) tab[(size_t)(slot * rec + 1 + q)] = v[q];
+  };
+  put(0, axis, pos);
+  for (int j = 0; j < nu; ++j) put(1 + j, o0, (double)j / (nu - 1));
+  for (int k = 0; k < nv; ++k) put(1 + nu + k, o1, (double)k / (nv - 1));
+  double* d_tab = static_cast<double*>(h->stage);
+  double* d_out = d_tab + ntab;
+  cudaError_t e = cudaMemcpyAsync(d_tab, tab.data(), (size_t)ntab * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = adi::plane_dev(*h, comp, axis, nu, nv, d_tab, d_out);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_out, (size_t)nout * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "adi_plane");
   return ADI_OK;
 }
 

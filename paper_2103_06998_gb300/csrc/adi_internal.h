@@ -208,6 +208,7 @@ struct Ctx {
   bool tmaps_ok = false;
   int* d_err = nullptr;  // device status word written by bounded waits
   int* d_bad = nullptr;  // device flag: a value that is not finite (field checks)
+  double* d_diag = nullptr;  // 8 doubles: sums of the norm diagnostics
 
   // graph of one step
   cudaGraphExec_t graph = nullptr;
@@ -230,6 +231,11 @@ cudaError_t get_fields_dev(Ctx& c, double* d_dst, int* d_bad);
 // d_bad |= 1 if any of the n doubles at d_src is NaN or Inf
 cudaError_t check_finite_dev(Ctx& c, const double* d_src, long long n, int* d_bad);
 cudaError_t set_clock(Ctx& c, double t0);
+// squared-norm sums of the state into d_acc[6] (zeroed first):
+// [int |E|^2, int |H|^2, int |grad E|^2, int |grad H|^2, int |curl E|^2, int |curl H|^2]
+cudaError_t field_norms_dev(Ctx& c, double* d_acc);
+// component comp on a plane grid; d_tab: 1D point records (first index, p+1 values)
+cudaError_t plane_dev(Ctx& c, int comp, int axis, int nu, int nv, const double* d_tab, double* d_out);
 // one bounded wait (0: E right-hand side tile wait, 1: x line bulk-copy wait) on a
 // barrier that never completes, with an iteration budget; gives up into c.d_err
 cudaError_t wait_selftest(Ctx& c, int which, int budget);

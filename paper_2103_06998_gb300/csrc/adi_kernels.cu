@@ -21,6 +21,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 #include <cstdio>
 
@@ -2832,6 +2833,154 @@ cudaError_t prepare_t(int p, int optin) {
   }
 }
 
+// ------------------------------------------------------------ diagnostics
+// Norms of the state as functions on the unit cube (the paper's L2 and H1 norms
+// of E and H over time in the head experiment, Figure head_norms, and the L2 /
+// H(curl) norms of its manufactured-solution errors).  Each squared norm is a
+// quadratic form of the Kronecker 1D matrices: for coefficients c of one
+// component, int u^2 = c . (M(x)M(x)M) c and int |grad u|^2 =
+// c . (S(x)M(x)M + M(x)S(x)M + M(x)M(x)S) c; int |curl u|^2 adds, for each curl
+// component (d_a u_b - d_b u_a), the two squares and minus twice the cross
+// term, e.g. int d2 u3 d3 u2 = u2 . (M(x)A(x)B) u3 (A: derivative on the trial,
+// B on the test function).  The generic right-hand-side kernel applies the
+// terms into the scratch arrays; dot3_kernel forms sum_i c_i . (K c)_i in FP64.
+template <typename T>
+__global__ void dot3_kernel(const T* __restrict__ a0, const T* __restrict__ a1, const T* __restrict__ a2,
+                            const T* __restrict__ b0, const T* __restrict__ b1, const T* __restrict__ b2, int Nx,
+                            int pitch, long long rows, double* out) {
+  __shared__ double part[32];
+  double s = 0.0;
+  const long long n = rows * Nx;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < n; g += (long long)gridDim.x * blockDim.x) {
+    const long long o = (g / Nx) * pitch + (g % Nx);
+    s += (double)a0[o] * (double)b0[o] + (double)a1[o] * (double)b1[o] + (double)a2[o] * (double)b2[o];
+  }
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) s += __shfl_down_sync(0xffffffffu, s, d);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) s += __shfl_down_sync(0xffffffffu, s, d);
+    if (threadIdx.x == 0) atomicAdd(out, s);
+  }
+}
+
+// Values of one coefficient array on a uniform grid of a plane: per output
+// point the (p+1)^3 B-splines that are nonzero there, from host tables
+// tab[axis][point] = (first index, p+1 values) of the three 1D point sets.
+template <typename T>
+__global__ void plane_kernel(const T* __restrict__ u, int Ny, int pitch, int p, int axis, int nu, int nv,
+                             const double* __restrict__ tab, double* __restrict__ out) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nu * nv) return;
+  const int j = idx % nu, k = idx / nu;
+  const int rec = p + 2;
+  const double* t0 = tab;                      // the plane's own coordinate (one point)
+  const double* tu = tab + rec;                // nu points
+  const double* tv = tab + rec * (1 + nu);     // nv points
+  // per axis x, y, z: the record of this output point
+  const double* r[3];
+  const int o0 = axis == 0 ? 1 : 0;            // first of the two in-plane axes
+  const int o1 = axis == 2 ? 1 : 2;
+  r[axis] = t0;
+  r[o0] = tu + (long long)j * rec;
+  r[o1] = tv + (long long)k * rec;
+  const int ix = (int)r[0][0], iy = (int)r[1][0], iz = (int)r[2][0];
+  double v = 0.0;
+  for (int cz = 0; cz <= p; ++cz)
+    for (int cy = 0; cy <= p; ++cy) {
+      const double wyz = r[2][1 + cz] * r[1][1 + cy];
+      const T* row = u + ((long long)(iz + cz) * Ny + (iy + cy)) * pitch + ix;
+      for (int cx = 0; cx <= p; ++cx) v += wyz * r[0][1 + cx] * (double)row[cx];
+    }
+  out[idx] = v;
+}
+
+template <typename T, int P>
+cudaError_t norms_tp(Ctx& c, double* d_acc) {
+  T** cur = reinterpret_cast<T**>(c.cur);
+  T** R = reinterpret_cast<T**>(c.rhs);
+  auto term = [](int field, int out, int ox, int oy, int oz, float sign) {
+    Term t{};
+    t.field = field;
+    t.out = out;
+    t.op[0] = ox;
+    t.op[1] = oy;
+    t.op[2] = oz;
+    t.coef = CF_ONE;
+    t.sign = sign;
+    return t;
+  };
+  const long long rows = (long long)c.N[1] * c.N[2];
+  for (int g = 0; g < 2; ++g) {  // E, then H
+    RhsParams<T> prm{};
+    for (int i = 0; i < 3; ++i) {
+      prm.fields[i] = cur[3 * g + i];
+      prm.out[i] = R[i];
+    }
+    prm.nfields = 3;
+    for (int k = 0; k < 5; ++k) prm.coef[k] = nullptr;
+    for (int d = 0; d < 3; ++d) prm.ax[d] = axis_dev<T>(c, d);
+    prm.Nx = c.N[0];
+    prm.Ny = c.N[1];
+    prm.Nz = c.N[2];
+    prm.pitch = c.pitch;
+    prm.src_comp = -1;
+    prm.clock_t0 = c.d_clock_t0;
+    prm.clock_step = c.d_clock_step;
+    prm.advance_clock = 0;
+    for (int form = 0; form < 3; ++form) {
+      int n = 0;
+      if (form == 0) {          // int u_i^2
+        for (int i = 0; i < 3; ++i) prm.terms[n++] = term(i, i, OP_M, OP_M, OP_M, 1.f);
+      } else if (form == 1) {   // int |grad u_i|^2
+        for (int i = 0; i < 3; ++i) {
+          prm.terms[n++] = term(i, i, OP_S, OP_M, OP_M, 1.f);
+          prm.terms[n++] = term(i, i, OP_M, OP_S, OP_M, 1.f);
+          prm.terms[n++] = term(i, i, OP_M, OP_M, OP_S, 1.f);
+        }
+      } else {                  // int |curl u|^2, terms grouped by the field they read
+        prm.terms[n++] = term(0, 0, OP_M, OP_M, OP_S, 1.f);   // (d3 u1)^2
+        prm.terms[n++] = term(0, 0, OP_M, OP_S, OP_M, 1.f);   // (d2 u1)^2
+        prm.terms[n++] = term(0, 2, OP_B, OP_M, OP_A, -2.f);  // -2 d3 u1 d1 u3
+        prm.terms[n++] = term(1, 1, OP_M, OP_M, OP_S, 1.f);   // (d3 u2)^2
+        prm.terms[n++] = term(1, 1, OP_S, OP_M, OP_M, 1.f);   // (d1 u2)^2
+        prm.terms[n++] = term(1, 0, OP_A, OP_B, OP_M, -2.f);  // -2 d1 u2 d2 u1
+        prm.terms[n++] = term(2, 2, OP_M, OP_S, OP_M, 1.f);   // (d2 u3)^2
+        prm.terms[n++] = term(2, 2, OP_S, OP_M, OP_M, 1.f);   // (d1 u3)^2
+        prm.terms[n++] = term(2, 1, OP_M, OP_A, OP_B, -2.f);  // -2 d2 u3 d3 u2
+      }
+      prm.nterms = n;
+      cudaError_t e = launch_rhs<T, P>(c, prm, "norm_form", (double)c.Nc * sizeof(T) * 6.0);
+      if (e != cudaSuccess) return e;
+      dot3_kernel<T><<<grid_for(rows * c.N[0], 256), 256, 0, c.stream>>>(
+          prm.fields[0], prm.fields[1], prm.fields[2], R[0], R[1], R[2], c.N[0], c.pitch, rows, d_acc + 2 * form + g);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t norms_t(Ctx& c, double* d_acc) {
+  switch (c.p) {
+    case 1: return norms_tp<T, 1>(c, d_acc);
+    case 2: return norms_tp<T, 2>(c, d_acc);
+    default: return norms_tp<T, 3>(c, d_acc);
+  }
+}
+
+template <typename T>
+cudaError_t plane_t(Ctx& c, int comp, int axis, int nu, int nv, const double* d_tab, double* d_out) {
+  const int n = nu * nv;
+  plane_kernel<T><<<(n + 255) / 256, 256, 0, c.stream>>>(reinterpret_cast<const T*>(c.cur[comp]), c.N[1], c.pitch,
+                                                          c.p, axis, nu, nv, d_tab, d_out);
+  return cudaGetLastError();
+}
+
 unsigned grid_for(long long n, int threads) {
   long long b = (n + threads - 1) / threads;
   if (b > 152LL * 64) b = 152LL * 64;
@@ -2862,9 +3011,26 @@ cudaError_t upload_tables_f64(Ctx& c, int optin) {
   return e;
 }
 cudaError_t run_substep_f64(Ctx& c, int which) { return substep_t<double>(c, which); }
+cudaError_t norms_f64(Ctx& c, double* d_acc) { return norms_t<double>(c, d_acc); }
+cudaError_t plane_f64(Ctx& c, int comp, int axis, int nu, int nv, const double* d_tab, double* d_out) {
+  return plane_t<double>(c, comp, axis, nu, nv, d_tab, d_out);
+}
 #else
 cudaError_t upload_tables_f64(Ctx& c, int optin);
 cudaError_t run_substep_f64(Ctx& c, int which);
+cudaError_t norms_f64(Ctx& c, double* d_acc);
+cudaError_t plane_f64(Ctx& c, int comp, int axis, int nu, int nv, const double* d_tab, double* d_out);
+
+cudaError_t field_norms_dev(Ctx& c, double* d_acc) {
+  cudaError_t e = cudaMemsetAsync(d_acc, 0, 6 * sizeof(double), c.stream);
+  if (e != cudaSuccess) return e;
+  return c.precision == ADI_PREC_FP64 ? norms_f64(c, d_acc) : norms_t<float>(c, d_acc);
+}
+
+cudaError_t plane_dev(Ctx& c, int comp, int axis, int nu, int nv, const double* d_tab, double* d_out) {
+  return c.precision == ADI_PREC_FP64 ? plane_f64(c, comp, axis, nu, nv, d_tab, d_out)
+                                      : plane_t<float>(c, comp, axis, nu, nv, d_tab, d_out);
+}
 
 cudaError_t upload_tables(Ctx& c) {
   int optin = 0;
