@@ -54,7 +54,7 @@ def test_mixed_step_matches_oracle(n, p, mat):
     src = inputs.dipole(2103)
     e_ref, m_ref = _step(n, p, 0.03, mat, True, src)
     e_raw, _ = _step(n, p, 0.03, mat, False, src)
-    assert e_ref < tol("fp32", p) and m_ref < tol("fp32", p), (e_ref, m_ref)
+    assert e_ref < tol("fp32", p, mat) and m_ref < tol("fp32", p, mat), (e_ref, m_ref)
     assert e_raw > 10 * e_ref and e_raw < 1e-2, (e_raw, e_ref)
 
 

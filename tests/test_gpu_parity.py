@@ -1,11 +1,17 @@
 """GPU parity: the CUDA path (through the C-ABI) against the FP64 CPU oracle.
 
-Tolerances: the FP64 GPU path must agree with the oracle to 1e-11 relative L2
-(only the summation order differs); the FP32 path to 1e-5 relative L2 per step
-from an identical state (coefficient l2 norm over all six components) for
-p <= 2.  FP32 rounding after the line solves grows with the condition number
-of the 3D mass matrix, kappa_1D^3; for p = 3 the bound is scaled by
-(kappa_1D(3) / kappa_1D(2))^3 (about 16), computed below.
+Tolerances (every check bounds both the relative l2 over all six components and
+the worst point of each component, tests/parity_check.py): the FP64 GPU path
+must agree with the oracle to 1e-11 (only the summation order differs); the
+FP32 path to 1e-5 per step from an identical state, the benchmark spec's bound.
+One case needs more: p = 3 with white-noise material (random eps, mu, sigma per
+element, the general-mu H path) and a white-noise state, where FP32 measured
+1.1e-5 relative l2 and 2.5e-5 at the worst point.  The FP32 rounding of the
+right-hand side is amplified by the inverse 3D mass matrix, whose condition
+number grows like kappa_1D(p)^3; for p = 3 that is about 16 times the p = 2
+value, and a white-noise state puts its error into the highest (most
+amplified) modes.  That case is checked at 3e-5; p = 3 on the head maps of the
+workloads stays at 1e-5.
 """
 import numpy as np
 import pytest
@@ -21,12 +27,10 @@ pytestmark = pytest.mark.gpu
 TOL = {"fp64": 1e-11, "fp32": 1e-5}
 
 
-def tol(prec, p):
-    if prec == "fp64" or p <= 2:
-        return TOL[prec]
-    from oracle import bspline
-    k = lambda q: np.linalg.cond(bspline.matrices_1d(32, q)[0])
-    return TOL[prec] * (k(p) / k(2)) ** 3
+def tol(prec, p, mat="head"):
+    if prec == "fp32" and p == 3 and mat == "random":
+        return 3e-5   # white-noise material and state, p = 3 (see the module docstring)
+    return TOL[prec]
 
 
 def _adi():
@@ -58,7 +62,7 @@ def _setup(n, p, tau, mat, prec, src=None, seed=3, t0=0.0):
 
 # ragged multi-tile sizes: RHS tiles are 32 x 8 x 8, line tiles 64 lines
 SMALL = [((37, 19, 11), 2, "head"), ((13, 30, 9), 1, "random"), ((11, 9, 21), 3, "random"),
-         ((5, 4, 3), 2, "uniform")]
+         ((5, 4, 3), 2, "uniform"), ((19, 14, 23), 3, "head")]
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
@@ -81,7 +85,7 @@ def test_each_substep_matches_oracle(n, p, mat, prec):
     got, tt = s.fields()
     s.close()
     assert abs(tt - (t + tau)) < 1e-12
-    assert_parity(got, E_new + H_new, tol(prec, p), what="%s p=%d %s" % (prec, p, mat))
+    assert_parity(got, E_new + H_new, tol(prec, p, mat), what="%s p=%d %s" % (prec, p, mat))
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
@@ -106,6 +110,22 @@ def test_graph_step_equals_substeps(prec):
     s.close()
     s2.close()
     assert np.array_equal(got, got2)
+
+
+@pytest.mark.parametrize("fac", [4.0, 40.0])
+def test_one_step_at_large_tau(fac):
+    # one FP32 step at the workloads' tau = 4 dt_CFL and at 40 dt_CFL, where c is
+    # about 50 h^2 in air (the stiffness lines are dominated by c S)
+    n, p = (40, 36, 33), 2
+    eps, mu, sigma, _ = inputs.head_map(n, 2103)
+    tau = fac * material.cfl_dt(n, p, material.row_hats(eps, n, p), material.row_hats(mu, n, p))
+    src = inputs.dipole(2103)
+    prob, s, st = _setup(n, p, tau, "head", "fp32", src=src, t0=1.6)
+    ref, _ = ma.run(prob, st, 1.6, 1)
+    s.step(1)
+    got, _ = s.fields()
+    s.close()
+    assert_parity(got, ref, TOL["fp32"], what="fp32 tau = %g dt_CFL" % fac)
 
 
 def test_config1_manufactured_fp64_against_oracle_and_exact():
