@@ -60,17 +60,20 @@ typedef enum {
  *  ADI_PREC_MIXED: FP32 state and line solves; in each E half step the
  *  right-hand side is contracted from field tiles rounded to BF16 with FP32
  *  accumulation, giving E*; then one refinement: the residual
- *  r = RHS - T E* of the E system T E = RHS is evaluated in FP64 arithmetic
- *  (from the FP32 state), T delta = r is solved in FP32 and E = E* + delta.
- *  The 1D factorisations are FP64 in every mode.  The paper states no
- *  precision; this mode is an addition. */
+ *  r = RHS - T E* of the E system T E = RHS is evaluated to about 48
+ *  significant bits (from the FP32 state), T delta = r is solved in FP32 and
+ *  E = E* + delta.  The residual's arithmetic is compensated double-float on
+ *  the FP32 pipe (TwoSum, TwoProduct by FMA) by default, or FP64 with
+ *  mixed_fp64_residual = 1.  The 1D factorisations are FP64 in every mode.
+ *  The paper states no precision; this mode is an addition. */
 enum { ADI_PREC_FP64 = 0, ADI_PREC_FP32 = 1, ADI_PREC_MIXED = 2 };
 
 typedef struct {
   int precision;        /* ADI_PREC_FP32 (default), ADI_PREC_FP64 or ADI_PREC_MIXED */
   int use_graph;        /* 1 (default): adi_step replays a captured CUDA graph of one step */
   int mixed_no_refine;  /* ADI_PREC_MIXED only: 1 skips the refinement (E = E*, for error studies) */
-  int reserved[5];      /* must be 0 */
+  int mixed_fp64_residual; /* ADI_PREC_MIXED only: 1 evaluates the residual in FP64 (default 0: float-float) */
+  int reserved[4];      /* must be 0 */
 } adi_options;
 
 /* Create a problem on the unit cube.

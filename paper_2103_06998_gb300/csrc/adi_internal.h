@@ -145,7 +145,8 @@ struct Ctx {
   int N[3] = {0, 0, 0};  // coefficients per axis
   int p = 2;
   int precision = ADI_PREC_FP32;  // FP32 and MIXED keep FP32 state (element type float)
-  int mixed_refine = 0;           // MIXED: one FP64 residual refinement per E half step
+  int mixed_refine = 0;           // MIXED: one residual refinement per E half step
+  int mixed_fp64_residual = 0;    // MIXED: the residual in FP64 arithmetic (default: float-float on the FP32 pipe)
   int use_graph = 1;
   int line_tile = 0;  // lines per line-solve CTA (0: largest that leaves two CTAs per SM)
   bool line_stream = true;  // y / z stiffness solves on the streaming kernel (precomputed factors)
@@ -188,6 +189,7 @@ struct Ctx {
   void* tab = nullptr;
   size_t tab_bytes = 0;
   double* tab64 = nullptr;  // MIXED: the band tables in FP64 for the residual
+  float2* tabff = nullptr;  // MIXED: the same tables as float pairs (hi, lo) for the float-float residual
   size_t tab64_bytes = 0;
   Axis1D axes[3];
   LuConst luconst[3][2];  // per axis: full and Dirichlet-reduced mass LU

@@ -186,6 +186,220 @@ __global__ void __launch_bounds__(TX* TY) rhs_kernel(const RhsParams<T> prm) {
     *prm.clock_step += 1;
 }
 
+// ------------------------------------- mixed-mode E right-hand side (BF16 MMA)
+// The contraction of eq. dupa1ab (and its half-step-2 analogue) with BF16
+// operands on the tensor cores: per 32 x 8 x 8 output tile and Kronecker term,
+// the first pass (along x) is a GEMM
+//     X[(z, y)][xo] = sum_k T[(z, y)][k] * Wx^T[k][xo]
+// of the haloed field tile T (rows: the (z, y) pairs of the haloed tile, k: the
+// haloed x index, both BF16: the field rounded to BF16) with the banded 1D
+// operator of the term's x factor (BF16), accumulated in FP32 by
+// mma.sync.m16n8k16 (M = 16 tile rows, N = 8 outputs, K = 16 haloed x values;
+// K is padded from 32 + 2p to 48 with zeros).  A operands come from shared
+// memory by ldmatrix, B operands are built in registers from the band table.
+// The y and z passes and the row scaling by a, b, c then run in FP32 on the
+// CUDA cores from the FP32 partial sums.  The refinement that follows (float-
+// float or FP64 residual) removes the BF16 error of this contraction.
+template <int P>
+struct MmaTile {
+  static constexpr int TX = 32, TY = 8, TZ = 8;
+  static constexpr int HX = TX + 2 * P, HY = TY + 2 * P, HZ = TZ + 2 * P;
+  static constexpr int ROWS = HZ * HY;               // (z, y) rows of the haloed tile
+  static constexpr int MT = (ROWS + 15) / 16;        // m tiles of 16 rows
+  static constexpr int KS = 3;                       // k steps of 16 (K padded to 48 >= HX)
+  static constexpr int TS = 56;                      // BF16 tile row stride (112 B: conflict-free ldmatrix)
+  static constexpr int XS = 36;                      // FP32 row stride of the x-pass result
+  static constexpr size_t TILE_B = sizeof(__nv_bfloat16) * (size_t)MT * 16 * TS;
+  static constexpr size_t X_B = sizeof(float) * (size_t)ROWS * XS;
+  static constexpr size_t Y_B = sizeof(float) * (size_t)HZ * TY * TX;
+  // B fragments of the three x operators M, A, B: [op][n tile][k step][half][lane]
+  static constexpr size_t BF_B = sizeof(unsigned) * 3 * 4 * KS * 2 * 32;
+  static constexpr size_t BYTES = TILE_B + X_B + Y_B + BF_B;
+  static_assert(HX <= 16 * KS, "x halo exceeds the padded K");
+};
+
+__device__ __forceinline__ unsigned pack_bf16x2(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);  // .x = lo (lower address)
+  return *reinterpret_cast<const unsigned*>(&v);
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) rhs_e_mma_kernel(const RhsParams<float> prm) {
+  using S = MmaTile<P>;
+  constexpr int TX = S::TX, TY = S::TY, TZ = S::TZ, HX = S::HX, HY = S::HY, HZ = S::HZ;
+  constexpr int W = 2 * P + 1;
+  constexpr int NT = TX * TY;
+  extern __shared__ __align__(16) unsigned char mma_smem[];
+  __nv_bfloat16* s_tile = reinterpret_cast<__nv_bfloat16*>(mma_smem);
+  float* s_x = reinterpret_cast<float*>(mma_smem + S::TILE_B);
+  float* s_y = reinterpret_cast<float*>(mma_smem + S::TILE_B + S::X_B);
+  unsigned* s_bf = reinterpret_cast<unsigned*>(mma_smem + S::TILE_B + S::X_B + S::Y_B);
+  __shared__ float s_by[TY][W], s_bz[TZ][W];
+
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
+  const int Nx = prm.Nx, Ny = prm.Ny, Nz = prm.Nz, pitch = prm.pitch;
+  const long long sxy = (long long)pitch * Ny;
+  const int gx = x0 + tx, gy = y0 + ty;
+  const bool col_in = gx < Nx && gy < Ny;
+
+  float cf[4][TZ];  // 1, a, b, c
+#pragma unroll
+  for (int zz = 0; zz < TZ; ++zz) {
+    const int gz = z0 + zz;
+    const bool in = col_in && gz < Nz;
+    const long long g = gz * sxy + (long long)gy * pitch + gx;
+    cf[0][zz] = 1.f;
+#pragma unroll
+    for (int k = 1; k < 4; ++k) cf[k][zz] = in && prm.coef[k] ? prm.coef[k][g] : 0.f;
+  }
+  float acc[3][TZ];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int zz = 0; zz < TZ; ++zz) acc[c][zz] = 0.f;
+
+  // zero the padding of the BF16 tile once: columns HX .. TS-1 and rows ROWS .. 16 MT - 1
+  for (int i = tid; i < S::MT * 16 * S::TS; i += NT) {
+    const int r = i / S::TS, k = i % S::TS;
+    if (k >= HX || r >= S::ROWS) s_tile[i] = __float2bfloat16(0.f);
+  }
+  // B fragments of this tile's x operators (the same for every term that uses
+  // the operator): B[k][n] = Wx[x0+n][k - n] (band index), BF16; lane l holds
+  // k = 2(l % 4) + {0, 1} (+ 8 for the second register), n = l / 4 (+ 8 nt)
+  for (int i = tid; i < 3 * 4 * S::KS * 2 * 32; i += NT) {
+    const int ln = i % 32, h = (i / 32) % 2, ks = (i / 64) % S::KS, nt = (i / (64 * S::KS)) % 4;
+    const int oi = i / (64 * S::KS * 4);
+    const float* bx = prm.ax[0].band[oi == 0 ? OP_M : (oi == 1 ? OP_A : OP_B)];
+    const int n = nt * 8 + (ln >> 2);
+    float v[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int q = ks * 16 + h * 8 + 2 * (ln & 3) + e - n;
+      v[e] = (x0 + n < Nx && q >= 0 && q < W) ? bx[(x0 + n) * W + q] : 0.f;
+    }
+    s_bf[i] = pack_bf16x2(v[0], v[1]);
+  }
+
+  int cur_field = -1;
+  for (int t = 0; t < prm.nterms; ++t) {
+    const Term tm = prm.terms[t];
+    __syncthreads();  // previous term done with s_tile / s_x / s_y / band rows
+    if (tm.field != cur_field) {  // the haloed field tile, rounded to BF16
+      const float* __restrict__ f = prm.fields[tm.field];
+      for (int i = tid; i < S::ROWS * HX; i += NT) {
+        const int xx = i % HX, r = i / HX, yy = r % HY, zz = r / HY;
+        const int X = x0 - P + xx, Y = y0 - P + yy, Z = z0 - P + zz;
+        float v = 0.f;
+        if (X >= 0 && X < Nx && Y >= 0 && Y < Ny && Z >= 0 && Z < Nz) v = f[Z * sxy + (long long)Y * pitch + X];
+        s_tile[r * S::TS + xx] = __float2bfloat16(v);
+      }
+      cur_field = tm.field;
+    }
+    {
+      const float* by = prm.ax[1].band[tm.op[1]];
+      const float* bz = prm.ax[2].band[tm.op[2]];
+      for (int i = tid; i < (TY + TZ) * W; i += NT) {
+        const int row = i / W, q = i % W;
+        if (row < TY) {
+          const int g = y0 + row;
+          s_by[row][q] = g < Ny ? by[g * W + q] : 0.f;
+        } else {
+          const int g = z0 + row - TY;
+          s_bz[row - TY][q] = g < Nz ? bz[g * W + q] : 0.f;
+        }
+      }
+    }
+    const unsigned* bf = s_bf + (tm.op[0] == OP_M ? 0 : (tm.op[0] == OP_A ? 1 : 2)) * (4 * S::KS * 2 * 32) + lane;
+    __syncthreads();
+    // x pass on the tensor cores: warp w takes m tiles w, w + 8, ...
+    for (int mt = warp; mt < S::MT; mt += NT / 32) {
+      unsigned afr[S::KS][4];
+      {
+        const int mi = lane >> 3, r8 = lane & 7;
+        const int row = mt * 16 + r8 + (mi & 1) * 8;
+#pragma unroll
+        for (int ks = 0; ks < S::KS; ++ks) {
+          const unsigned addr = (unsigned)__cvta_generic_to_shared(s_tile + row * S::TS + ks * 16 + (mi >> 1) * 8);
+          asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+                       : "=r"(afr[ks][0]), "=r"(afr[ks][1]), "=r"(afr[ks][2]), "=r"(afr[ks][3])
+                       : "r"(addr));
+        }
+      }
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int ks = 0; ks < S::KS; ++ks)
+          asm volatile(
+              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+              "{%0, %1, %2, %3};\n"
+              : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+              : "r"(afr[ks][0]), "r"(afr[ks][1]), "r"(afr[ks][2]), "r"(afr[ks][3]),
+                "r"(bf[((nt * S::KS + ks) * 2 + 0) * 32]), "r"(bf[((nt * S::KS + ks) * 2 + 1) * 32]));
+        const int g4 = lane >> 2, t4 = lane & 3;
+        const int r0 = mt * 16 + g4, c0 = nt * 8 + 2 * t4;
+        if (r0 < S::ROWS) {
+          s_x[r0 * S::XS + c0] = d[0];
+          s_x[r0 * S::XS + c0 + 1] = d[1];
+        }
+        if (r0 + 8 < S::ROWS) {
+          s_x[(r0 + 8) * S::XS + c0] = d[2];
+          s_x[(r0 + 8) * S::XS + c0 + 1] = d[3];
+        }
+      }
+    }
+    __syncthreads();
+    // y pass (FP32): s_y[zh][yo][xo] = sum_q Wy[yo][q] X[(zh, yo + q)][xo]
+    for (int i = tid; i < HZ * TY * TX; i += NT) {
+      const int xo = i % TX, r = i / TX, yo = r % TY, zh = r / TY;
+      float v = 0.f;
+#pragma unroll
+      for (int q = 0; q < W; ++q) v += s_by[yo][q] * s_x[(zh * HY + yo + q) * S::XS + xo];
+      s_y[i] = v;
+    }
+    __syncthreads();
+    // z pass (FP32) and accumulation into this thread's outputs
+    const float sg = tm.sign;
+    const int ck = tm.coef == CF_A ? 1 : tm.coef == CF_B ? 2 : tm.coef == CF_C ? 3 : 0;
+#pragma unroll
+    for (int zz = 0; zz < TZ; ++zz) {
+      float v = 0.f;
+#pragma unroll
+      for (int q = 0; q < W; ++q) v += s_bz[zz][q] * s_y[((zz + q) * TY + ty) * TX + tx];
+      const float w = sg * cf[ck][zz] * v;
+      if (tm.out == 0) acc[0][zz] += w;
+      else if (tm.out == 1) acc[1][zz] += w;
+      else acc[2][zz] += w;
+    }
+  }
+
+  // point source: -b amp g(t_mid) B_r(x0) B_s(y0) B_t(z0) on its component
+  double g = 0.0;
+  if (prm.src_comp >= 0 && src_in_tile(prm.src_i0, P, x0, y0, z0, TX, TY, TZ)) {
+    const double tmid = *prm.clock_t0 + ((double)*prm.clock_step + prm.t_frac) * prm.tau;
+    const double u = tmid - prm.src_t0;
+    g = prm.src_amp * sin(2.0 * 3.14159265358979323846 * prm.src_f0 * u) * exp(-(u / prm.src_s) * (u / prm.src_s));
+  }
+  if (!col_in) return;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+#pragma unroll
+    for (int zz = 0; zz < TZ; ++zz) {
+      const int gz = z0 + zz;
+      if (gz >= Nz) continue;
+      float v = acc[c][zz];
+      if (c == prm.src_comp) {
+        const int ix = gx - prm.src_i0[0], iy = gy - prm.src_i0[1], iz = gz - prm.src_i0[2];
+        if (ix >= 0 && ix <= P && iy >= 0 && iy <= P && iz >= 0 && iz <= P)
+          v -= cf[2][zz] * (float)g * prm.src_w[0][ix] * prm.src_w[1][iy] * prm.src_w[2][iz];
+      }
+      prm.out[c][gz * sxy + (long long)gy * pitch + gx] = v;
+    }
+  }
+}
+
 // ------------------------------------------------ mixed-mode FP64 residual
 // r = RHS - T E* of the E system, in FP64 arithmetic from FP32 arrays:
 // fields 0..5 are the inputs of the E right-hand side (E, H of the old level),
@@ -324,6 +538,194 @@ __global__ void __launch_bounds__(256) resid_kernel(const ResidParams prm) {
           v -= cf[2][zz] * g * prm.src_w[0][ix] * prm.src_w[1][iy] * prm.src_w[2][iz];
       }
       prm.out[c][gz * sxy + (long long)gy * pitch + gx] = (float)v;
+    }
+  }
+}
+
+// ------------------------------------- mixed-mode float-float residual
+// The same residual r = RHS - T E* as resid_kernel, evaluated in compensated
+// double-float arithmetic on the FP32 pipe instead of the FP64 pipe (GB300 runs
+// FP64 at 1/64 of the FP32 rate).  A value is an unevaluated sum hi + lo of two
+// floats (about 48 significant bits).  The error-free transformations are the
+// published ones: TwoSum (Knuth, TAOCP vol. 2: s = a + b and its exact
+// rounding error, six additions) and TwoProduct by fused multiply-add (the
+// product's rounding error is fma(a, b, -a*b); Dekker's product, 1971, without
+// splitting); sums of double-float values renormalise with Fast-TwoSum.  The
+// roundings are explicit (__fadd_rn / __fmul_rn), so the compiler cannot fuse
+// them into FMAs that would break the transformations.  The fields and the
+// row coefficients are FP32 (exact as double-float), the band tables are the
+// FP64 tables split into hi + lo on the host.
+struct ff {
+  float hi, lo;
+};
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ ff ff_fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+// sum of two double-float values: TwoSum of the high parts, the low parts added
+// to its error, renormalised (error about 2^-44 of |a| + |b|)
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  const ff s = ff_two_sum(a.hi, b.hi);
+  return ff_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+// a * b for a double-float a and a float b
+__device__ __forceinline__ ff ff_mul_f(ff a, float b) {
+  const float p = __fmul_rn(a.hi, b);
+  const float e = __fmaf_rn(a.lo, b, __fmaf_rn(a.hi, b, -p));
+  return ff_fast_two_sum(p, e);
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+  return ff_fast_two_sum(p, e);
+}
+
+struct ResidFFParams {
+  const float* fields[9];
+  const float* coef[5];  // [CF_A], [CF_B], [CF_C]
+  float* out[3];
+  const float2* band[3][4];  // [axis][op]: (hi, lo) of the FP64 band tables
+  Term terms[kMaxResidTerms];
+  int nterms;
+  int Nx, Ny, Nz, pitch;
+  int src_comp;
+  int src_i0[3];
+  double src_w[3][kMaxP + 1];
+  double src_amp, src_f0, src_t0, src_s;
+  double tau, t_frac;
+  const double* clock_t0;
+  const long long* clock_step;
+};
+
+template <int P>
+__global__ void __launch_bounds__(256) resid_ff_kernel(const ResidFFParams prm) {
+  constexpr int TX = 32, TY = 8, TZ = 8;
+  constexpr int W = 2 * P + 1;
+  constexpr int HX = TX + 2 * P, HY = TY + 2 * P, HZ = TZ + 2 * P;
+  constexpr int NT = TX * TY;
+  extern __shared__ __align__(16) unsigned char resid_ff_smem[];
+  float* s_in = reinterpret_cast<float*>(resid_ff_smem);              // FP32 inputs (exact)
+  ff* s_z = reinterpret_cast<ff*>(s_in + ((HZ * HY * HX + 1) & ~1));  // z pass, double-float
+  ff* s_y = s_z + TZ * HY * HX;                                       // y pass
+  __shared__ ff s_bx[TX][W], s_by[TY][W], s_bz[TZ][W];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
+  const int Nx = prm.Nx, Ny = prm.Ny, Nz = prm.Nz, pitch = prm.pitch;
+  const long long sxy = (long long)pitch * Ny;
+  const int gx = x0 + tx, gy = y0 + ty;
+  const bool col_in = gx < Nx && gy < Ny;
+  float cf[4][TZ];  // 1, a, b, c (FP32 arrays: exact)
+#pragma unroll
+  for (int zz = 0; zz < TZ; ++zz) {
+    const int gz = z0 + zz;
+    const bool in = col_in && gz < Nz;
+    const long long g = gz * sxy + (long long)gy * pitch + gx;
+    cf[0][zz] = 1.f;
+#pragma unroll
+    for (int k = 1; k < 4; ++k) cf[k][zz] = in ? prm.coef[k][g] : 0.f;
+  }
+  ff acc[3][TZ];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int zz = 0; zz < TZ; ++zz) acc[c][zz] = ff{0.f, 0.f};
+  int cur_field = -1;
+  for (int t = 0; t < prm.nterms; ++t) {
+    const Term tm = prm.terms[t];
+    __syncthreads();
+    if (tm.field != cur_field) {
+      const float* __restrict__ f = prm.fields[tm.field];
+      for (int i = tid; i < HZ * HY * HX; i += NT) {
+        const int xx = i % HX, r = i / HX, yy = r % HY, zz = r / HY;
+        const int X = x0 - P + xx, Y = y0 - P + yy, Z = z0 - P + zz;
+        float v = 0.f;
+        if (X >= 0 && X < Nx && Y >= 0 && Y < Ny && Z >= 0 && Z < Nz) v = f[Z * sxy + (long long)Y * pitch + X];
+        s_in[i] = v;
+      }
+      cur_field = tm.field;
+    }
+    {
+      const float2* bx = prm.band[0][tm.op[0]];
+      const float2* by = prm.band[1][tm.op[1]];
+      const float2* bz = prm.band[2][tm.op[2]];
+      for (int i = tid; i < (TX + TY + TZ) * W; i += NT) {
+        const int row = i / W, q = i % W;
+        float2 v = make_float2(0.f, 0.f);
+        if (row < TX) {
+          const int g = x0 + row;
+          if (g < Nx) v = bx[g * W + q];
+          s_bx[row][q] = ff{v.x, v.y};
+        } else if (row < TX + TY) {
+          const int g = y0 + row - TX;
+          if (g < Ny) v = by[g * W + q];
+          s_by[row - TX][q] = ff{v.x, v.y};
+        } else {
+          const int g = z0 + row - TX - TY;
+          if (g < Nz) v = bz[g * W + q];
+          s_bz[row - TX - TY][q] = ff{v.x, v.y};
+        }
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < TZ * HY * HX; i += NT) {
+      const int rem = i % (HY * HX), zz = i / (HY * HX);
+      ff v{0.f, 0.f};
+#pragma unroll
+      for (int q = 0; q < W; ++q) v = ff_add(v, ff_mul_f(s_bz[zz][q], s_in[(zz + q) * HY * HX + rem]));
+      s_z[i] = v;
+    }
+    __syncthreads();
+    for (int i = tid; i < TZ * TY * HX; i += NT) {
+      const int xx = i % HX, r = i / HX, yy = r % TY, zz = r / TY;
+      ff v{0.f, 0.f};
+#pragma unroll
+      for (int q = 0; q < W; ++q) v = ff_add(v, ff_mul(s_by[yy][q], s_z[(zz * HY + yy + q) * HX + xx]));
+      s_y[i] = v;
+    }
+    __syncthreads();
+    const int ck = tm.coef == CF_A ? 1 : tm.coef == CF_B ? 2 : tm.coef == CF_C ? 3 : 0;
+#pragma unroll
+    for (int zz = 0; zz < TZ; ++zz) {
+      ff v{0.f, 0.f};
+#pragma unroll
+      for (int q = 0; q < W; ++q) v = ff_add(v, ff_mul(s_bx[tx][q], s_y[(zz * TY + ty) * HX + tx + q]));
+      ff w = ff_mul_f(v, tm.sign * cf[ck][zz]);  // sign is +-1: exact
+      if (tm.out == 0) acc[0][zz] = ff_add(acc[0][zz], w);
+      else if (tm.out == 1) acc[1][zz] = ff_add(acc[1][zz], w);
+      else acc[2][zz] = ff_add(acc[2][zz], w);
+    }
+  }
+  double g = 0.0;
+  if (prm.src_comp >= 0 && src_in_tile(prm.src_i0, P, x0, y0, z0, TX, TY, TZ)) {
+    const double tmid = *prm.clock_t0 + ((double)*prm.clock_step + prm.t_frac) * prm.tau;
+    const double u = tmid - prm.src_t0;
+    g = prm.src_amp * sin(2.0 * 3.14159265358979323846 * prm.src_f0 * u) * exp(-(u / prm.src_s) * (u / prm.src_s));
+  }
+  if (!col_in) return;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+#pragma unroll
+    for (int zz = 0; zz < TZ; ++zz) {
+      const int gz = z0 + zz;
+      if (gz >= Nz) continue;
+      ff v = acc[c][zz];
+      if (c == prm.src_comp) {
+        const int ix = gx - prm.src_i0[0], iy = gy - prm.src_i0[1], iz = gz - prm.src_i0[2];
+        if (ix >= 0 && ix <= P && iy >= 0 && iy <= P && iz >= 0 && iz <= P) {
+          // the source row (one point per tile) in FP64, split into hi + lo
+          const double sv = (double)cf[2][zz] * g * prm.src_w[0][ix] * prm.src_w[1][iy] * prm.src_w[2][iz];
+          const float sh = (float)sv;
+          v = ff_add(v, ff{-sh, -(float)(sv - (double)sh)});
+        }
+      }
+      prm.out[c][gz * sxy + (long long)gy * pitch + gx] = __fadd_rn(v.hi, v.lo);
     }
   }
 }
@@ -1754,8 +2156,8 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 // them across fields: [z(F) and x(F-1)] | [y(F)], so each field costs two
 // block barriers (plus its tile wait) instead of three.
 // Stage z: wait for the field's tile (every thread; the give-up decision is
-// block-wide), optional BF16 rounding, z pass into s_zr.
-template <typename T, int P, int H, int F, bool BFT>
+// block-wide), z pass into s_zr.
+template <typename T, int P, int H, int F>
 __device__ __forceinline__ bool zstage(const RhsParams<T>& prm, T* s_tile, T* s_zr, unsigned long long* bars, int z0,
                                        bool inZ) {
   using S = Smem<T, P>;
@@ -1765,12 +2167,6 @@ __device__ __forceinline__ bool zstage(const RhsParams<T>& prm, T* s_tile, T* s_
   constexpr unsigned PAR = S::NBUF == 2 ? (F / 2) & 1 : F & 1;  // its barrier phase
   if (!__syncthreads_and(mbar_wait(&bars[B], PAR))) return false;
   const T* tl = s_tile + B * S::TILE;
-  if (BFT) {  // mixed precision: the field tile rounded to BF16 (FP32 accumulation below)
-    T* tw = s_tile + B * S::TILE;
-    for (int i = tid; i < S::TILE; i += NT) tw[i] = T(__bfloat162float(__float2bfloat16_rn(float(tw[i]))));
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // before TMA reuses the buffer
-    __syncthreads();
-  }
   constexpr bool zshare = PL::z0 == PL::z1;
   if constexpr (P == 2) {  // pairs of columns
     for (int i2 = tid; i2 < S::HY * S::HX / 2; i2 += NT) {
@@ -1846,7 +2242,7 @@ __device__ __forceinline__ void xstage(const RhsParams<T>& prm, const T* s_yr, i
 // tile buffer refilled here held field F-1, whose z pass ended before the
 // previous barrier (one buffer: the tile is reloaded after z(F)); x(F-1) reads
 // s_yr, which y(F) overwrites only after the barrier that follows it.
-template <typename T, int P, int H, int F, bool BFT>
+template <typename T, int P, int H, int F>
 __device__ __forceinline__ bool pipe_field(const RhsParams<T>& prm, const TmaMaps& maps, T* s_tile, T* s_zr,
                                            T* s_yr, unsigned long long* bars, int x0, int y0, int z0, bool inZ,
                                            bool inY, bool inX, int xp, int rg, T (&cf)[3][RPT][2],
@@ -1855,7 +2251,7 @@ __device__ __forceinline__ bool pipe_field(const RhsParams<T>& prm, const TmaMap
   const int tid = threadIdx.x;
   if (S::NBUF == 2 && F + 1 < 6 && tid == 0)
     tma_tile<T, P>(&maps.m[F + 1], s_tile + ((F + 1) & 1) * S::TILE, &bars[(F + 1) & 1], x0 - 4, y0 - P, z0 - P);
-  if (!zstage<T, P, H, F, BFT>(prm, s_tile, s_zr, bars, z0, inZ)) return false;
+  if (!zstage<T, P, H, F>(prm, s_tile, s_zr, bars, z0, inZ)) return false;
   if (F > 0) xstage<T, P, H, (F > 0 ? F - 1 : 0)>(prm, s_yr, x0, inX, xp, rg, cf, acc);
   __syncthreads();
   if (S::NBUF == 1 && F + 1 < 6 && tid == 0)  // single buffer (FP64): load the next tile during the y pass
@@ -1866,7 +2262,7 @@ __device__ __forceinline__ bool pipe_field(const RhsParams<T>& prm, const TmaMap
 }
 }  // namespace rhs2
 
-template <typename T, int P, int H, bool BFT>
+template <typename T, int P, int H>
 __global__ void __launch_bounds__(rhs2::NT, sizeof(T) == 4 ? ADI_RHS_MINB : 1)
     rhs_e_kernel(const RhsParams<T> prm, const __grid_constant__ TmaMaps maps) {
   using namespace rhs2;
@@ -1912,12 +2308,12 @@ __global__ void __launch_bounds__(rhs2::NT, sizeof(T) == 4 ? ADI_RHS_MINB : 1)
   }
   __syncthreads();
   if (tid == 0) tma_tile<T, P>(&maps.m[0], s_tile, &bars[0], x0 - 4, y0 - P, z0 - P);
-  bool ok = pipe_field<T, P, H, 0, BFT>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
-  if (ok) ok = pipe_field<T, P, H, 1, BFT>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
-  if (ok) ok = pipe_field<T, P, H, 2, BFT>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
-  if (ok) ok = pipe_field<T, P, H, 3, BFT>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
-  if (ok) ok = pipe_field<T, P, H, 4, BFT>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
-  if (ok) ok = pipe_field<T, P, H, 5, BFT>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+  bool ok = pipe_field<T, P, H, 0>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+  if (ok) ok = pipe_field<T, P, H, 1>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+  if (ok) ok = pipe_field<T, P, H, 2>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+  if (ok) ok = pipe_field<T, P, H, 3>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+  if (ok) ok = pipe_field<T, P, H, 4>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+  if (ok) ok = pipe_field<T, P, H, 5>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
   if (ok) xstage<T, P, H, 5>(prm, s_yr, x0, inX, xp, rg, cf, acc);
   if (!ok) {
     // a tile never arrived: report, give the copies in flight a bounded time, leave
@@ -2295,6 +2691,14 @@ size_t rhs_smem() {
                       (size_t)TZ * TY * (TX + 2 * P));
 }
 
+template <int P>
+size_t resid_ff_smem() {
+  constexpr int TX = 32, TY = 8, TZ = 8;
+  const size_t nin = (size_t)(TZ + 2 * P) * (TY + 2 * P) * (TX + 2 * P);
+  return sizeof(float) * ((nin + 1) & ~(size_t)1) +
+         sizeof(float) * 2 * ((size_t)TZ * (TY + 2 * P) * (TX + 2 * P) + (size_t)TZ * TY * (TX + 2 * P));
+}
+
 template <typename T, int P>
 cudaError_t launch_rhs(Ctx& c, RhsParams<T>& prm, const char* name, double bytes) {
   constexpr int TX = 32, TY = 8, TZ = 8;
@@ -2362,18 +2766,18 @@ cudaError_t launch_rhs_e(Ctx& c, RhsParams<T>& prm, int half, double bytes, bool
     maps.m[3 + i] = c.tmap_cur[3 + i];                         // H (one buffer)
   }
   dim3 grid((c.N[0] + TX - 1) / TX, (c.N[1] + TY - 1) / TY, (c.N[2] + TZ - 1) / TZ);
-  prof_begin(c, "rhs_E", bytes);
   bool done = false;
-  if constexpr (sizeof(T) == 4) {  // BF16 field tiles: mixed mode, FP32 only
+  if constexpr (sizeof(T) == 4) {  // mixed mode: BF16 operands on the tensor cores (the generic term list)
     if (bf16_tiles) {
-      if (half == 1) rhs_e_kernel<T, P, 1, true><<<grid, NT, rhs_e_smem<T, P>(), c.stream>>>(prm, maps);
-      else rhs_e_kernel<T, P, 2, true><<<grid, NT, rhs_e_smem<T, P>(), c.stream>>>(prm, maps);
+      prof_begin(c, "rhs_E_mma", bytes);
+      rhs_e_mma_kernel<P><<<grid, dim3(32, 8), MmaTile<P>::BYTES, c.stream>>>(prm);
       done = true;
     }
   }
+  if (!done) prof_begin(c, "rhs_E", bytes);
   if (!done) {
-    if (half == 1) rhs_e_kernel<T, P, 1, false><<<grid, NT, rhs_e_smem<T, P>(), c.stream>>>(prm, maps);
-    else rhs_e_kernel<T, P, 2, false><<<grid, NT, rhs_e_smem<T, P>(), c.stream>>>(prm, maps);
+    if (half == 1) rhs_e_kernel<T, P, 1><<<grid, NT, rhs_e_smem<T, P>(), c.stream>>>(prm, maps);
+    else rhs_e_kernel<T, P, 2><<<grid, NT, rhs_e_smem<T, P>(), c.stream>>>(prm, maps);
   }
   prof_end(c);
   return cudaGetLastError();
@@ -2590,6 +2994,68 @@ cudaError_t launch_resid(Ctx& c, int half, float* const* Ein, float* const* Hin,
   return cudaGetLastError();
 }
 
+// float-float band table of (axis d, op o) inside c.tabff
+inline const float2* bandff(const Ctx& c, int d, int o) {
+  size_t off = 0;
+  const int W = 2 * c.p + 1;
+  for (int k = 0; k < d; ++k) off += 4 * (size_t)c.N[k] * W;
+  return c.tabff + off + (size_t)o * c.N[d] * W;
+}
+
+template <int P>
+cudaError_t launch_resid_ff(Ctx& c, int half, float* const* Ein, float* const* Hin, float* const* Estar,
+                            float* const* R) {
+  float** cf = reinterpret_cast<float**>(c.coef);
+  ResidFFParams prm{};
+  for (int i = 0; i < 3; ++i) {
+    prm.fields[i] = Ein[i];
+    prm.fields[3 + i] = Hin[3 + i];
+    prm.fields[6 + i] = Estar[i];
+    prm.out[i] = R[i];
+  }
+  prm.coef[CF_A] = cf[0];
+  prm.coef[CF_B] = cf[1];
+  prm.coef[CF_C] = cf[2];
+  for (int d = 0; d < 3; ++d)
+    for (int o = 0; o < 4; ++o) prm.band[d][o] = bandff(c, d, o);
+  int n = e_terms(half, prm.terms);
+  for (int k = 0; k < 3; ++k) {
+    Term t{};
+    t.field = 6 + k;
+    t.out = k;
+    t.op[0] = t.op[1] = t.op[2] = OP_M;
+    t.coef = CF_ONE;
+    t.sign = -1.f;
+    prm.terms[n++] = t;
+    t.op[kStiffDir[half - 1][k]] = OP_S;
+    t.coef = CF_C;
+    prm.terms[n++] = t;
+  }
+  prm.nterms = n;
+  prm.Nx = c.N[0];
+  prm.Ny = c.N[1];
+  prm.Nz = c.N[2];
+  prm.pitch = c.pitch;
+  prm.src_comp = (c.src_comp >= 0 && c.src_amp != 0.0) ? c.src_comp : -1;
+  for (int d = 0; d < 3; ++d) {
+    prm.src_i0[d] = c.src_i0[d];
+    for (int q = 0; q <= kMaxP; ++q) prm.src_w[d][q] = c.src_w[d][q];
+  }
+  prm.src_amp = c.src_amp;
+  prm.src_f0 = c.src_f0;
+  prm.src_t0 = c.src_t0;
+  prm.src_s = c.src_s;
+  prm.tau = c.dt;
+  prm.t_frac = half == 1 ? 0.25 : 0.75;
+  prm.clock_t0 = c.d_clock_t0;
+  prm.clock_step = c.d_clock_step;
+  dim3 grid((c.N[0] + 31) / 32, (c.N[1] + 7) / 8, (c.N[2] + 7) / 8);
+  prof_begin(c, "resid_Eff", (double)c.Nc * 4.0 * 15.0);  // reads 9 fields + a, b, c, writes 3
+  resid_ff_kernel<P><<<grid, dim3(32, 8), resid_ff_smem<P>(), c.stream>>>(prm);
+  prof_end(c);
+  return cudaGetLastError();
+}
+
 // E half step: the right-hand side, then the line solves (e_solve).
 template <typename T, int P>
 cudaError_t e_substep(Ctx& c, int half) {
@@ -2639,7 +3105,8 @@ cudaError_t e_substep(Ctx& c, int half) {
   if (e != cudaSuccess || !mixed || !c.mixed_refine) return e;
   if constexpr (sizeof(T) == 4) {
     // one refinement: R = RHS - T E* in FP64, T delta = R in place, E = E* + delta
-    e = launch_resid<P>(c, half, Ein, Hin, Eout, R);
+    e = c.mixed_fp64_residual ? launch_resid<P>(c, half, Ein, Hin, Eout, R)
+                              : launch_resid_ff<P>(c, half, Ein, Hin, Eout, R);
     if (e == cudaSuccess) e = e_solve<T, P>(c, half, R, R);
     if (e == cudaSuccess) {
       const long long rows = (long long)c.N[1] * c.N[2];
@@ -2804,14 +3271,14 @@ template <typename T, int P>
 cudaError_t prepare_tp(int optin) {
   cudaError_t e = opt_in(rhs_kernel<T, P, 32, 8, 8>, optin);
   if (e == cudaSuccess) e = opt_in(line_xws_kernel<T, P>, optin);
-  if (e == cudaSuccess) e = opt_in(rhs_e_kernel<T, P, 1, false>, optin);
-  if (e == cudaSuccess) e = opt_in(rhs_e_kernel<T, P, 2, false>, optin);
+  if (e == cudaSuccess) e = opt_in(rhs_e_kernel<T, P, 1>, optin);
+  if (e == cudaSuccess) e = opt_in(rhs_e_kernel<T, P, 2>, optin);
   if constexpr (sizeof(T) == 4) {
     if (e == cudaSuccess) e = opt_in(line_xw_kernel<P, LM_MASS>, optin);
     if (e == cudaSuccess) e = opt_in(line_xw_kernel<P, LM_DERIV>, optin);
-    if (e == cudaSuccess) e = opt_in(rhs_e_kernel<T, P, 1, true>, optin);
-    if (e == cudaSuccess) e = opt_in(rhs_e_kernel<T, P, 2, true>, optin);
+    if (e == cudaSuccess) e = opt_in(rhs_e_mma_kernel<P>, optin);
     if (e == cudaSuccess) e = opt_in(resid_kernel<P>, optin);
+    if (e == cudaSuccess) e = opt_in(resid_ff_kernel<P>, optin);
   }
   if (e == cudaSuccess) e = opt_in(line_kernel<T, P, LM_MASS, true>, optin);
   if (e == cudaSuccess) e = opt_in(line_kernel<T, P, LM_STIFF, true>, optin);
@@ -3054,6 +3521,15 @@ cudaError_t upload_tables(Ctx& c) {
       c.tab64_bytes = h.size() * sizeof(double);
     }
     e = cudaMemcpyAsync(c.tab64, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream);
+    // the same tables as float pairs hi + lo (hi = the nearest float, lo = the nearest float of the rest)
+    std::vector<float2> hf(h.size());
+    for (size_t i = 0; i < h.size(); ++i) {
+      const float hi = (float)h[i];
+      hf[i] = make_float2(hi, (float)(h[i] - (double)hi));
+    }
+    if (e == cudaSuccess && !c.tabff) e = cudaMalloc((void**)&c.tabff, hf.size() * sizeof(float2));
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c.tabff, hf.data(), hf.size() * sizeof(float2), cudaMemcpyHostToDevice, c.stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
     if (e != cudaSuccess) return e;
   }

@@ -2,8 +2,8 @@
 
 The E right-hand side is contracted from field tiles rounded to BF16 (FP32
 accumulation), which alone leaves a relative error of order 2^-9 ~ 2e-3 in E*.
-One refinement (residual in FP64, correction solved in FP32) brings the step
-back to FP32 accuracy: relative l2 per step from an identical state within the
+One refinement (residual in compensated float-float arithmetic, or in FP64;
+correction solved in FP32) brings the step back to FP32 accuracy: relative l2 per step from an identical state within the
 FP32 bound of tests/test_gpu_parity.py.  Without the refinement the error must
 be at least ten times larger and still below 1e-2 (the BF16 rounding bound
 with the 3D mass-matrix conditioning).
@@ -26,7 +26,7 @@ def _adi():
     return adi
 
 
-def _step(n, p, tau, mat, refine, src, t0=1.37, steps=1, use_graph=True):
+def _step(n, p, tau, mat, refine, src, t0=1.37, steps=1, use_graph=True, residual="ff", want_state=False):
     adi = _adi()
     if mat == "uniform":
         eps = mu = sigma = None
@@ -36,7 +36,8 @@ def _step(n, p, tau, mat, refine, src, t0=1.37, steps=1, use_graph=True):
         eps, mu, sigma = inputs.random_material(n, 7, mu_range=(1.0, 2.0))
     prob = ma.make_problem(n, p, tau, eps, mu, sigma)
     ma.set_source(prob, src["x0"], src["comp"], src["amp"], src["f0"], src["t0"], src["s"])
-    s = adi.Solver(n, p, tau, eps, mu, sigma, precision="mixed", refine=refine, use_graph=use_graph)
+    s = adi.Solver(n, p, tau, eps, mu, sigma, precision="mixed", refine=refine, use_graph=use_graph,
+                   residual=residual)
     s.factor()
     s.set_source(src["x0"], src["comp"], src["amp"], src["f0"], src["t0"], src["s"])
     st = ma.apply_dirichlet(list(inputs.random_fields(prob.shape, 3)))
@@ -46,6 +47,8 @@ def _step(n, p, tau, mat, refine, src, t0=1.37, steps=1, use_graph=True):
     got, _ = s.fields()
     s.close()
     rel, elem = errors(got, ref)
+    if want_state:
+        return rel, max(elem), got
     return rel, max(elem)   # global relative l2, worst point of any component
 
 
@@ -89,3 +92,17 @@ def test_mixed_graph_equals_substeps():
         out.append(s.fields()[0])
         s.close()
     assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("n,p,mat", SMALL)
+def test_float_float_residual_matches_fp64_residual(n, p, mat):
+    # the refinement's residual in compensated float-float arithmetic (the
+    # default) against the same residual in FP64: both refined steps meet the
+    # FP32 bound against the oracle, and they agree with each other to FP32
+    # rounding of the state (E* is the same; only the correction can differ)
+    src = inputs.dipole(2103)
+    e_ff, m_ff, g_ff = _step(n, p, 0.03, mat, True, src, residual="ff", want_state=True)
+    e_64, m_64, g_64 = _step(n, p, 0.03, mat, True, src, residual="fp64", want_state=True)
+    assert max(e_ff, m_ff) < tol("fp32", p, mat) and max(e_64, m_64) < tol("fp32", p, mat)
+    rel, elem = errors(g_ff, g_64)
+    assert rel < 1e-6 and max(elem) < 2e-6, (rel, elem)
