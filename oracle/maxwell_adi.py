@@ -21,6 +21,14 @@ coefficients a, b, c, d (``oracle.material``).  Readings of the paper taken here
   B-spline coefficients in the two directions other than i, H_i in direction i.
 * The current source -J enters the E rows as -b (J, B_rst) at the midpoint
   time of each half step, t_n + tau/4 and t_n + 3 tau/4.
+* Material in the right-hand side, two readings.  "row" (the paper's, default):
+  every row rst is scaled by its coefficients a, b, c, d formed from the row's
+  hat values.  "quad": the right-hand side integrals carry the per-element
+  coefficients inside the integrand, sum_e kappa_e int_e (...) B_rst with
+  kappa_e in {a_e, b_e, c_e, d_e} formed from the element's eps, mu, sigma by the
+  same formulas (the source row then uses b of the element holding the dipole);
+  the left-hand sides stay row-scaled, which keeps their Kronecker structure.
+  Both agree for uniform material.
 
 Components are ordered (E1, E2, E3, H1, H2, H3), each an array (Nz, Ny, Nx).
 
@@ -35,7 +43,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import bspline
-from .banded import kron3, solve_lines
+from .banded import apply_1d, kron3, solve_lines
 from . import material
 
 # direction of the stiffness (material) solve of E_i in half step 1 and 2
@@ -56,6 +64,8 @@ class Problem:
     d: np.ndarray
     mats: dict = field(default_factory=dict)   # axis -> (M, S, A, B)
     source: dict = None     # point source (see set_source)
+    rhs_material: str = "row"   # "row" or "quad" (see the module docstring)
+    elem: dict = None       # "quad": per-element coefficients a, b, c, d, shape (nz, ny, nx)
 
     @property
     def shape(self):
@@ -64,10 +74,12 @@ class Problem:
         return (nz + p, ny + p, nx + p)
 
 
-def make_problem(n, p, tau, eps=None, mu=None, sigma=None):
+def make_problem(n, p, tau, eps=None, mu=None, sigma=None, rhs_material="row"):
     """Build the 1D matrices and the per-row coefficients.
 
     eps, mu, sigma: per-element arrays (nz, ny, nx) or None for 1, 1, 0.
+    rhs_material: "row" (the paper's row scaling) or "quad" (per-element
+    coefficients inside the right-hand side integrals).
     """
     nx, ny, nz = n
     shp_e = (nz, ny, nx)
@@ -80,7 +92,13 @@ def make_problem(n, p, tau, eps=None, mu=None, sigma=None):
     a, b, c, d = material.coefficients(eh, mh, sh, tau)
     mats = {"x": bspline.matrices_1d(nx, p), "y": bspline.matrices_1d(ny, p),
             "z": bspline.matrices_1d(nz, p)}
-    return Problem(n=tuple(n), p=p, tau=tau, a=a, b=b, c=c, d=d, mats=mats)
+    prob = Problem(n=tuple(n), p=p, tau=tau, a=a, b=b, c=c, d=d, mats=mats, rhs_material=rhs_material)
+    if rhs_material == "quad":
+        ae, be, ce, de = material.coefficients(eps, mu, sigma, tau)
+        prob.elem = dict(a=ae, b=be, c=ce, d=de)
+    elif rhs_material != "row":
+        raise ValueError("rhs_material must be 'row' or 'quad'")
+    return prob
 
 
 def set_source(prob, x0, comp, amp, f0, t0, s):
@@ -93,7 +111,7 @@ def set_source(prob, x0, comp, amp, f0, t0, s):
     wx = bspline.point_values(nx, prob.p, x0[0])
     wy = bspline.point_values(ny, prob.p, x0[1])
     wz = bspline.point_values(nz, prob.p, x0[2])
-    prob.source = dict(w=np.einsum("k,j,i->kji", wz, wy, wx), comp=comp, amp=amp,
+    prob.source = dict(w=np.einsum("k,j,i->kji", wz, wy, wx), comp=comp, amp=amp, x0=tuple(x0),
                        f0=f0, t0=t0, s=s)
 
 
@@ -110,27 +128,74 @@ def _K(prob, ops, u):
     return kron3(X, Y, Z, u)
 
 
+def _quad_axes(prob):
+    """Per axis: Gauss points (p + 1 per element, exact for the degree-2p
+    integrands), weights, element of each point, basis values and derivatives."""
+    if getattr(prob, "_qa", None) is None:
+        out = []
+        for ne in prob.n:
+            x, w, e = bspline.gauss_points(ne, prob.p + 1)
+            v, d = bspline.eval_basis(ne, prob.p, x, e)
+            out.append((w, e, v, d))
+        prob._qa = out
+    return prob._qa
+
+
+def _Kq(prob, ops, u, kappa):
+    """sum_e kappa_e int_e (D_test B_rst) (D_trial u) over the elements e: the
+    Kronecker term named by ``ops`` with the per-element coefficient ``kappa``
+    (nz, ny, nx) inside the integral.  Per axis, A puts the derivative on the
+    trial function, B on the test function, S on both, M on neither."""
+    qa = _quad_axes(prob)
+    trial = [qa[a][3] if ops[a] in "AS" else qa[a][2] for a in range(3)]
+    test = [qa[a][3] if ops[a] in "BS" else qa[a][2] for a in range(3)]
+    val = apply_1d(trial[0], apply_1d(trial[1], apply_1d(trial[2], u, "z"), "y"), "x")
+    (wx, ex, _, _), (wy, ey, _, _), (wz, ez, _, _) = qa
+    wk = np.einsum("k,j,i->kji", wz, wy, wx) * kappa[ez[:, None, None], ey[None, :, None], ex[None, None, :]]
+    return apply_1d(test[0].T, apply_1d(test[1].T, apply_1d(test[2].T, val * wk, "z"), "y"), "x")
+
+
+def _term(prob, ops, u, coef):
+    """coef in 'a', 'b', 'c', 'd' or '1': the row-scaled term, or under "quad"
+    the term with the per-element coefficient inside the integral."""
+    if prob.rhs_material == "quad":
+        kappa = np.ones(prob.elem["a"].shape) if coef == "1" else prob.elem[coef]
+        return _Kq(prob, ops, u, kappa)
+    k = 1.0 if coef == "1" else getattr(prob, coef)
+    return k * _K(prob, ops, u)
+
+
+def _source_b(prob):
+    """b of the source row: the row's b ("row"), or b of the element that holds
+    the dipole ("quad", the element convention of the point evaluation)."""
+    if prob.rhs_material != "quad":
+        return prob.b
+    x0 = prob.source["x0"]
+    e = [min(int(np.floor(x0[a] * prob.n[a])), prob.n[a] - 1) for a in range(3)]
+    return prob.elem["b"][e[2], e[1], e[0]]
+
+
 def rhs_E(prob, half, E, H, t_mid):
     """Right-hand sides of the E rows, eq. (dupa1ab) for half step 1 (R1) and
     the analogous rows of eq. (discrete3) for half step 2 (R2), row-scaled."""
     E1, E2, E3 = E
     H1, H2, H3 = H
-    a, b, c = prob.a, prob.b, prob.c
+    T = lambda ops, u, k: _term(prob, ops, u, k)
     curl = (
-        -_K(prob, "MMA", H2) + _K(prob, "MAM", H3),
-        _K(prob, "MMA", H1) - _K(prob, "AMM", H3),
-        -_K(prob, "MAM", H1) + _K(prob, "AMM", H2),
+        -T("MMA", H2, "b") + T("MAM", H3, "b"),
+        T("MMA", H1, "b") - T("AMM", H3, "b"),
+        -T("MAM", H1, "b") + T("AMM", H2, "b"),
     )
     if half == 1:   # R1 = [[0, A(x)B(x)M, 0], [0, 0, M(x)A(x)B], [B(x)M(x)A, 0, 0]]
-        cross = (_K(prob, "ABM", E2), _K(prob, "MAB", E3), _K(prob, "BMA", E1))
+        cross = (T("ABM", E2, "c"), T("MAB", E3, "c"), T("BMA", E1, "c"))
     else:           # R2 = [[0, 0, A(x)M(x)B], [B(x)A(x)M, 0, 0], [0, M(x)B(x)A, 0]]
-        cross = (_K(prob, "AMB", E3), _K(prob, "BAM", E1), _K(prob, "MBA", E2))
+        cross = (T("AMB", E3, "c"), T("BAM", E1, "c"), T("MBA", E2, "c"))
     out = []
     for i, Ei in enumerate(E):
-        r = a * _K(prob, "MMM", Ei) + b * curl[i] + c * cross[i]
+        r = T("MMM", Ei, "a") + curl[i] + cross[i]
         if prob.source is not None and prob.source["comp"] == i:
             src = prob.source
-            r = r - b * src["amp"] * source_profile(src, t_mid) * src["w"]
+            r = r - _source_b(prob) * src["amp"] * source_profile(src, t_mid) * src["w"]
         out.append(r)
     return out
 
@@ -164,10 +229,10 @@ def rhs_H(prob, H, E_alpha, E_beta):
     H1, H2, H3 = H
     Ea1, Ea2, Ea3 = E_alpha
     Eb1, Eb2, Eb3 = E_beta
-    d = prob.d
-    C1 = (_K(prob, "MAM", Ea3), _K(prob, "MMA", Ea1), _K(prob, "AMM", Ea2))
-    C2 = (_K(prob, "MMA", Eb2), _K(prob, "AMM", Eb3), _K(prob, "MAM", Eb1))
-    return [_K(prob, "MMM", H[i]) + d * (-C1[i] + C2[i]) for i in range(3)]
+    T = lambda ops, u: _term(prob, ops, u, "d")
+    C1 = (T("MAM", Ea3), T("MMA", Ea1), T("AMM", Ea2))
+    C2 = (T("MMA", Eb2), T("AMM", Eb3), T("MAM", Eb1))
+    return [_K(prob, "MMM", H[i]) - C1[i] + C2[i] for i in range(3)]
 
 
 def solve_H(prob, rhs):

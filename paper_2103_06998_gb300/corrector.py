@@ -45,12 +45,13 @@ def cfl_tau(n, p, eps, mu, sigma, factor=4.0):
     return dt
 
 
-def solver_pair(n, p, k, seed, tau=None, f0=None):
+def solver_pair(n, p, k, seed, tau=None, f0=None, tau_factor=4.0):
     """Fine (tau) and coarse (k tau) FP32 solvers on map `seed` with its dipole
-    (carrier frequency f0 if given, else the dipole's own, with s = 1/f0, t0 = 3 s)."""
+    (carrier frequency f0 if given, else the dipole's own, with s = 1/f0, t0 = 3 s);
+    tau defaults to tau_factor x the map's explicit limit."""
     eps, mu, sigma, _ = inputs.head_map(n, seed)
     if tau is None:
-        tau = cfl_tau(n, p, eps, mu, sigma)
+        tau = cfl_tau(n, p, eps, mu, sigma, tau_factor)
     src = inputs.dipole(seed)
     if f0 is not None:
         src = dict(src, f0=f0, s=1.0 / f0, t0=3.0 / f0)
@@ -63,15 +64,16 @@ def solver_pair(n, p, k, seed, tau=None, f0=None):
     return out[0], out[1], tau
 
 
-def pairs(net, n, p, k, seeds, per_map, warm_time=0.5, f0s=(None,)):
+def pairs(net, n, p, k, seeds, per_map, warm_time=0.5, f0s=(None,), tau_factor=4.0):
     """List of (X, T) device tensors, `per_map` consecutive pairs per map; map i
-    is driven at carrier frequency f0s[i % len(f0s)] (None: the dipole's own)."""
+    is driven at carrier frequency f0s[i % len(f0s)] (None: the dipole's own);
+    fine step tau_factor x the explicit limit, coarse step k times that."""
     torch = _torch()
     N = tuple(v + p for v in n)
     V = N[0] * N[1] * N[2]
     out = []
     for m, sd in enumerate(seeds):
-        fine, coarse, tau = solver_pair(n, p, k, sd, f0=f0s[m % len(f0s)])
+        fine, coarse, tau = solver_pair(n, p, k, sd, f0=f0s[m % len(f0s)], tau_factor=tau_factor)
         fine.step(max(1, int(round(warm_time / tau))))
         for _ in range(per_map):
             X = torch.zeros((V, 16), dtype=torch.bfloat16, device="cuda")
@@ -149,6 +151,7 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=64)
     ap.add_argument("--p", type=int, default=2)
     ap.add_argument("--k", type=int, default=8)
+    ap.add_argument("--tau-factor", type=float, default=4.0, help="fine time step in units of the explicit limit")
     ap.add_argument("--maps", type=int, default=80)
     ap.add_argument("--per-map", type=int, default=25)
     ap.add_argument("--epochs", type=int, default=6)
@@ -164,8 +167,8 @@ def main(argv=None):
     net.set_params(adi.net_flatten(inputs.net_init(2103)))
     t0 = time.time()
     f0s = tuple(float(v) for v in a.f0.split(","))
-    data = pairs(net, n, a.p, a.k, range(10000, 10000 + a.maps), a.per_map, f0s=f0s)
-    held = pairs(net, n, a.p, a.k, range(20000, 20000 + a.test_maps), a.per_map)
+    data = pairs(net, n, a.p, a.k, range(10000, 10000 + a.maps), a.per_map, f0s=f0s, tau_factor=a.tau_factor)
+    held = pairs(net, n, a.p, a.k, range(20000, 20000 + a.test_maps), a.per_map, tau_factor=a.tau_factor)
     log("pairs: %d train, %d held out, %.1f s" % (len(data), len(held), time.time() - t0))
     b0, f0 = evaluate(net, held)
     t0 = time.time()

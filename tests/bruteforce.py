@@ -69,6 +69,22 @@ class Dense3D:
         U = self.phi if trial_deriv is None else self.grad[trial_deriv]
         return T.T @ (self.W[:, None] * U)
 
+    def inner_w(self, test_deriv, trial_deriv, elem_field):
+        """G[row, col] = sum_e f_e int_e D_test B_row D_trial B_col for a
+        per-element field f (nz, ny, nx): the weight of every Gauss point is
+        multiplied by f of the element that holds it."""
+        T = self.phi if test_deriv is None else self.grad[test_deriv]
+        U = self.phi if trial_deriv is None else self.grad[trial_deriv]
+        return T.T @ ((self.W * self._at_points(elem_field))[:, None] * U)
+
+    def _at_points(self, elem_field):
+        nx, ny, nz = self.n
+        q = self.p + 2
+        ex = np.repeat(np.arange(nx), q)
+        ey = np.repeat(np.arange(ny), q)
+        ez = np.repeat(np.arange(nz), q)
+        return elem_field[ez[:, None, None], ey[None, :, None], ex[None, None, :]].ravel()
+
     def free(self, dirs):
         """Mask of unconstrained DOFs for Dirichlet directions ``dirs`` (0,1,2)."""
         Nx, Ny, Nz = self.N
@@ -104,8 +120,11 @@ E_DIR = ((1, 2), (0, 2), (0, 1))
 H_DIR = ((0,), (1,), (2,))
 
 
-def e_substep(D, half, E, H, a, b, c, J=None):
-    """Dense solve of the E rows of half step ``half``; returns (E1, E2, E3)."""
+def e_substep(D, half, E, H, a, b, c, J=None, elem=None):
+    """Dense solve of the E rows of half step ``half``; returns (E1, E2, E3).
+    elem = (a_e, b_e, c_e, b_src): per-element coefficients inside the
+    right-hand side integrals (and b of the source row) instead of the row
+    scaling by a, b, c; the left-hand side stays row-scaled by c."""
     f = lambda u: np.asarray(u).ravel()
     a, b, c = f(a), f(b), f(c)
     mass = D.inner(None, None)
@@ -117,17 +136,23 @@ def e_substep(D, half, E, H, a, b, c, J=None):
     else:
         stiff = (2, 0, 1)
         cross = ((2, 0, E[2]), (0, 1, E[0]), (1, 2, E[1]))
-    curl = (-D.inner(None, 2) @ H[1] + D.inner(None, 1) @ H[2],
-            D.inner(None, 2) @ H[0] - D.inner(None, 0) @ H[2],
-            -D.inner(None, 1) @ H[0] + D.inner(None, 0) @ H[1])
+    if elem is None:
+        G = lambda td, ud, k: k * D.inner(td, ud)          # row-scaled
+        ka, kb, kc, bsrc = a[:, None], b[:, None], c[:, None], b
+    else:
+        G = lambda td, ud, k: D.inner_w(td, ud, k)         # coefficient in the integrand
+        ka, kb, kc, bsrc = elem
+    curl = (-G(None, 2, kb) @ H[1] + G(None, 1, kb) @ H[2],
+            G(None, 2, kb) @ H[0] - G(None, 0, kb) @ H[2],
+            -G(None, 1, kb) @ H[0] + G(None, 0, kb) @ H[1])
     out = []
     for i in range(3):
         s = stiff[i]
         lhs = mass + c[:, None] * D.inner(s, s)
         td, ud, fld = cross[i]
-        rhs = a * (mass @ E[i]) + b * curl[i] + c * (D.inner(td, ud) @ fld)
+        rhs = G(None, None, ka) @ E[i] + curl[i] + G(td, ud, kc) @ fld
         if J is not None:
-            rhs = rhs - b * J[i]
+            rhs = rhs - bsrc * J[i]
         m = D.free(E_DIR[i])
         x = np.zeros_like(rhs)
         x[m] = np.linalg.solve(lhs[np.ix_(m, m)], rhs[m])
@@ -135,17 +160,23 @@ def e_substep(D, half, E, H, a, b, c, J=None):
     return out
 
 
-def h_substep(D, H, E_alpha, E_beta, d):
+def h_substep(D, H, E_alpha, E_beta, d, d_elem=None):
+    """Dense solve of the H rows; d_elem: per-element d inside the integrals
+    instead of the row scaling by d."""
     f = lambda u: np.asarray(u).ravel()
     d = f(d)
     mass = D.inner(None, None)
     Ea = [f(u) for u in E_alpha]
     Eb = [f(u) for u in E_beta]
-    C1 = (D.inner(None, 1) @ Ea[2], D.inner(None, 2) @ Ea[0], D.inner(None, 0) @ Ea[1])
-    C2 = (D.inner(None, 2) @ Eb[1], D.inner(None, 0) @ Eb[2], D.inner(None, 1) @ Eb[0])
+    if d_elem is None:
+        G = lambda ud: d[:, None] * D.inner(None, ud)
+    else:
+        G = lambda ud: D.inner_w(None, ud, d_elem)
+    C1 = (G(1) @ Ea[2], G(2) @ Ea[0], G(0) @ Ea[1])
+    C2 = (G(2) @ Eb[1], G(0) @ Eb[2], G(1) @ Eb[0])
     out = []
     for i in range(3):
-        rhs = mass @ f(H[i]) + d * (-C1[i] + C2[i])
+        rhs = mass @ f(H[i]) - C1[i] + C2[i]
         m = D.free(H_DIR[i])
         x = np.zeros_like(rhs)
         x[m] = np.linalg.solve(mass[np.ix_(m, m)], rhs[m])
