@@ -68,12 +68,26 @@ typedef enum {
  *  The paper states no precision; this mode is an addition. */
 enum { ADI_PREC_FP64 = 0, ADI_PREC_FP32 = 1, ADI_PREC_MIXED = 2 };
 
+/* Where the per-element material enters the right-hand sides (section
+ * "Incorporating non-regular material data").  ADI_RHS_ROW (default, the
+ * paper's reading): every row rst is scaled by its coefficients a, b, c, d
+ * formed from the hat values eps^, mu^, sigma^ of test function rst.
+ * ADI_RHS_QUAD: each right-hand-side integral carries the element's own
+ * coefficients inside the integrand, sum_e kappa_e int_e (...) B_rst with
+ * kappa_e = a_e, b_e, c_e, d_e formed from the element's eps, mu, sigma by the
+ * same formulas (the dipole row uses b of the element that holds it).  The
+ * left-hand sides stay row-scaled in both readings (that keeps their Kronecker
+ * structure, hence the line solves); the two readings agree for uniform
+ * material.  With uniform mu the H half steps are the same in both. */
+enum { ADI_RHS_ROW = 0, ADI_RHS_QUAD = 1 };
+
 typedef struct {
   int precision;        /* ADI_PREC_FP32 (default), ADI_PREC_FP64 or ADI_PREC_MIXED */
   int use_graph;        /* 1 (default): adi_step replays a captured CUDA graph of one step */
   int mixed_no_refine;  /* ADI_PREC_MIXED only: 1 skips the refinement (E = E*, for error studies) */
   int mixed_fp64_residual; /* ADI_PREC_MIXED only: 1 evaluates the residual in FP64 (default 0: float-float) */
-  int reserved[4];      /* must be 0 */
+  int rhs_material;     /* ADI_RHS_ROW (default) or ADI_RHS_QUAD (not with ADI_PREC_MIXED) */
+  int reserved[3];      /* must be 0 */
 } adi_options;
 
 /* Create a problem on the unit cube.

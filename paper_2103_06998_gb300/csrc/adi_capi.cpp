@@ -35,7 +35,7 @@ void free_ctx(Ctx* c0) {
   adi_ctx* c = static_cast<adi_ctx*>(c0);
   if (c->graph) cudaGraphExecDestroy(c->graph);
   for (auto* l : c->pending) delete l;
-  void* ptrs[] = {c->d_eps,        c->d_mu,  c->d_sigma, c->stage,  c->tab,   c->tab64, c->tabff,
+  void* ptrs[] = {c->d_eps,        c->d_mu,  c->d_sigma, c->stage,  c->tab,   c->tab64, c->tabff, c->tabq,
                   c->d_clock_t0,   c->d_clock_step, c->d_err, c->d_bad, c->d_diag};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -162,12 +162,16 @@ static adi_status create_impl(int nx, int ny, int nz, int p, double dt, const do
   if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, ADI_EINVAL, "adi_create: element counts must be >= 1");
   if (p < 1 || p > adi::kMaxP) return fail(nullptr, ADI_EINVAL, "adi_create: p must be in 1..3");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(nullptr, ADI_EINVAL, "adi_create: dt must be finite and > 0");
-  int prec = ADI_PREC_FP32, use_graph = 1, refine = 1, res64 = 0;
+  int prec = ADI_PREC_FP32, use_graph = 1, refine = 1, res64 = 0, quad = 0;
   if (opt) {
     if (opt->precision != ADI_PREC_FP32 && opt->precision != ADI_PREC_FP64 && opt->precision != ADI_PREC_MIXED)
       return fail(nullptr, ADI_EINVAL, "adi_create: precision must be ADI_PREC_FP32, ADI_PREC_FP64 or ADI_PREC_MIXED");
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 3; ++i)
       if (opt->reserved[i] != 0) return fail(nullptr, ADI_EINVAL, "adi_create: reserved option fields must be 0");
+    if (opt->rhs_material != ADI_RHS_ROW && opt->rhs_material != ADI_RHS_QUAD)
+      return fail(nullptr, ADI_EINVAL, "adi_create: rhs_material must be ADI_RHS_ROW or ADI_RHS_QUAD");
+    if (opt->rhs_material == ADI_RHS_QUAD && opt->precision == ADI_PREC_MIXED)
+      return fail(nullptr, ADI_EINVAL, "adi_create: ADI_RHS_QUAD is not available with ADI_PREC_MIXED");
     if (opt->mixed_no_refine != 0 && opt->mixed_no_refine != 1)
       return fail(nullptr, ADI_EINVAL, "adi_create: mixed_no_refine must be 0 or 1");
     if (opt->mixed_fp64_residual != 0 && opt->mixed_fp64_residual != 1)
@@ -176,6 +180,7 @@ static adi_status create_impl(int nx, int ny, int nz, int p, double dt, const do
     use_graph = opt->use_graph ? 1 : 0;
     refine = opt->mixed_no_refine ? 0 : 1;
     res64 = opt->mixed_fp64_residual;
+    quad = opt->rhs_material == ADI_RHS_QUAD ? 1 : 0;
   }
   const size_t ne = (size_t)nx * ny * nz;
   for (const double* arr : {eps, mu}) {
@@ -203,6 +208,7 @@ static adi_status create_impl(int nx, int ny, int nz, int p, double dt, const do
   c->use_graph = use_graph;
   c->mixed_refine = prec == ADI_PREC_MIXED ? refine : 0;
   c->mixed_fp64_residual = res64;
+  c->rhs_quad = quad;
   c->esize = prec == ADI_PREC_FP64 ? 8 : 4;
   c->dt = dt;
   cudaError_t e = cudaGetDevice(&c->device);

@@ -35,6 +35,8 @@ void band_lu(const std::vector<double>& base, const std::vector<double>* stiff, 
              int lo, int hi, BandLU& out);
 double lambda_max(const Axis1D& ax);
 int point_basis(int n, int p, double x0, double* vals);
+// per-element blocks of M, S, A, B: loc[((e*4 + op)*(p+1) + test)*(p+1) + trial]
+void element_matrices(const Axis1D& ax, std::vector<double>& loc);
 
 // ---------------------------------------------------------- device structures
 // Operator codes of one Kronecker factor.
@@ -98,6 +100,30 @@ struct RhsParams {
   int* err;            // device status word: bit 0 = a bounded wait gave up
 };
 
+// Right-hand side with per-element coefficients inside the integrals: the
+// terms of RhsParams, the element blocks of the 1D matrices, the material.
+template <typename T>
+struct QuadParams {
+  const T* fields[9];
+  T* out[3];
+  const T* loc[3];  // per axis: [e][op M, S, A, B][test][trial]
+  const double* eps;
+  const double* mu;
+  const double* sigma;
+  double tau;
+  Term terms[kMaxTerms];
+  int nterms;
+  int n[3];
+  int Nx, Ny, Nz, pitch;
+  int src_comp;  // < 0: none
+  int src_e[3];  // element holding the dipole (its first B-spline per axis)
+  T src_w[3][kMaxP + 1];
+  double src_amp, src_f0, src_t0, src_s;
+  double t_frac;
+  const double* clock_t0;
+  const long long* clock_step;
+};
+
 // TMA descriptors of the six input fields of one E right-hand side launch.
 struct TmaMaps {
   CUtensorMap m[6];
@@ -147,6 +173,8 @@ struct Ctx {
   int precision = ADI_PREC_FP32;  // FP32 and MIXED keep FP32 state (element type float)
   int mixed_refine = 0;           // MIXED: one residual refinement per E half step
   int mixed_fp64_residual = 0;    // MIXED: the residual in FP64 arithmetic (default: float-float on the FP32 pipe)
+  int rhs_quad = 0;               // 1: per-element material inside the right-hand side integrals (ADI_RHS_QUAD)
+  void* tabq = nullptr;           // rhs_quad: element blocks of the 1D matrices per axis (element type T)
   int use_graph = 1;
   int line_tile = 0;  // lines per line-solve CTA (0: largest that leaves two CTAs per SM)
   bool line_stream = true;  // y / z stiffness solves on the streaming kernel (precomputed factors)

@@ -186,6 +186,136 @@ __global__ void __launch_bounds__(TX* TY) rhs_kernel(const RhsParams<T> prm) {
     *prm.clock_step += 1;
 }
 
+// ---------------------------- right-hand side, material inside the integrals
+// The "quad" reading of section "Incorporating non-regular material data": every
+// right-hand-side term is sum_e kappa_e int_e (D_test B_rst)(D_trial u), kappa_e
+// in {1, a_e, b_e, c_e, d_e} formed from the element's eps, mu, sigma (the same
+// formulas as the row coefficients).  With kappa constant on each element, the
+// integral over element e factorises into the element blocks of the 1D
+// matrices: (X_e (x) Y_e (x) Z_e) applied to the element's (p+1)^3
+// coefficients.  One CTA takes 8^3 elements (one thread each): each thread
+// applies its element's three (p+1) x (p+1) blocks to its coefficients (sum
+// factorisation inside the element), scales by kappa_e and adds the (p+1)^3
+// results into a shared tile of the outputs; the tile is then added into the
+// zeroed output arrays (neighbouring tiles share their border coefficients).
+// The source row uses b of the element that holds the dipole.
+template <typename T, int P>
+struct QuadTile {
+  static constexpr int TE = 8, Q = P + 1, HT = TE + P, HT3 = HT * HT * HT;
+  // output tiles in FP64 (the (p+1)^3 element contributions of a coefficient are
+  // summed in FP64 whatever the working precision), coefficient tile and blocks in T
+  static constexpr size_t BYTES = sizeof(double) * 3 * HT3 + sizeof(T) * (HT3 + (size_t)3 * TE * 4 * Q * Q);
+};
+
+template <typename T, int P>
+__global__ void __launch_bounds__(512) rhs_quad_kernel(const QuadParams<T> prm) {
+  using S = QuadTile<T, P>;
+  constexpr int TE = S::TE, Q = S::Q, HT = S::HT, HT3 = S::HT3;
+  extern __shared__ __align__(16) unsigned char quad_smem[];
+  double* s_out = reinterpret_cast<double*>(quad_smem);  // [3][HT3] output tiles (FP64 sums)
+  T* s_u = reinterpret_cast<T*>(s_out + 3 * HT3);        // the field's coefficient tile
+  T* s_loc = s_u + HT3;                                  // [axis][element][op][test][trial]
+  const int tid = threadIdx.x;
+  const int lx = tid % TE, ly = (tid / TE) % TE, lz = tid / (TE * TE);
+  const int e0[3] = {(int)blockIdx.x * TE, (int)blockIdx.y * TE, (int)blockIdx.z * TE};
+  const int ex = e0[0] + lx, ey = e0[1] + ly, ez = e0[2] + lz;
+  const bool ein = ex < prm.n[0] && ey < prm.n[1] && ez < prm.n[2];
+  const int Nx = prm.Nx, Ny = prm.Ny, Nz = prm.Nz, pitch = prm.pitch;
+  const long long sxy = (long long)pitch * Ny;
+  for (int i = tid; i < 3 * HT3; i += TE * TE * TE) s_out[i] = 0.0;
+  for (int i = tid; i < 3 * TE * 4 * Q * Q; i += TE * TE * TE) {
+    const int rc = i % (Q * Q), op = (i / (Q * Q)) % 4, le = (i / (4 * Q * Q)) % TE, ax = i / (4 * Q * Q * TE);
+    const int e = e0[ax] + le;
+    s_loc[i] = e < prm.n[ax] ? prm.loc[ax][((long long)e * 4 + op) * Q * Q + rc] : T(0);
+  }
+  auto loc = [&](int ax, int le, int op) { return s_loc + ((ax * TE + le) * 4 + op) * Q * Q; };
+  // this element's coefficients (FP64 from the per-element material, as the row coefficients)
+  double kap[5] = {1.0, 0.0, 0.0, 0.0, 0.0};  // indexed by Coef: 1, a, b, c, d
+  if (ein) {
+    const long long e = ((long long)ez * prm.n[1] + ey) * prm.n[0] + ex;
+    const double ep = prm.eps[e], mu = prm.mu[e], sg = prm.sigma[e], tau = prm.tau;
+    const double al = sg * tau / (4.0 * ep);
+    kap[CF_A] = (1.0 - al) / (1.0 + al);
+    kap[CF_B] = tau / (2.0 * ep * (1.0 + al));
+    kap[CF_C] = tau * tau / (4.0 * ep * mu * (1.0 + al));
+    kap[CF_D] = tau / (2.0 * mu);
+  }
+  const T* ub = s_u + (lz * HT + ly) * HT + lx;  // this element's first coefficient in the tile
+  int cur = -1;
+  for (int t = 0; t < prm.nterms; ++t) {
+    const Term tm = prm.terms[t];
+    if (tm.field != cur) {  // the coefficient tile of the field: (8 + p)^3, zero outside the grid
+      __syncthreads();
+      const T* __restrict__ f = prm.fields[tm.field];
+      for (int i = tid; i < HT3; i += TE * TE * TE) {
+        const int X = e0[0] + i % HT, Y = e0[1] + (i / HT) % HT, Z = e0[2] + i / (HT * HT);
+        s_u[i] = (X < Nx && Y < Ny && Z < Nz) ? f[Z * sxy + (long long)Y * pitch + X] : T(0);
+      }
+      cur = tm.field;
+      __syncthreads();
+    }
+    if (!ein) continue;
+    const T* Zm = loc(2, lz, tm.op[2]);
+    const T* Ym = loc(1, ly, tm.op[1]);
+    const T* Xm = loc(0, lx, tm.op[0]);
+    const T w = T((double)tm.sign * kap[tm.coef]);
+    double* o = s_out + tm.out * HT3 + (lz * HT + ly) * HT + lx;
+    // one output plane c' at a time (few live registers): z, y, then x with the scaling
+#pragma unroll
+    for (int c2 = 0; c2 < Q; ++c2) {
+      T t1[Q][Q];
+#pragma unroll
+      for (int b = 0; b < Q; ++b)
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+          T sm = T(0);
+#pragma unroll
+          for (int k = 0; k < Q; ++k) sm += Zm[c2 * Q + k] * ub[(k * HT + b) * HT + a];
+          t1[b][a] = sm;
+        }
+#pragma unroll
+      for (int b2 = 0; b2 < Q; ++b2) {
+        T t2[Q];
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+          T sm = T(0);
+#pragma unroll
+          for (int k = 0; k < Q; ++k) sm += Ym[b2 * Q + k] * t1[k][a];
+          t2[a] = sm;
+        }
+#pragma unroll
+        for (int a2 = 0; a2 < Q; ++a2) {
+          T sm = T(0);
+#pragma unroll
+          for (int k = 0; k < Q; ++k) sm += Xm[a2 * Q + k] * t2[k];
+          atomicAdd(&o[(c2 * HT + b2) * HT + a2], (double)(w * sm));
+        }
+      }
+    }
+  }
+  if (prm.src_comp >= 0 && ein && ex == prm.src_e[0] && ey == prm.src_e[1] && ez == prm.src_e[2]) {
+    const double tmid = *prm.clock_t0 + ((double)*prm.clock_step + prm.t_frac) * prm.tau;
+    const double uu = tmid - prm.src_t0;
+    const double g = prm.src_amp * sin(2.0 * 3.14159265358979323846 * prm.src_f0 * uu) *
+                     exp(-(uu / prm.src_s) * (uu / prm.src_s));
+    const double bg = kap[CF_B] * g;
+    double* o = s_out + prm.src_comp * HT3 + (lz * HT + ly) * HT + lx;
+    for (int c = 0; c < Q; ++c)
+      for (int b = 0; b < Q; ++b)
+        for (int a = 0; a < Q; ++a)
+          atomicAdd(&o[(c * HT + b) * HT + a],
+                    -bg * (double)prm.src_w[0][a] * (double)prm.src_w[1][b] * (double)prm.src_w[2][c]);
+  }
+  __syncthreads();
+  for (int i = tid; i < HT3; i += TE * TE * TE) {
+    const int X = e0[0] + i % HT, Y = e0[1] + (i / HT) % HT, Z = e0[2] + i / (HT * HT);
+    if (X >= Nx || Y >= Ny || Z >= Nz) continue;
+    const long long g = Z * sxy + (long long)Y * pitch + X;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) atomicAdd(prm.out[c] + g, T(s_out[c * HT3 + i]));  // result unused: a reduction in L2
+  }
+}
+
 // ------------------------------------- mixed-mode E right-hand side (BF16 MMA)
 // The contraction of eq. dupa1ab (and its half-step-2 analogue) with BF16
 // operands on the tensor cores: per 32 x 8 x 8 output tile and Kronecker term,
@@ -2548,6 +2678,24 @@ AxisDev<T> axis_dev(const Ctx& c, int d) {
   return a;
 }
 
+// element blocks of the 1D matrices (rhs_quad), per axis, in the working precision
+template <typename T>
+cudaError_t upload_quad_tables(Ctx& c) {
+  std::vector<T> h;
+  for (int d = 0; d < 3; ++d) {
+    std::vector<double> loc;
+    element_matrices(c.axes[d], loc);
+    for (double v : loc) h.push_back(T(v));
+  }
+  if (!c.tabq) {
+    cudaError_t e = cudaMalloc(&c.tabq, h.size() * sizeof(T));
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e = cudaMemcpyAsync(c.tabq, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, c.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  return e;
+}
+
 template <typename T>
 cudaError_t upload_tables_t(Ctx& c) {
   Layout<T> L = table_layout<T>(c);
@@ -3056,6 +3204,55 @@ cudaError_t launch_resid_ff(Ctx& c, int half, float* const* Ein, float* const* H
   return cudaGetLastError();
 }
 
+// Right-hand side with the material inside the integrals (rhs_quad): zero the
+// outputs, then one launch over tiles of 8^3 elements.  fields / terms as for
+// rhs_kernel; the source (E half steps) with b of the element holding it.
+template <typename T, int P>
+cudaError_t launch_rhs_quad(Ctx& c, const T* const* fields, int nfields, T* const* out, const Term* terms,
+                            int nterms, bool source, double t_frac) {
+  QuadParams<T> prm{};
+  for (int i = 0; i < nfields; ++i) prm.fields[i] = fields[i];
+  for (int i = 0; i < 3; ++i) {
+    prm.out[i] = out[i];
+    cudaError_t e = cudaMemsetAsync(out[i], 0, c.Np * sizeof(T), c.stream);
+    if (e != cudaSuccess) return e;
+  }
+  const T* tq = reinterpret_cast<const T*>(c.tabq);
+  size_t off = 0;
+  for (int d = 0; d < 3; ++d) {
+    prm.loc[d] = tq + off;
+    off += (size_t)c.n[d] * 4 * (P + 1) * (P + 1);
+    prm.n[d] = c.n[d];
+  }
+  prm.eps = c.d_eps;
+  prm.mu = c.d_mu;
+  prm.sigma = c.d_sigma;
+  prm.tau = c.dt;
+  for (int k = 0; k < nterms; ++k) prm.terms[k] = terms[k];
+  prm.nterms = nterms;
+  prm.Nx = c.N[0];
+  prm.Ny = c.N[1];
+  prm.Nz = c.N[2];
+  prm.pitch = c.pitch;
+  prm.src_comp = (source && c.src_comp >= 0 && c.src_amp != 0.0) ? c.src_comp : -1;
+  for (int d = 0; d < 3; ++d) {
+    prm.src_e[d] = c.src_i0[d];
+    for (int q = 0; q <= kMaxP; ++q) prm.src_w[d][q] = T(c.src_w[d][q]);
+  }
+  prm.src_amp = c.src_amp;
+  prm.src_f0 = c.src_f0;
+  prm.src_t0 = c.src_t0;
+  prm.src_s = c.src_s;
+  prm.t_frac = t_frac;
+  prm.clock_t0 = c.d_clock_t0;
+  prm.clock_step = c.d_clock_step;
+  dim3 grid((c.n[0] + 7) / 8, (c.n[1] + 7) / 8, (c.n[2] + 7) / 8);
+  prof_begin(c, "rhs_quad", (double)c.Nc * sizeof(T) * (nfields + 3));
+  rhs_quad_kernel<T, P><<<grid, 512, QuadTile<T, P>::BYTES, c.stream>>>(prm);
+  prof_end(c);
+  return cudaGetLastError();
+}
+
 // E half step: the right-hand side, then the line solves (e_solve).
 template <typename T, int P>
 cudaError_t e_substep(Ctx& c, int half) {
@@ -3099,7 +3296,8 @@ cudaError_t e_substep(Ctx& c, int half) {
   prm.advance_clock = 0;
   double bytes = (double)c.Nc * sizeof(T) * 12.0;
   const bool mixed = c.precision == ADI_PREC_MIXED;
-  cudaError_t e = launch_rhs_e<T, P>(c, prm, half, bytes, mixed);
+  cudaError_t e = c.rhs_quad ? launch_rhs_quad<T, P>(c, prm.fields, 6, R, prm.terms, prm.nterms, true, prm.t_frac)
+                             : launch_rhs_e<T, P>(c, prm, half, bytes, mixed);
   if (e != cudaSuccess) return e;
   e = e_solve<T, P>(c, half, R, Eout);
   if (e != cudaSuccess || !mixed || !c.mixed_refine) return e;
@@ -3153,7 +3351,13 @@ cudaError_t h_substep_general(Ctx& c, int half) {
   prm.clock_step = c.d_clock_step;
   prm.advance_clock = half == 2 ? 1 : 0;
   double bytes = (double)c.Nc * sizeof(T) * 13.0;
-  cudaError_t e = launch_rhs<T, P>(c, prm, "rhs_H", bytes);
+  cudaError_t e;
+  if (c.rhs_quad) {  // the clock advances in its own launch (the quad kernel does not touch it)
+    e = launch_rhs_quad<T, P>(c, prm.fields, 9, R, prm.terms, prm.nterms, false, 0.0);
+    if (e == cudaSuccess && half == 2) e = advance_clock(c);
+  } else {
+    e = launch_rhs<T, P>(c, prm, "rhs_H", bytes);
+  }
   if (e != cudaSuccess) return e;
   static const char* mass_name[3] = {"line_x_mass", "line_y_mass", "line_z_mass"};
   for (int d = 0; d < 3; ++d) {
@@ -3280,6 +3484,7 @@ cudaError_t prepare_tp(int optin) {
     if (e == cudaSuccess) e = opt_in(resid_kernel<P>, optin);
     if (e == cudaSuccess) e = opt_in(resid_ff_kernel<P>, optin);
   }
+  if (e == cudaSuccess) e = opt_in(rhs_quad_kernel<T, P>, optin);
   if (e == cudaSuccess) e = opt_in(line_kernel<T, P, LM_MASS, true>, optin);
   if (e == cudaSuccess) e = opt_in(line_kernel<T, P, LM_STIFF, true>, optin);
   if (e == cudaSuccess) e = opt_in(line_kernel<T, P, LM_DERIV, true>, optin);
@@ -3474,6 +3679,7 @@ cudaError_t pivots_t(Ctx& c) {
 cudaError_t upload_tables_f64(Ctx& c, int optin) {
   cudaError_t e = prepare_t<double>(c.p, optin);
   if (e == cudaSuccess) e = upload_tables_t<double>(c);
+  if (e == cudaSuccess && c.rhs_quad) e = upload_quad_tables<double>(c);
   if (e == cudaSuccess) e = pivots_t<double>(c);
   return e;
 }
@@ -3508,6 +3714,7 @@ cudaError_t upload_tables(Ctx& c) {
   e = prepare_t<float>(c.p, optin);
   if (e != cudaSuccess) return e;
   e = upload_tables_t<float>(c);
+  if (e == cudaSuccess && c.rhs_quad) e = upload_quad_tables<float>(c);
   if (e != cudaSuccess) return e;
   if (c.precision == ADI_PREC_MIXED) {  // FP64 bands for the residual: per axis M, S, A, B
     std::vector<double> h;

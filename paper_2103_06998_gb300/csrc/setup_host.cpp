@@ -142,6 +142,35 @@ void build_axis(int n, int p, Axis1D& ax) {
   }
 }
 
+// The same integrals restricted to one element: loc[((e * 4 + op) * (p+1) + a) *
+// (p+1) + b] = int over element e of the op's integrand for test function e + a
+// and trial function e + b, op = M, S, A, B (as the bands; the bands are the
+// sums of these blocks over the elements).  Used by the right-hand side with
+// per-element material inside the integrals.
+void element_matrices(const Axis1D& ax, std::vector<double>& loc) {
+  const int n = ax.n, p = ax.p, Q = p + 1;
+  loc.assign(size_t(n) * 4 * Q * Q, 0.0);
+  std::vector<double> U = knots(n, p), gx, gw;
+  gauss_legendre(p + 1, gx, gw);
+  std::vector<double> v(p + 1), d(p + 1);
+  const double h = 1.0 / n;
+  for (int e = 0; e < n; ++e) {
+    double* blk = loc.data() + size_t(e) * 4 * Q * Q;
+    for (int q = 0; q <= p; ++q) {
+      double t = (e + 0.5) * h + 0.5 * h * gx[q];
+      double w = 0.5 * h * gw[q];
+      local_basis(U, p, e, t, v.data(), d.data());
+      for (int a = 0; a <= p; ++a)
+        for (int b = 0; b <= p; ++b) {
+          blk[0 * Q * Q + a * Q + b] += w * v[b] * v[a];
+          blk[1 * Q * Q + a * Q + b] += w * d[b] * d[a];
+          blk[2 * Q * Q + a * Q + b] += w * d[b] * v[a];
+          blk[3 * Q * Q + a * Q + b] += w * v[b] * d[a];
+        }
+    }
+  }
+}
+
 // Doolittle LU without pivoting of the banded matrix base + diag(c) stiff on
 // rows lo..hi (columns outside are dropped).  c may be null (c = 0).
 void band_lu(const std::vector<double>& base, const std::vector<double>* stiff, int N, int p,
