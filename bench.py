@@ -432,6 +432,48 @@ def run_learned(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def quad_result(n, tau, eps, mu, sigma, src, st, steps, warmup, local=0):
+    """The quad reading of the material (per-element coefficients inside the
+    right-hand side integrals) on the same workload in FP32: time per step, and
+    its one-step error against the FP64 GPU step of the same reading."""
+    import torch
+    from paper_2103_06998_gb300 import adi
+    out = {}
+    for prec in ("fp64", "fp32"):
+        s = adi.Solver((n, n, n), P, tau, eps, mu, sigma, precision=prec, rhs_material="quad")
+        s.factor()
+        s.set_source(src["x0"], src["comp"], src["amp"], src["f0"], src["t0"], src["s"])
+        stream = torch.cuda.Stream()
+        torch.cuda.set_stream(stream)
+        s.set_stream(stream.cuda_stream)
+        s.set_fields(st, 1.5)
+        s.step(1)
+        out[prec] = s.fields()[0]
+        if prec == "fp32":
+            for _ in range(warmup):
+                s.step(1)
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with ClockSampler(local) as clk:
+                ev0.record(stream)
+                s.step(steps)
+                ev1.record(stream)
+                torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1) / steps
+            s.set_profiling(True)
+            s.step(1)
+            stats = s.kernel_stats()
+            s.set_profiling(False)
+        s.close()
+        torch.cuda.set_stream(torch.cuda.default_stream())
+    a, b = out["fp32"], out["fp64"]
+    Nc = (n + P) ** 3
+    return {"value": 6 * Nc / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps, "warmup": warmup,
+            "error_vs_fp64_per_step": float(np.sqrt(np.sum((a - b) ** 2) / np.sum(b ** 2))), "dtype": "f32",
+            "reading": "per-element eps, mu, sigma inside the right-hand side integrals (ADI_RHS_QUAD)",
+            "kernels_ms_per_step": {k["name"]: k["total_ms"] for k in stats}, "clocks": clk.summary()}
+
+
 def mixed_result(n, tau, eps, mu, sigma, src, st, ref64, steps, warmup, local=0):
     """The mixed-precision step on the same workload: time per step over ``steps``
     graph replays, and its one-step error against the FP64 GPU step ``ref64``
@@ -612,13 +654,17 @@ def main():
     extras = {}
     if rank == 0 and world == 1 and not args.no_extras and args.precision == "fp32":
         # the other forms of the method, each measured here on its own workload (untimed by the driver's
-        # clock of the FP32 step above): mixed precision on the same 256^3 map, the 48-instance batch, and
-        # the guarded learned corrector at 128^3
+        # clock of the FP32 step above): mixed precision and the quad reading of the material on the same
+        # 256^3 map, the 48-instance batch, and the guarded learned corrector at 128^3
         try:
             extras["mixed"] = mixed_result(n, tau, eps, mu, sigma, src, st, ref64, 5, 2, local)
             extras["mixed"]["vs_fp32_sim_time"] = extras["mixed"]["sim_per_s"] / (tau / (ms_max * 1e-3 / args.steps))
         except Exception as ex:  # reported, never silently dropped
             extras["mixed"] = {"error": repr(ex)}
+        try:
+            extras["quad"] = quad_result(n, tau, eps, mu, sigma, src, st, 5, 2, local)
+        except Exception as ex:
+            extras["quad"] = {"error": repr(ex)}
         try:
             extras["batched"] = batched_result("fp32", 10, 3, rank, local)
         except Exception as ex:

@@ -193,28 +193,35 @@ __global__ void __launch_bounds__(TX* TY) rhs_kernel(const RhsParams<T> prm) {
 // formulas as the row coefficients).  With kappa constant on each element, the
 // integral over element e factorises into the element blocks of the 1D
 // matrices: (X_e (x) Y_e (x) Z_e) applied to the element's (p+1)^3
-// coefficients.  One CTA takes 8^3 elements (one thread each): each thread
-// applies its element's three (p+1) x (p+1) blocks to its coefficients (sum
-// factorisation inside the element), scales by kappa_e and adds the (p+1)^3
-// results into a shared tile of the outputs; the tile is then added into the
-// zeroed output arrays (neighbouring tiles share their border coefficients).
-// The source row uses b of the element that holds the dipole.
+// coefficients.  One CTA takes 8^3 elements (one thread each) and holds the
+// coefficient tiles of all input fields.  Per output component and output
+// plane c' of the element, each thread sums its element's contributions of the
+// component's terms (sum factorisation inside the element, scaled by sign
+// kappa_e) into (p+1)^2 registers and stores them; then every point of the
+// tile gathers the contributions of the elements whose plane c' covers it and
+// adds them to an FP64 output tile (no atomics).  The tile is finally added
+// into the zeroed output arrays (neighbouring tiles share their border
+// coefficients).  The source row uses b of the element that holds the dipole.
 template <typename T, int P>
 struct QuadTile {
-  static constexpr int TE = 8, Q = P + 1, HT = TE + P, HT3 = HT * HT * HT;
-  // output tiles in FP64 (the (p+1)^3 element contributions of a coefficient are
-  // summed in FP64 whatever the working precision), coefficient tile and blocks in T
-  static constexpr size_t BYTES = sizeof(double) * 3 * HT3 + sizeof(T) * (HT3 + (size_t)3 * TE * 4 * Q * Q);
+  static constexpr int TE = 8, Q = P + 1, HT = TE + P, HT3 = HT * HT * HT, NE = TE * TE * TE;
+  // FP64 output tiles, then (T) the element contributions of one plane, the
+  // coefficient tiles of up to 9 fields and the element blocks
+  static constexpr size_t OUT_B = sizeof(double) * 3 * HT3;
+  static size_t bytes(int nfields) {
+    return OUT_B + sizeof(T) * ((size_t)Q * Q * NE + (size_t)nfields * HT3 + (size_t)3 * TE * 4 * Q * Q);
+  }
 };
 
 template <typename T, int P>
-__global__ void __launch_bounds__(512) rhs_quad_kernel(const QuadParams<T> prm) {
+__global__ void __launch_bounds__(512) rhs_quad_kernel(const QuadParams<T> prm, int nfields) {
   using S = QuadTile<T, P>;
-  constexpr int TE = S::TE, Q = S::Q, HT = S::HT, HT3 = S::HT3;
+  constexpr int TE = S::TE, Q = S::Q, HT = S::HT, HT3 = S::HT3, NE = S::NE;
   extern __shared__ __align__(16) unsigned char quad_smem[];
-  double* s_out = reinterpret_cast<double*>(quad_smem);  // [3][HT3] output tiles (FP64 sums)
-  T* s_u = reinterpret_cast<T*>(s_out + 3 * HT3);        // the field's coefficient tile
-  T* s_loc = s_u + HT3;                                  // [axis][element][op][test][trial]
+  double* s_out = reinterpret_cast<double*>(quad_smem);           // [3][HT3]
+  T* s_con = reinterpret_cast<T*>(quad_smem + S::OUT_B);          // [Q][Q][NE] contributions of one plane
+  T* s_u = s_con + Q * Q * NE;                                     // [nfields][HT3]
+  T* s_loc = s_u + nfields * HT3;                                  // [axis][element][op][test][trial]
   const int tid = threadIdx.x;
   const int lx = tid % TE, ly = (tid / TE) % TE, lz = tid / (TE * TE);
   const int e0[3] = {(int)blockIdx.x * TE, (int)blockIdx.y * TE, (int)blockIdx.z * TE};
@@ -222,11 +229,18 @@ __global__ void __launch_bounds__(512) rhs_quad_kernel(const QuadParams<T> prm) 
   const bool ein = ex < prm.n[0] && ey < prm.n[1] && ez < prm.n[2];
   const int Nx = prm.Nx, Ny = prm.Ny, Nz = prm.Nz, pitch = prm.pitch;
   const long long sxy = (long long)pitch * Ny;
-  for (int i = tid; i < 3 * HT3; i += TE * TE * TE) s_out[i] = 0.0;
-  for (int i = tid; i < 3 * TE * 4 * Q * Q; i += TE * TE * TE) {
+  for (int i = tid; i < 3 * HT3; i += NE) s_out[i] = 0.0;
+  for (int i = tid; i < 3 * TE * 4 * Q * Q; i += NE) {
     const int rc = i % (Q * Q), op = (i / (Q * Q)) % 4, le = (i / (4 * Q * Q)) % TE, ax = i / (4 * Q * Q * TE);
     const int e = e0[ax] + le;
     s_loc[i] = e < prm.n[ax] ? prm.loc[ax][((long long)e * 4 + op) * Q * Q + rc] : T(0);
+  }
+  for (int f = 0; f < nfields; ++f) {  // coefficient tiles (8 + p)^3, zero outside the grid
+    const T* __restrict__ src = prm.fields[f];
+    for (int i = tid; i < HT3; i += NE) {
+      const int X = e0[0] + i % HT, Y = e0[1] + (i / HT) % HT, Z = e0[2] + i / (HT * HT);
+      s_u[f * HT3 + i] = (X < Nx && Y < Ny && Z < Nz) ? src[Z * sxy + (long long)Y * pitch + X] : T(0);
+    }
   }
   auto loc = [&](int ax, int le, int op) { return s_loc + ((ax * TE + le) * 4 + op) * Q * Q; };
   // this element's coefficients (FP64 from the per-element material, as the row coefficients)
@@ -240,74 +254,97 @@ __global__ void __launch_bounds__(512) rhs_quad_kernel(const QuadParams<T> prm) 
     kap[CF_C] = tau * tau / (4.0 * ep * mu * (1.0 + al));
     kap[CF_D] = tau / (2.0 * mu);
   }
-  const T* ub = s_u + (lz * HT + ly) * HT + lx;  // this element's first coefficient in the tile
-  int cur = -1;
-  for (int t = 0; t < prm.nterms; ++t) {
-    const Term tm = prm.terms[t];
-    if (tm.field != cur) {  // the coefficient tile of the field: (8 + p)^3, zero outside the grid
-      __syncthreads();
-      const T* __restrict__ f = prm.fields[tm.field];
-      for (int i = tid; i < HT3; i += TE * TE * TE) {
-        const int X = e0[0] + i % HT, Y = e0[1] + (i / HT) % HT, Z = e0[2] + i / (HT * HT);
-        s_u[i] = (X < Nx && Y < Ny && Z < Nz) ? f[Z * sxy + (long long)Y * pitch + X] : T(0);
-      }
-      cur = tm.field;
-      __syncthreads();
-    }
-    if (!ein) continue;
-    const T* Zm = loc(2, lz, tm.op[2]);
-    const T* Ym = loc(1, ly, tm.op[1]);
-    const T* Xm = loc(0, lx, tm.op[0]);
-    const T w = T((double)tm.sign * kap[tm.coef]);
-    double* o = s_out + tm.out * HT3 + (lz * HT + ly) * HT + lx;
-    // one output plane c' at a time (few live registers): z, y, then x with the scaling
-#pragma unroll
-    for (int c2 = 0; c2 < Q; ++c2) {
-      T t1[Q][Q];
-#pragma unroll
-      for (int b = 0; b < Q; ++b)
-#pragma unroll
-        for (int a = 0; a < Q; ++a) {
-          T sm = T(0);
-#pragma unroll
-          for (int k = 0; k < Q; ++k) sm += Zm[c2 * Q + k] * ub[(k * HT + b) * HT + a];
-          t1[b][a] = sm;
-        }
-#pragma unroll
-      for (int b2 = 0; b2 < Q; ++b2) {
-        T t2[Q];
-#pragma unroll
-        for (int a = 0; a < Q; ++a) {
-          T sm = T(0);
-#pragma unroll
-          for (int k = 0; k < Q; ++k) sm += Ym[b2 * Q + k] * t1[k][a];
-          t2[a] = sm;
-        }
-#pragma unroll
-        for (int a2 = 0; a2 < Q; ++a2) {
-          T sm = T(0);
-#pragma unroll
-          for (int k = 0; k < Q; ++k) sm += Xm[a2 * Q + k] * t2[k];
-          atomicAdd(&o[(c2 * HT + b2) * HT + a2], (double)(w * sm));
-        }
-      }
-    }
-  }
-  if (prm.src_comp >= 0 && ein && ex == prm.src_e[0] && ey == prm.src_e[1] && ez == prm.src_e[2]) {
+  const bool src_here = prm.src_comp >= 0 && ein && ex == prm.src_e[0] && ey == prm.src_e[1] && ez == prm.src_e[2];
+  double bg = 0.0;
+  if (src_here) {
     const double tmid = *prm.clock_t0 + ((double)*prm.clock_step + prm.t_frac) * prm.tau;
     const double uu = tmid - prm.src_t0;
-    const double g = prm.src_amp * sin(2.0 * 3.14159265358979323846 * prm.src_f0 * uu) *
-                     exp(-(uu / prm.src_s) * (uu / prm.src_s));
-    const double bg = kap[CF_B] * g;
-    double* o = s_out + prm.src_comp * HT3 + (lz * HT + ly) * HT + lx;
-    for (int c = 0; c < Q; ++c)
-      for (int b = 0; b < Q; ++b)
-        for (int a = 0; a < Q; ++a)
-          atomicAdd(&o[(c * HT + b) * HT + a],
-                    -bg * (double)prm.src_w[0][a] * (double)prm.src_w[1][b] * (double)prm.src_w[2][c]);
+    bg = kap[CF_B] * prm.src_amp * sin(2.0 * 3.14159265358979323846 * prm.src_f0 * uu) *
+         exp(-(uu / prm.src_s) * (uu / prm.src_s));
   }
+  const int eoff = (lz * HT + ly) * HT + lx;  // this element's first coefficient in a tile
   __syncthreads();
-  for (int i = tid; i < HT3; i += TE * TE * TE) {
+  for (int comp = 0; comp < 3; ++comp) {
+    for (int c2 = 0; c2 < Q; ++c2) {
+      T acc[Q][Q];
+#pragma unroll
+      for (int b = 0; b < Q; ++b)
+#pragma unroll
+        for (int a = 0; a < Q; ++a) acc[b][a] = T(0);
+      if (ein) {
+        for (int t = 0; t < prm.nterms; ++t) {
+          const Term tm = prm.terms[t];
+          if (tm.out != comp) continue;
+          const T* ub = s_u + tm.field * HT3 + eoff;
+          const T* Zm = loc(2, lz, tm.op[2]) + c2 * Q;
+          const T* Ym = loc(1, ly, tm.op[1]);
+          const T* Xm = loc(0, lx, tm.op[0]);
+          const T w = T((double)tm.sign * kap[tm.coef]);
+          T t1[Q][Q];
+#pragma unroll
+          for (int b = 0; b < Q; ++b)
+#pragma unroll
+            for (int a = 0; a < Q; ++a) {
+              T sm = T(0);
+#pragma unroll
+              for (int k = 0; k < Q; ++k) sm += Zm[k] * ub[(k * HT + b) * HT + a];
+              t1[b][a] = sm;
+            }
+#pragma unroll
+          for (int b2 = 0; b2 < Q; ++b2) {
+            T t2[Q];
+#pragma unroll
+            for (int a = 0; a < Q; ++a) {
+              T sm = T(0);
+#pragma unroll
+              for (int k = 0; k < Q; ++k) sm += Ym[b2 * Q + k] * t1[k][a];
+              t2[a] = sm;
+            }
+#pragma unroll
+            for (int a2 = 0; a2 < Q; ++a2) {
+              T sm = T(0);
+#pragma unroll
+              for (int k = 0; k < Q; ++k) sm += Xm[a2 * Q + k] * t2[k];
+              acc[b2][a2] += w * sm;
+            }
+          }
+        }
+        if (src_here && comp == prm.src_comp) {
+#pragma unroll
+          for (int b = 0; b < Q; ++b)
+#pragma unroll
+            for (int a = 0; a < Q; ++a)
+              acc[b][a] -= T(bg * (double)prm.src_w[0][a] * (double)prm.src_w[1][b] * (double)prm.src_w[2][c2]);
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < Q; ++b)
+#pragma unroll
+        for (int a = 0; a < Q; ++a) s_con[(b * Q + a) * NE + tid] = ein ? acc[b][a] : T(0);
+      __syncthreads();
+      // every tile point (Z, Y, X) of plane offset c2 gathers from the elements (Z - c2, Y - b, X - a)
+      for (int i = tid; i < HT3; i += NE) {
+        const int X = i % HT, Y = (i / HT) % HT, Z = i / (HT * HT);
+        const int zl = Z - c2;
+        if (zl < 0 || zl >= TE) continue;
+        double sm = 0.0;
+#pragma unroll
+        for (int b = 0; b < Q; ++b) {
+          const int yl = Y - b;
+          if (yl < 0 || yl >= TE) continue;
+#pragma unroll
+          for (int a = 0; a < Q; ++a) {
+            const int xl = X - a;
+            if (xl < 0 || xl >= TE) continue;
+            sm += (double)s_con[(b * Q + a) * NE + (zl * TE + yl) * TE + xl];
+          }
+        }
+        s_out[comp * HT3 + i] += sm;
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = tid; i < HT3; i += NE) {
     const int X = e0[0] + i % HT, Y = e0[1] + (i / HT) % HT, Z = e0[2] + i / (HT * HT);
     if (X >= Nx || Y >= Ny || Z >= Nz) continue;
     const long long g = Z * sxy + (long long)Y * pitch + X;
@@ -3248,7 +3285,7 @@ cudaError_t launch_rhs_quad(Ctx& c, const T* const* fields, int nfields, T* cons
   prm.clock_step = c.d_clock_step;
   dim3 grid((c.n[0] + 7) / 8, (c.n[1] + 7) / 8, (c.n[2] + 7) / 8);
   prof_begin(c, "rhs_quad", (double)c.Nc * sizeof(T) * (nfields + 3));
-  rhs_quad_kernel<T, P><<<grid, 512, QuadTile<T, P>::BYTES, c.stream>>>(prm);
+  rhs_quad_kernel<T, P><<<grid, 512, QuadTile<T, P>::bytes(nfields), c.stream>>>(prm, nfields);
   prof_end(c);
   return cudaGetLastError();
 }

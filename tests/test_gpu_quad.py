@@ -3,11 +3,8 @@ inside the right-hand side integrals, element-wise kernel) against the FP64
 oracle's quad form, element by element; and equal to the row reading for
 uniform material on the GPU as well.
 
-Tolerances per step: those of the row reading (tests/test_gpu_parity.py),
-except FP32 with p = 3 and white-noise material and state, 1e-4 (measured
-3.5e-5): on top of the mass-matrix amplification of that case, each
-coefficient's right-hand side is the FP32 sum of the contributions of its
-(p+1)^3 = 64 elements, added in no fixed order."""
+Tolerances per step: those of the row reading (tests/test_gpu_parity.py); the
+(p+1)^3 element contributions of each coefficient are summed in FP64."""
 import numpy as np
 import pytest
 
@@ -52,9 +49,8 @@ def test_quad_step_matches_oracle(n, p, kind, prec):
     got, t = s.fields()
     s.close()
     assert abs(t - (1.6 + tau)) < 1e-12
-    # per step from an identical state (see the module docstring)
-    bound = 1e-4 if (prec == "fp32" and p == 3 and kind == "random") else tol(prec, p, kind)
-    assert_parity(got, ref, bound, what="quad %s p=%d %s" % (prec, p, kind))
+    # per step from an identical state
+    assert_parity(got, ref, tol(prec, p, kind), what="quad %s p=%d %s" % (prec, p, kind))
     # the quad reading is a different discretisation than the row one on this material
     row = ma.make_problem(n, p, tau, eps, mu, sigma)
     ma.set_source(row, src["x0"], src["comp"], src["amp"], src["f0"], src["t0"], src["s"])
