@@ -198,8 +198,9 @@ __global__ void __launch_bounds__(TX* TY) rhs_kernel(const RhsParams<T> prm) {
 // plane c' of the element, each thread sums its element's contributions of the
 // component's terms (sum factorisation inside the element, scaled by sign
 // kappa_e) into (p+1)^2 registers and stores them; then every point of the
-// tile gathers the contributions of the elements whose plane c' covers it and
-// adds them to an FP64 output tile (no atomics).  The tile is finally added
+// tile gathers the contributions of the elements whose plane c' covers it
+// (summed in the working precision) and adds them to an FP64 output tile (no
+// atomics; the planes' partial sums meet in FP64).  The tile is finally added
 // into the zeroed output arrays (neighbouring tiles share their border
 // coefficients).  The source row uses b of the element that holds the dipole.
 template <typename T, int P>
@@ -254,6 +255,9 @@ __global__ void __launch_bounds__(512) rhs_quad_kernel(const QuadParams<T> prm, 
     kap[CF_C] = tau * tau / (4.0 * ep * mu * (1.0 + al));
     kap[CF_D] = tau / (2.0 * mu);
   }
+  T kapT[5];  // in the working precision, for the element products
+#pragma unroll
+  for (int k = 0; k < 5; ++k) kapT[k] = T(kap[k]);
   const bool src_here = prm.src_comp >= 0 && ein && ex == prm.src_e[0] && ey == prm.src_e[1] && ez == prm.src_e[2];
   double bg = 0.0;
   if (src_here) {
@@ -279,7 +283,7 @@ __global__ void __launch_bounds__(512) rhs_quad_kernel(const QuadParams<T> prm, 
           const T* Zm = loc(2, lz, tm.op[2]) + c2 * Q;
           const T* Ym = loc(1, ly, tm.op[1]);
           const T* Xm = loc(0, lx, tm.op[0]);
-          const T w = T((double)tm.sign * kap[tm.coef]);
+          const T w = T(tm.sign) * kapT[tm.coef];
           T t1[Q][Q];
 #pragma unroll
           for (int b = 0; b < Q; ++b)
@@ -327,7 +331,7 @@ __global__ void __launch_bounds__(512) rhs_quad_kernel(const QuadParams<T> prm, 
         const int X = i % HT, Y = (i / HT) % HT, Z = i / (HT * HT);
         const int zl = Z - c2;
         if (zl < 0 || zl >= TE) continue;
-        double sm = 0.0;
+        T sm = T(0);  // the (p+1)^2 contributions of this plane in T, the planes in FP64
 #pragma unroll
         for (int b = 0; b < Q; ++b) {
           const int yl = Y - b;
@@ -336,10 +340,10 @@ __global__ void __launch_bounds__(512) rhs_quad_kernel(const QuadParams<T> prm, 
           for (int a = 0; a < Q; ++a) {
             const int xl = X - a;
             if (xl < 0 || xl >= TE) continue;
-            sm += (double)s_con[(b * Q + a) * NE + (zl * TE + yl) * TE + xl];
+            sm += s_con[(b * Q + a) * NE + (zl * TE + yl) * TE + xl];
           }
         }
-        s_out[comp * HT3 + i] += sm;
+        s_out[comp * HT3 + i] += (double)sm;
       }
       __syncthreads();
     }
