@@ -86,12 +86,12 @@ typedef struct {
   int use_graph;        /* 1 (default): adi_step replays a captured CUDA graph of one step */
   int mixed_no_refine;  /* ADI_PREC_MIXED only: 1 skips the refinement (E = E*, for error studies) */
   int mixed_fp64_residual; /* ADI_PREC_MIXED only: 1 evaluates the residual in FP64 (default 0: float-float) */
-  int rhs_material;     /* ADI_RHS_ROW (default) or ADI_RHS_QUAD (not with ADI_PREC_MIXED) */
+  int rhs_material;     /* ADI_RHS_ROW (default) or ADI_RHS_QUAD (not with ADI_PREC_MIXED; p <= 3 in FP64) */
   int reserved[3];      /* must be 0 */
 } adi_options;
 
 /* Create a problem on the unit cube.
- *  nx, ny, nz >= 1 elements per axis; 1 <= p <= 3 (B-spline degree, C^{p-1});
+ *  nx, ny, nz >= 1 elements per axis; 1 <= p <= 4 (B-spline degree, C^{p-1});
  *  dt > 0 is the full time step tau (each half step advances tau/2);
  *  eps, mu, sigma: per-element relative permittivity, permeability and
  *  conductivity ([z][y][x], n_x n_y n_z doubles each); NULL means 1, 1, 0.

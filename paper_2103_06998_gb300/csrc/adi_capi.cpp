@@ -160,7 +160,7 @@ static adi_status create_impl(int nx, int ny, int nz, int p, double dt, const do
   if (!out) return fail(nullptr, ADI_EINVAL, "adi_create: out is NULL");
   *out = nullptr;
   if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, ADI_EINVAL, "adi_create: element counts must be >= 1");
-  if (p < 1 || p > adi::kMaxP) return fail(nullptr, ADI_EINVAL, "adi_create: p must be in 1..3");
+  if (p < 1 || p > adi::kMaxP) return fail(nullptr, ADI_EINVAL, "adi_create: p must be in 1..4");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(nullptr, ADI_EINVAL, "adi_create: dt must be finite and > 0");
   int prec = ADI_PREC_FP32, use_graph = 1, refine = 1, res64 = 0, quad = 0;
   if (opt) {
@@ -172,6 +172,8 @@ static adi_status create_impl(int nx, int ny, int nz, int p, double dt, const do
       return fail(nullptr, ADI_EINVAL, "adi_create: rhs_material must be ADI_RHS_ROW or ADI_RHS_QUAD");
     if (opt->rhs_material == ADI_RHS_QUAD && opt->precision == ADI_PREC_MIXED)
       return fail(nullptr, ADI_EINVAL, "adi_create: ADI_RHS_QUAD is not available with ADI_PREC_MIXED");
+    if (opt->rhs_material == ADI_RHS_QUAD && opt->precision == ADI_PREC_FP64 && p > 3)
+      return fail(nullptr, ADI_EINVAL, "adi_create: ADI_RHS_QUAD in FP64 needs p <= 3");
     if (opt->mixed_no_refine != 0 && opt->mixed_no_refine != 1)
       return fail(nullptr, ADI_EINVAL, "adi_create: mixed_no_refine must be 0 or 1");
     if (opt->mixed_fp64_residual != 0 && opt->mixed_fp64_residual != 1)

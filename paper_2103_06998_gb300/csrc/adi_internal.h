@@ -12,7 +12,7 @@
 
 namespace adi {
 
-constexpr int kMaxP = 3;
+constexpr int kMaxP = 4;
 constexpr int kMaxTerms = 12;
 constexpr int kMaxResidTerms = 18;  // E right-hand side (12) and T E* (6) of the mixed-mode residual
 

@@ -1728,13 +1728,27 @@ __global__ void __launch_bounds__(32) line_xw_kernel(const LineJobs<float> jobs,
     float win[W];
 #pragma unroll
     for (int d = 0; d < W; ++d) win[d] = (MODE == LM_DERIV && d >= P && d - P < N) ? row[d - P] : 0.f;
-    float4 cv = *reinterpret_cast<const float4*>(row);
+    // registers hold rows k0 .. k0 + 4 NV - 1: the block and, for DERIV, the
+    // window feed u[k + P + 1] of its last row (k0 + P + 4); one more block of 4
+    // is loaded ahead, so lpk >= 4 NC + 4 NV (the launcher leaves 12 of slack)
+    constexpr int NV = MODE == LM_DERIV ? (P + 8) / 4 : 1;
+    float4 buf[NV + 1];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) buf[v] = *reinterpret_cast<const float4*>(row + 4 * v);
     for (int b = 0; b < NC; ++b) {
       const int k0 = 4 * b;
-      // the next block is read before this block's results are stored
-      const float4 nv = *reinterpret_cast<const float4*>(row + k0 + 4);  // lpk >= 4 NC + 4
-      const float cur[8] = {cv.x, cv.y, cv.z, cv.w, nv.x, nv.y, nv.z, nv.w};  // DERIV: u[k0 .. k0+7]
-      cv = nv;
+      // the rows ahead are read before this block's results are stored
+      buf[NV] = *reinterpret_cast<const float4*>(row + k0 + 4 * NV);
+      float cur[4 * NV];  // DERIV: u[k0 .. k0 + 4 NV - 1]
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        cur[4 * v] = buf[v].x;
+        cur[4 * v + 1] = buf[v].y;
+        cur[4 * v + 2] = buf[v].z;
+        cur[4 * v + 3] = buf[v].w;
+      }
+#pragma unroll
+      for (int v = 0; v < NV; ++v) buf[v] = buf[v + 1];
       float out[4];
       if (k0 >= c0 && k0 + 3 <= c1) {  // constant block (warp-uniform)
 #pragma unroll
@@ -3002,7 +3016,9 @@ cudaError_t launch_line(Ctx& c, int dir, int mode, const LineJobs<T>& jobs, int 
   }
   // x lines on one warp per 32 lines: rows [line][k] of shared memory with a pitch lpk of a
   // multiple of 4 elements, lpk / 4 odd (conflict-free 16-byte lane accesses in FP32)
-  int lpk = ((lp.N + 3) & ~3) + 4;      // a line padded to 4 elements, plus 4 elements of slack
+  // a line padded to 4 elements, plus 12 elements of slack (the derivative sweep
+  // reads up to 4 (NV - 1) <= 8 rows beyond its block of 4, plus one block ahead)
+  int lpk = ((lp.N + 3) & ~3) + 12;
   if (((lpk >> 2) & 1) == 0) lpk += 4;
   const size_t smw = sizeof(T) * 32 * (size_t)lpk;
   // x stiffness lines with precomputed row factors (FP32 and FP64): plane plus a two-stage ring
@@ -3288,10 +3304,14 @@ cudaError_t launch_rhs_quad(Ctx& c, const T* const* fields, int nfields, T* cons
   prm.clock_t0 = c.d_clock_t0;
   prm.clock_step = c.d_clock_step;
   dim3 grid((c.n[0] + 7) / 8, (c.n[1] + 7) / 8, (c.n[2] + 7) / 8);
-  prof_begin(c, "rhs_quad", (double)c.Nc * sizeof(T) * (nfields + 3));
-  rhs_quad_kernel<T, P><<<grid, 512, QuadTile<T, P>::bytes(nfields), c.stream>>>(prm, nfields);
-  prof_end(c);
-  return cudaGetLastError();
+  if constexpr (sizeof(T) == 8 && P > 3) {  // the FP64 tiles of p >= 4 do not fit in shared memory
+    return cudaErrorInvalidValue;          // (adi_create rejects that combination)
+  } else {
+    prof_begin(c, "rhs_quad", (double)c.Nc * sizeof(T) * (nfields + 3));
+    rhs_quad_kernel<T, P><<<grid, 512, QuadTile<T, P>::bytes(nfields), c.stream>>>(prm, nfields);
+    prof_end(c);
+    return cudaGetLastError();
+  }
 }
 
 // E half step: the right-hand side, then the line solves (e_solve).
@@ -3498,7 +3518,8 @@ cudaError_t substep_t(Ctx& c, int which) {
   switch (c.p) {
     case 1: return substep_tp<T, 1>(c, which);
     case 2: return substep_tp<T, 2>(c, which);
-    default: return substep_tp<T, 3>(c, which);
+    case 3: return substep_tp<T, 3>(c, which);
+    default: return substep_tp<T, 4>(c, which);
   }
 }
 
@@ -3525,7 +3546,8 @@ cudaError_t prepare_tp(int optin) {
     if (e == cudaSuccess) e = opt_in(resid_kernel<P>, optin);
     if (e == cudaSuccess) e = opt_in(resid_ff_kernel<P>, optin);
   }
-  if (e == cudaSuccess) e = opt_in(rhs_quad_kernel<T, P>, optin);
+  if constexpr (!(sizeof(T) == 8 && P > 3))
+    if (e == cudaSuccess) e = opt_in(rhs_quad_kernel<T, P>, optin);
   if (e == cudaSuccess) e = opt_in(line_kernel<T, P, LM_MASS, true>, optin);
   if (e == cudaSuccess) e = opt_in(line_kernel<T, P, LM_STIFF, true>, optin);
   if (e == cudaSuccess) e = opt_in(line_kernel<T, P, LM_DERIV, true>, optin);
@@ -3542,7 +3564,8 @@ cudaError_t prepare_t(int p, int optin) {
   switch (p) {
     case 1: return prepare_tp<T, 1>(optin);
     case 2: return prepare_tp<T, 2>(optin);
-    default: return prepare_tp<T, 3>(optin);
+    case 3: return prepare_tp<T, 3>(optin);
+    default: return prepare_tp<T, 4>(optin);
   }
 }
 
@@ -3682,7 +3705,8 @@ cudaError_t norms_t(Ctx& c, double* d_acc) {
   switch (c.p) {
     case 1: return norms_tp<T, 1>(c, d_acc);
     case 2: return norms_tp<T, 2>(c, d_acc);
-    default: return norms_tp<T, 3>(c, d_acc);
+    case 3: return norms_tp<T, 3>(c, d_acc);
+    default: return norms_tp<T, 4>(c, d_acc);
   }
 }
 
@@ -3708,7 +3732,8 @@ cudaError_t pivots_t(Ctx& c) {
   switch (c.p) {
     case 1: return pivots_tp<T, 1>(c);
     case 2: return pivots_tp<T, 2>(c);
-    default: return pivots_tp<T, 3>(c);
+    case 3: return pivots_tp<T, 3>(c);
+    default: return pivots_tp<T, 4>(c);
   }
 }
 

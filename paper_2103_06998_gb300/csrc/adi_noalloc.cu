@@ -97,7 +97,7 @@ extern "C" adi_status adi_cfl_dt_noalloc(int nx, int ny, int nz, int p, const do
                                          void* cuda_stream, double* dt_out) {
   if (!dt_out || !d_eps || !d_mu) return adi::fail_global(ADI_EINVAL, "adi_cfl_dt_noalloc: NULL pointer");
   if (nx < 1 || ny < 1 || nz < 1) return adi::fail_global(ADI_EINVAL, "adi_cfl_dt_noalloc: element counts must be >= 1");
-  if (p < 1 || p > adi::kMaxP) return adi::fail_global(ADI_EINVAL, "adi_cfl_dt_noalloc: p must be in 1..3");
+  if (p < 1 || p > adi::kMaxP) return adi::fail_global(ADI_EINVAL, "adi_cfl_dt_noalloc: p must be in 1..4");
   // widened term by term: the int sum nx + ny + nz may wrap for huge sizes
   const long long need = kTablesOffset + ((long long)nx + ny + nz + 3LL * p) * (p + 1);
   if (need > kNoallocScratchDoubles)

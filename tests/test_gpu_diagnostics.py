@@ -19,7 +19,7 @@ def _adi():
 
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-6)])
-@pytest.mark.parametrize("n,p", [((11, 9, 13), 2), ((7, 10, 6), 3), ((12, 5, 8), 1), ((37, 35, 33), 2)])
+@pytest.mark.parametrize("n,p", [((11, 9, 13), 2), ((7, 10, 6), 3), ((12, 5, 8), 1), ((37, 35, 33), 2), ((8, 7, 9), 4)])
 def test_norms_match_oracle(n, p, prec, tol):
     adi = _adi()
     eps, mu, sigma, _ = inputs.head_map(n, 2103)

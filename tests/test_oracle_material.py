@@ -13,7 +13,7 @@ def test_uniform_material_gives_uniform_hat():
     np.testing.assert_allclose(material.row_hats(f, n, p), 7.25, rtol=1e-14)
 
 
-@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
 def test_hat_equals_3d_quadrature(p):
     # eps^_rst = int eps B_rst / int B_rst, by a full 3D Gauss sum
     n = (3, 4, 2)

@@ -18,7 +18,7 @@ def _greville(ne, p):
     return np.array([U[i + 1:i + p + 1].mean() for i in range(ne + p)])
 
 
-@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
 def test_constant_and_linear_fields(p):
     n = (4, 5, 3)
     shp = (n[2] + p, n[1] + p, n[0] + p)
@@ -41,7 +41,7 @@ def test_constant_and_linear_fields(p):
     np.testing.assert_allclose([l2, h1, hc], [np.sqrt(1 / 3), np.sqrt(4 / 3), np.sqrt(4 / 3)], rtol=1e-13)
 
 
-@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
 def test_norms_equal_matrix_quadratic_forms(p):
     n = (3, 4, 5)
     rng = np.random.default_rng(p)
