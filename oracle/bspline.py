@@ -9,8 +9,10 @@ the derivative on the test function.  Rows are test functions, columns trial
 functions.  The paper states both A and B with the derivative on the trial
 function; the integrands of eq. (dupa1abcd) put the derivative of B on the test
 function, which is the reading used here, so B = A^T.  The basis is the open
-uniform knot vector of degree p with C^{p-1} continuity on (0, 1) ("quadratic
-C^1" in the head experiment; linear example in the Appendix).
+knot vector of degree p with C^{p-1} continuity on (0, 1) ("quadratic C^1" in
+the head experiment; linear example in the Appendix) on uniform elements, or
+on the element boundaries given by ``breaks`` (the formulation admits any
+knots: the matrices keep bandwidth p).
 
 Pins (tests/test_oracle_bspline.py): closed-form interior stencils of the
 uniform p = 2 matrices, partition of unity, S.1 = 0, A + A^T = e_N e_N^T -
@@ -21,9 +23,27 @@ eigenvalue of M^{-1} S.
 import numpy as np
 
 
-def knot_vector(n, p):
-    """Open uniform knot vector on [0, 1] with ``n`` elements, degree ``p``."""
-    return np.concatenate([np.zeros(p), np.linspace(0.0, 1.0, n + 1), np.ones(p)])
+def _breaks(n, breaks):
+    """Element boundaries 0 = x_0 < x_1 < ... < x_n = 1 (uniform if None)."""
+    if breaks is None:
+        return np.linspace(0.0, 1.0, n + 1)
+    b = np.asarray(breaks, dtype=np.float64)
+    assert b.shape == (n + 1,) and b[0] == 0.0 and b[-1] == 1.0 and np.all(np.diff(b) > 0)
+    return b
+
+
+def knot_vector(n, p, breaks=None):
+    """Open knot vector on [0, 1] with ``n`` elements, degree ``p``: the element
+    boundaries (uniform unless ``breaks`` is given) with the end knots repeated
+    p + 1 times."""
+    return np.concatenate([np.zeros(p), _breaks(n, breaks), np.ones(p)])
+
+
+def element_of(n, x0, breaks=None):
+    """The element (knot span 0..n-1) that holds x0; a point on an element
+    boundary belongs to the element on its right, x0 = 1 to the last one."""
+    b = _breaks(n, breaks)
+    return int(min(max(np.searchsorted(b, x0, side="right") - 1, 0), n - 1))
 
 
 def n_basis(n, p):
@@ -31,7 +51,7 @@ def n_basis(n, p):
     return n + p
 
 
-def eval_basis(n, p, x, elem):
+def eval_basis(n, p, x, elem, breaks=None):
     """Values and first derivatives of all N B-splines at points ``x``.
 
     ``elem[q]`` is the element (knot span 0..n-1) that contains ``x[q]``; it
@@ -41,7 +61,7 @@ def eval_basis(n, p, x, elem):
     p/(U_{i+p}-U_i) N_{i,p-1} - p/(U_{i+p+1}-U_{i+1}) N_{i+1,p-1}.
     Returns (vals, ders), each of shape (len(x), N).
     """
-    U = knot_vector(n, p)
+    U = knot_vector(n, p, breaks)
     x = np.asarray(x, dtype=np.float64)
     elem = np.asarray(elem)
     nq = x.shape[0]
@@ -76,20 +96,21 @@ def eval_basis(n, p, x, elem):
     return vals, ders
 
 
-def gauss_points(n, q):
+def gauss_points(n, q, breaks=None):
     """Gauss-Legendre points and weights, ``q`` per element, on [0, 1].
 
     Returns (x, w, elem) for all n*q points.
     """
     g, gw = np.polynomial.legendre.leggauss(q)
-    h = 1.0 / n
-    x = np.concatenate([(e + 0.5) * h + 0.5 * h * g for e in range(n)])
-    w = np.concatenate([0.5 * h * gw for _ in range(n)])
+    b = _breaks(n, breaks)
+    h = np.diff(b)
+    x = np.concatenate([0.5 * (b[e] + b[e + 1]) + 0.5 * h[e] * g for e in range(n)])
+    w = np.concatenate([0.5 * h[e] * gw for e in range(n)])
     elem = np.repeat(np.arange(n), q)
     return x, w, elem
 
 
-def matrices_1d(n, p, q=None):
+def matrices_1d(n, p, q=None, breaks=None):
     """The 1D matrices M, S, A, B (dense N x N, FP64).
 
     M[l, i] = int B_i B_l, S[l, i] = int B_i' B_l', A[l, i] = int B_i' B_l,
@@ -99,8 +120,8 @@ def matrices_1d(n, p, q=None):
     """
     if q is None:
         q = p + 1
-    x, w, elem = gauss_points(n, q)
-    v, d = eval_basis(n, p, x, elem)
+    x, w, elem = gauss_points(n, q, breaks)
+    v, d = eval_basis(n, p, x, elem, breaks)
     M = (v * w[:, None]).T @ v
     S = (d * w[:, None]).T @ d
     A = (v * w[:, None]).T @ d  # A[l, i] = sum_q w B_l B_i'
@@ -108,10 +129,10 @@ def matrices_1d(n, p, q=None):
     return M, S, A, B
 
 
-def element_integrals(n, p):
+def element_integrals(n, p, breaks=None):
     """G[r, e] = integral over element e of B_r (used by the material hats)."""
-    x, w, elem = gauss_points(n, p + 1)
-    v, _ = eval_basis(n, p, x, elem)
+    x, w, elem = gauss_points(n, p + 1, breaks)
+    v, _ = eval_basis(n, p, x, elem, breaks)
     G = np.zeros((v.shape[1], n))
     for e in range(n):
         sel = elem == e
@@ -119,8 +140,8 @@ def element_integrals(n, p):
     return G
 
 
-def point_values(n, p, x0):
+def point_values(n, p, x0, breaks=None):
     """Values of all N B-splines at one point x0 in [0, 1]."""
-    e = min(int(np.floor(x0 * n)), n - 1)
-    v, _ = eval_basis(n, p, np.array([x0]), np.array([e]))
+    e = element_of(n, x0, breaks)
+    v, _ = eval_basis(n, p, np.array([x0]), np.array([e]), breaks)
     return v[0]

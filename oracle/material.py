@@ -46,12 +46,14 @@ from . import bspline
 from .banded import apply_1d
 
 
-def row_hats(field, n, p):
-    """Support-weighted mean of per-element ``field`` (nz, ny, nx) per row."""
+def row_hats(field, n, p, breaks=None):
+    """Support-weighted mean of per-element ``field`` (nz, ny, nx) per row;
+    breaks: per-axis element boundaries (x, y, z) or None for uniform."""
     nx, ny, nz = n
-    Gx = bspline.element_integrals(nx, p)
-    Gy = bspline.element_integrals(ny, p)
-    Gz = bspline.element_integrals(nz, p)
+    bx, by, bz = breaks if breaks is not None else (None, None, None)
+    Gx = bspline.element_integrals(nx, p, bx)
+    Gy = bspline.element_integrals(ny, p, by)
+    Gz = bspline.element_integrals(nz, p, bz)
     num = apply_1d(Gx, apply_1d(Gy, apply_1d(Gz, field, "z"), "y"), "x")
     one = np.ones_like(field)
     den = apply_1d(Gx, apply_1d(Gy, apply_1d(Gz, one, "z"), "y"), "x")
@@ -68,15 +70,16 @@ def coefficients(eps_hat, mu_hat, sigma_hat, tau):
     return a, b, c, d
 
 
-def lambda_max(n, p):
+def lambda_max(n, p, breaks=None):
     """Largest eigenvalue of M_D^{-1} S_D (Dirichlet-reduced) on one axis."""
-    M, S, _, _ = bspline.matrices_1d(n, p)
+    M, S, _, _ = bspline.matrices_1d(n, p, breaks=breaks)
     w = scipy.linalg.eigh(S[1:-1, 1:-1], M[1:-1, 1:-1], eigvals_only=True)
     return float(w.max())
 
 
-def cfl_dt(n, p, eps_hat, mu_hat):
+def cfl_dt(n, p, eps_hat, mu_hat, breaks=None):
     nx, ny, nz = n
-    lam = lambda_max(nx, p) + lambda_max(ny, p) + lambda_max(nz, p)
+    bx, by, bz = breaks if breaks is not None else (None, None, None)
+    lam = lambda_max(nx, p, bx) + lambda_max(ny, p, by) + lambda_max(nz, p, bz)
     cmax = 1.0 / np.sqrt(np.min(eps_hat * mu_hat))
     return 2.0 / (cmax * np.sqrt(lam))

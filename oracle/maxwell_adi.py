@@ -66,6 +66,7 @@ class Problem:
     source: dict = None     # point source (see set_source)
     rhs_material: str = "row"   # "row" or "quad" (see the module docstring)
     elem: dict = None       # "quad": per-element coefficients a, b, c, d, shape (nz, ny, nx)
+    breaks: tuple = None    # per-axis element boundaries (x, y, z), None: uniform elements
 
     @property
     def shape(self):
@@ -74,25 +75,29 @@ class Problem:
         return (nz + p, ny + p, nx + p)
 
 
-def make_problem(n, p, tau, eps=None, mu=None, sigma=None, rhs_material="row"):
+def make_problem(n, p, tau, eps=None, mu=None, sigma=None, rhs_material="row", breaks=None):
     """Build the 1D matrices and the per-row coefficients.
 
     eps, mu, sigma: per-element arrays (nz, ny, nx) or None for 1, 1, 0.
     rhs_material: "row" (the paper's row scaling) or "quad" (per-element
     coefficients inside the right-hand side integrals).
+    breaks: per-axis element boundaries (x, y, z), each n_d + 1 increasing values
+    from 0 to 1, or None for uniform elements.
     """
     nx, ny, nz = n
     shp_e = (nz, ny, nx)
     eps = np.ones(shp_e) if eps is None else np.asarray(eps, dtype=np.float64)
     mu = np.ones(shp_e) if mu is None else np.asarray(mu, dtype=np.float64)
     sigma = np.zeros(shp_e) if sigma is None else np.asarray(sigma, dtype=np.float64)
-    eh = material.row_hats(eps, n, p)
-    mh = material.row_hats(mu, n, p)
-    sh = material.row_hats(sigma, n, p)
+    br = tuple(breaks) if breaks is not None else (None, None, None)
+    eh = material.row_hats(eps, n, p, br)
+    mh = material.row_hats(mu, n, p, br)
+    sh = material.row_hats(sigma, n, p, br)
     a, b, c, d = material.coefficients(eh, mh, sh, tau)
-    mats = {"x": bspline.matrices_1d(nx, p), "y": bspline.matrices_1d(ny, p),
-            "z": bspline.matrices_1d(nz, p)}
-    prob = Problem(n=tuple(n), p=p, tau=tau, a=a, b=b, c=c, d=d, mats=mats, rhs_material=rhs_material)
+    mats = {"x": bspline.matrices_1d(nx, p, breaks=br[0]), "y": bspline.matrices_1d(ny, p, breaks=br[1]),
+            "z": bspline.matrices_1d(nz, p, breaks=br[2])}
+    prob = Problem(n=tuple(n), p=p, tau=tau, a=a, b=b, c=c, d=d, mats=mats, rhs_material=rhs_material,
+                   breaks=br)
     if rhs_material == "quad":
         ae, be, ce, de = material.coefficients(eps, mu, sigma, tau)
         prob.elem = dict(a=ae, b=be, c=ce, d=de)
@@ -108,9 +113,10 @@ def set_source(prob, x0, comp, amp, f0, t0, s):
     g(t) = sin(2 pi f0 (t - t0)) exp(-((t - t0) / s)^2).
     """
     nx, ny, nz = prob.n
-    wx = bspline.point_values(nx, prob.p, x0[0])
-    wy = bspline.point_values(ny, prob.p, x0[1])
-    wz = bspline.point_values(nz, prob.p, x0[2])
+    br = prob.breaks if prob.breaks is not None else (None, None, None)
+    wx = bspline.point_values(nx, prob.p, x0[0], br[0])
+    wy = bspline.point_values(ny, prob.p, x0[1], br[1])
+    wz = bspline.point_values(nz, prob.p, x0[2], br[2])
     prob.source = dict(w=np.einsum("k,j,i->kji", wz, wy, wx), comp=comp, amp=amp, x0=tuple(x0),
                        f0=f0, t0=t0, s=s)
 
@@ -133,9 +139,10 @@ def _quad_axes(prob):
     integrands), weights, element of each point, basis values and derivatives."""
     if getattr(prob, "_qa", None) is None:
         out = []
-        for ne in prob.n:
-            x, w, e = bspline.gauss_points(ne, prob.p + 1)
-            v, d = bspline.eval_basis(ne, prob.p, x, e)
+        br = prob.breaks if prob.breaks is not None else (None, None, None)
+        for ne, b in zip(prob.n, br):
+            x, w, e = bspline.gauss_points(ne, prob.p + 1, b)
+            v, d = bspline.eval_basis(ne, prob.p, x, e, b)
             out.append((w, e, v, d))
         prob._qa = out
     return prob._qa
@@ -171,7 +178,8 @@ def _source_b(prob):
     if prob.rhs_material != "quad":
         return prob.b
     x0 = prob.source["x0"]
-    e = [min(int(np.floor(x0[a] * prob.n[a])), prob.n[a] - 1) for a in range(3)]
+    br = prob.breaks if prob.breaks is not None else (None, None, None)
+    e = [bspline.element_of(prob.n[a], x0[a], br[a]) for a in range(3)]
     return prob.elem["b"][e[2], e[1], e[0]]
 
 

@@ -1,7 +1,8 @@
 """Dense brute-force assembly of one ADI sub-step on tiny meshes (test helper).
 
-Independent of the oracle's code: the basis comes from scipy.interpolate.BSpline,
-every integral is a sum over a full 3D Gauss grid (no Kronecker factorisation),
+Independent of the oracle's code: the basis comes from scipy.interpolate.BSpline
+(uniform elements, or the element boundaries ``breaks`` per axis), every
+integral is a sum over a full 3D Gauss grid (no Kronecker factorisation),
 and the rows are written straight from the weak forms (weak1)-(weak4) of the
 paper with per-row coefficients a, b, c, d:
 
@@ -20,8 +21,12 @@ import numpy as np
 from scipy.interpolate import BSpline
 
 
-def _basis_1d(n, p, x):
-    t = np.concatenate([np.zeros(p), np.linspace(0, 1, n + 1), np.ones(p)])
+def _edges(n, breaks):
+    return np.linspace(0, 1, n + 1) if breaks is None else np.asarray(breaks, dtype=np.float64)
+
+
+def _basis_1d(n, p, x, breaks=None):
+    t = np.concatenate([np.zeros(p), _edges(n, breaks), np.ones(p)])
     N = n + p
     v = np.zeros((len(x), N))
     d = np.zeros((len(x), N))
@@ -34,26 +39,28 @@ def _basis_1d(n, p, x):
     return v, d
 
 
-def _gauss(n, q):
+def _gauss(n, q, breaks=None):
     g, w = np.polynomial.legendre.leggauss(q)
-    h = 1.0 / n
-    x = np.concatenate([(e + 0.5) * h + 0.5 * h * g for e in range(n)])
-    ww = np.concatenate([0.5 * h * w] * n)
+    b = _edges(n, breaks)
+    x = np.concatenate([0.5 * (b[e] + b[e + 1]) + 0.5 * (b[e + 1] - b[e]) * g for e in range(n)])
+    ww = np.concatenate([0.5 * (b[e + 1] - b[e]) * w for e in range(n)])
     return x, ww
 
 
 class Dense3D:
     """Dense 3D operators on the tensor B-spline space of (nx, ny, nz), p."""
 
-    def __init__(self, n, p):
+    def __init__(self, n, p, breaks=None):
         self.n, self.p = n, p
+        self.breaks = tuple(breaks) if breaks is not None else (None, None, None)
+        bx, by, bz = self.breaks
         nx, ny, nz = n
         self.N = (nx + p, ny + p, nz + p)
         q = p + 2
-        (x, wx), (y, wy), (z, wz) = _gauss(nx, q), _gauss(ny, q), _gauss(nz, q)
-        vx, dx = _basis_1d(nx, p, x)
-        vy, dy = _basis_1d(ny, p, y)
-        vz, dz = _basis_1d(nz, p, z)
+        (x, wx), (y, wy), (z, wz) = _gauss(nx, q, bx), _gauss(ny, q, by), _gauss(nz, q, bz)
+        vx, dx = _basis_1d(nx, p, x, bx)
+        vy, dy = _basis_1d(ny, p, y, by)
+        vz, dz = _basis_1d(nz, p, z, bz)
         # index order (k, j, i) with i (x) fastest, points (qz, qy, qx)
         self.W = np.kron(np.kron(wz, wy), wx)
         self.phi = np.kron(np.kron(vz, vy), vx)
@@ -99,7 +106,7 @@ class Dense3D:
         """B_rst(x0) for all rst (flattened)."""
         out = []
         for d in range(3):
-            v, _ = _basis_1d(self.n[d], self.p, np.array([x0[d]]))
+            v, _ = _basis_1d(self.n[d], self.p, np.array([x0[d]]), self.breaks[d])
             out.append(v[0])
         return np.kron(np.kron(out[2], out[1]), out[0])
 
