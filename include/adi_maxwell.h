@@ -107,6 +107,22 @@ adi_status adi_create(int nx, int ny, int nz, int p, double dt,
                       const double* eps, const double* mu, const double* sigma,
                       const adi_options* opt, adi_handle* out);
 
+/* adi_create on non-uniform elements (section "Variational formulation": the
+ * 1D matrices are defined for any open knot vector; bandwidth stays 2p + 1).
+ *  breaks_x, breaks_y, breaks_z (host, caller-owned, copied): the element
+ *  boundaries of each axis, n_d + 1 doubles, 0 = x_0 < x_1 < ... < x_{n_d} = 1
+ *  (NULL: uniform elements on that axis); the knot vector repeats the end
+ *  points p + 1 times.  Material, source position and plane coordinates refer
+ *  to these elements (a point on an element boundary belongs to the element on
+ *  its right).  Kernels use the constant interior stencil only on rows whose
+ *  band rows agree with it (a uniform core), the band tables elsewhere.
+ * Errors as adi_create; ADI_EINVAL also for boundaries that are not strictly
+ * increasing from 0 to 1.  The batched instances, the corrector and
+ * adi_cfl_dt_noalloc use uniform elements. */
+adi_status adi_create_knots(int nx, int ny, int nz, int p, double dt, const double* breaks_x,
+                            const double* breaks_y, const double* breaks_z, const double* eps, const double* mu,
+                            const double* sigma, const adi_options* opt, adi_handle* out);
+
 /* Build the 1D matrices M, S, A (B = A^T) of every axis by Gauss-Legendre
  * quadrature in FP64 (definitions after eq. discrete4), factor the mass
  * matrices (full and Dirichlet-reduced) without pivoting, and upload the

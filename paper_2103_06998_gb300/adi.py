@@ -18,7 +18,7 @@ PREC_FP64, PREC_FP32, PREC_MIXED = 0, 1, 2
 _PREC = {"fp64": PREC_FP64, "fp32": PREC_FP32, "mixed": PREC_MIXED}
 
 # every symbol declared in include/adi_maxwell.h
-EXPORTS = ("adi_create", "adi_factor", "adi_set_dt", "adi_set_stream", "adi_set_fields",
+EXPORTS = ("adi_create", "adi_create_knots", "adi_factor", "adi_set_dt", "adi_set_stream", "adi_set_fields",
            "adi_set_source", "adi_step", "adi_substep", "adi_fields", "adi_fields_device",
            "adi_cfl_dt", "adi_cfl_dt_noalloc", "adi_sync", "adi_wait_selftest", "adi_norms", "adi_plane", "adi_set_profiling", "adi_kernel_stats", "adi_dims",
            "adi_destroy", "adi_last_error", "adi_status_string", "adi_set_line_tile",
@@ -63,6 +63,7 @@ def load_library(path=LIB_PATH):
     P = ctypes.POINTER
     sig = {
         "adi_create": (I, [I, I, I, I, D, P(D), P(D), P(D), P(AdiOptions), P(H)]),
+        "adi_create_knots": (I, [I, I, I, I, D, P(D), P(D), P(D), P(D), P(D), P(D), P(AdiOptions), P(H)]),
         "adi_factor": (I, [H]),
         "adi_set_dt": (I, [H, D]),
         "adi_set_stream": (I, [H, ctypes.c_void_p]),
@@ -132,7 +133,7 @@ class Solver:
     """One ADI Maxwell problem on the GPU (owns an adi_handle)."""
 
     def __init__(self, n, p, dt, eps=None, mu=None, sigma=None, precision="fp32", use_graph=True, _handle=None,
-                 refine=True, residual="ff", rhs_material="row"):
+                 refine=True, residual="ff", rhs_material="row", breaks=None):
         lib = load_library()
         self._lib = lib
         if _handle is not None:  # an instance owned by a Batch
@@ -164,8 +165,13 @@ class Solver:
             return _dptr(a)
 
         h = ctypes.c_void_p()
-        st = lib.adi_create(self.n[0], self.n[1], self.n[2], self.p, float(dt), arr(eps), arr(mu), arr(sigma),
-                            ctypes.byref(opt), ctypes.byref(h))
+        if breaks is None:
+            st = lib.adi_create(self.n[0], self.n[1], self.n[2], self.p, float(dt), arr(eps), arr(mu), arr(sigma),
+                                ctypes.byref(opt), ctypes.byref(h))
+        else:
+            bx, by, bz = (None if b is None else arr(b) for b in breaks)
+            st = lib.adi_create_knots(self.n[0], self.n[1], self.n[2], self.p, float(dt), bx, by, bz, arr(eps),
+                                      arr(mu), arr(sigma), ctypes.byref(opt), ctypes.byref(h))
         if st != ADI_OK:
             raise AdiError(st, lib.adi_last_error(None).decode())
         self.h = h

@@ -141,25 +141,44 @@ const char* adi_last_error(adi_handle h) {
   return h->err.c_str();
 }
 
-static adi_status create_impl(int nx, int ny, int nz, int p, double dt, const double* eps, const double* mu,
-                              const double* sigma, const adi_options* opt, adi_handle* out);
+static adi_status create_impl(int nx, int ny, int nz, int p, double dt, const double* const* breaks,
+                              const double* eps, const double* mu, const double* sigma, const adi_options* opt,
+                              adi_handle* out);
 
-adi_status adi_create(int nx, int ny, int nz, int p, double dt, const double* eps, const double* mu,
-                      const double* sigma, const adi_options* opt, adi_handle* out) {
+adi_status adi_create_knots(int nx, int ny, int nz, int p, double dt, const double* breaks_x,
+                            const double* breaks_y, const double* breaks_z, const double* eps, const double* mu,
+                            const double* sigma, const adi_options* opt, adi_handle* out) {
   // no exception crosses the C-ABI: a failed host allocation is ADI_ENOMEM
+  const double* br[3] = {breaks_x, breaks_y, breaks_z};
   try {
-    return create_impl(nx, ny, nz, p, dt, eps, mu, sigma, opt, out);
+    return create_impl(nx, ny, nz, p, dt, br, eps, mu, sigma, opt, out);
   } catch (const std::bad_alloc&) {
     if (out) *out = nullptr;
     return fail(nullptr, ADI_ENOMEM, "adi_create: host allocation failed");
   }
 }
 
-static adi_status create_impl(int nx, int ny, int nz, int p, double dt, const double* eps, const double* mu,
-                              const double* sigma, const adi_options* opt, adi_handle* out) {
+adi_status adi_create(int nx, int ny, int nz, int p, double dt, const double* eps, const double* mu,
+                      const double* sigma, const adi_options* opt, adi_handle* out) {
+  return adi_create_knots(nx, ny, nz, p, dt, nullptr, nullptr, nullptr, eps, mu, sigma, opt, out);
+}
+
+static adi_status create_impl(int nx, int ny, int nz, int p, double dt, const double* const* breaks,
+                              const double* eps, const double* mu, const double* sigma, const adi_options* opt,
+                              adi_handle* out) {
   if (!out) return fail(nullptr, ADI_EINVAL, "adi_create: out is NULL");
   *out = nullptr;
   if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, ADI_EINVAL, "adi_create: element counts must be >= 1");
+  const int ns[3] = {nx, ny, nz};
+  for (int d = 0; d < 3; ++d) {
+    const double* b = breaks[d];
+    if (!b) continue;
+    bool ok = b[0] == 0.0 && b[ns[d]] == 1.0;
+    for (int i = 0; i < ns[d] && ok; ++i) ok = std::isfinite(b[i + 1]) && b[i + 1] > b[i];
+    if (!ok)
+      return fail(nullptr, ADI_EINVAL,
+                  "adi_create_knots: element boundaries must increase strictly from 0 to 1 (n_d + 1 values)");
+  }
   if (p < 1 || p > adi::kMaxP) return fail(nullptr, ADI_EINVAL, "adi_create: p must be in 1..4");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(nullptr, ADI_EINVAL, "adi_create: dt must be finite and > 0");
   int prec = ADI_PREC_FP32, use_graph = 1, refine = 1, res64 = 0, quad = 0;
@@ -280,7 +299,7 @@ static adi_status create_impl(int nx, int ny, int nz, int p, double dt, const do
         break;
       }
   c->d_uniform = dt / (2.0 * c->mu_value);
-  for (int d = 0; d < 3; ++d) adi::build_axis(c->n[d], p, c->axes[d]);
+  for (int d = 0; d < 3; ++d) adi::build_axis(c->n[d], p, c->axes[d], breaks[d]);
   e = adi::compute_coefficients(*c);
   if (e == cudaSuccess) {
     for (int i = 0; i < 6 && e == cudaSuccess; ++i) {
@@ -381,7 +400,7 @@ adi_status adi_set_source(adi_handle h, double x0, double y0, double z0, int com
     return fail(h, ADI_EINVAL, "adi_set_source: amp, f0, t0 must be finite and s > 0");
   for (int d = 0; d < 3; ++d) {
     double v[adi::kMaxP + 1] = {};
-    h->src_i0[d] = adi::point_basis(h->n[d], h->p, xs[d], v);
+    h->src_i0[d] = adi::point_basis(h->axes[d], xs[d], v);
     for (int q = 0; q <= adi::kMaxP; ++q) h->src_w[d][q] = q <= h->p ? v[q] : 0.0;
   }
   h->src_comp = comp;
@@ -545,7 +564,7 @@ adi_status adi_plane(adi_handle h, int comp, int axis, double pos, int nu, int n
   std::vector<double> tab((size_t)ntab, 0.0);
   auto put = [&](long long slot, int d, double x) {
     double v[adi::kMaxP + 1] = {};
-    const int e = adi::point_basis(h->n[d], h->p, x, v);
+    const int e = adi::point_basis(h->axes[d], x, v);
     tab[(size_t)(slot * rec)] = (double)e;
     for (int q = 0; q <= h->p; ++q) tab[(size_t)(slot * rec + 1 + q)] = v[q];
   };

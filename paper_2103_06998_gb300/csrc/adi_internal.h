@@ -19,8 +19,12 @@ constexpr int kMaxResidTerms = 18;  // E right-hand side (12) and T E* (6) of th
 // ---------------------------------------------------------------- host setup
 struct Axis1D {
   int n = 0, p = 0, N = 0;
+  std::vector<double> breaks;      // element boundaries x_0 = 0 < ... < x_n = 1 (empty: uniform)
   std::vector<double> M, S, A, B;  // bands, row k: [k*(2p+1) + d] = X[k][k+d-p]
   std::vector<double> G;           // G[r*(p+1) + a] = int over element r-p+a of B_r
+  // rows inner_lo .. inner_hi (inside 2p .. N-1-2p) have the band rows of the middle
+  // row (the interior stencil; all of 2p .. N-1-2p for uniform elements)
+  int inner_lo = 1, inner_hi = 0;
 };
 struct LuConst {  // rows lo..hi of a mass LU share the factors v (in the working precision)
   int lo = 1, hi = 0;
@@ -30,11 +34,15 @@ struct BandLU {
   int N = 0, p = 0, lo = 0, hi = 0;
   std::vector<double> L, inv_d, U;  // L[k*p+q-1], U[k*p+q-1] for q = 1..p
 };
-void build_axis(int n, int p, Axis1D& ax);
+// breaks: n + 1 element boundaries from 0 to 1, or NULL for uniform elements
+void build_axis(int n, int p, Axis1D& ax, const double* breaks = nullptr);
 void band_lu(const std::vector<double>& base, const std::vector<double>* stiff, int N, int p,
              int lo, int hi, BandLU& out);
 double lambda_max(const Axis1D& ax);
 int point_basis(int n, int p, double x0, double* vals);
+// the element of ax that holds x0 (a boundary point belongs to the element on its
+// right, x0 = 1 to the last) and the p + 1 B-splines nonzero there, at x0
+int point_basis(const Axis1D& ax, double x0, double* vals);
 // per-element blocks of M, S, A, B: loc[((e*4 + op)*(p+1) + test)*(p+1) + trial]
 void element_matrices(const Axis1D& ax, std::vector<double>& loc);
 

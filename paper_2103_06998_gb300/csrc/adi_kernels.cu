@@ -2715,8 +2715,8 @@ AxisDev<T> axis_dev(const Ctx& c, int d) {
   a.N = c.N[d];
   const Axis1D& h = c.axes[d];
   const int p = h.p, W = 2 * p + 1;
-  a.inner_lo = 2 * p;
-  a.inner_hi = h.N - 1 - 2 * p;
+  a.inner_lo = h.inner_lo;  // the rows with the interior stencil (detected by build_axis)
+  a.inner_hi = h.inner_hi;
   for (int o = 0; o < 4; ++o)
     for (int q = 0; q < 2 * kMaxP + 1; ++q) a.inner[o][q] = T(0);
   if (a.inner_lo <= a.inner_hi) {
@@ -2947,8 +2947,8 @@ template <typename T>
 Stencils<T> stencils_of(const Axis1D& ax) {
   Stencils<T> s{};
   const int p = ax.p, W = 2 * p + 1;
-  s.lo = 2 * p;
-  s.hi = ax.N - 1 - 2 * p;
+  s.lo = ax.inner_lo;  // the rows with the interior stencil (detected by build_axis)
+  s.hi = ax.inner_hi;
   if (s.lo <= s.hi) {
     const std::vector<double>* src[3] = {&ax.M, &ax.A, &ax.B};
     for (int o = 0; o < 3; ++o)

@@ -12,6 +12,7 @@
 // (column k - q), 1/U[k][k] and the normalised upper entries U[k][k+q]/U[k][k].
 #include "adi_internal.h"
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -97,34 +98,50 @@ void local_basis(const std::vector<double>& U, int p, int e, double t, double* v
   }
 }
 
-std::vector<double> knots(int n, int p) {
+std::vector<double> knots(int n, int p, const std::vector<double>& breaks = {}) {
   std::vector<double> U;
   for (int i = 0; i < p; ++i) U.push_back(0.0);
-  for (int i = 0; i <= n; ++i) U.push_back(double(i) / n);
+  for (int i = 0; i <= n; ++i) U.push_back(breaks.empty() ? double(i) / n : breaks[i]);
   for (int i = 0; i < p; ++i) U.push_back(1.0);
   return U;
 }
 
+// Gauss point q (reference node gx, weight gw) of element e: position and weight
+inline void elem_point(const Axis1D& ax, int e, double gx, double gw, double& t, double& w) {
+  if (ax.breaks.empty()) {
+    const double h = 1.0 / ax.n;
+    t = (e + 0.5) * h + 0.5 * h * gx;
+    w = 0.5 * h * gw;
+  } else {
+    const double a = ax.breaks[e], b = ax.breaks[e + 1];
+    t = 0.5 * (a + b) + 0.5 * (b - a) * gx;
+    w = 0.5 * (b - a) * gw;
+  }
+}
+
 }  // namespace
 
-void build_axis(int n, int p, Axis1D& ax) {
+void find_interior(Axis1D& ax);
+
+void build_axis(int n, int p, Axis1D& ax, const double* breaks) {
   const int N = n + p, W = 2 * p + 1;
   ax.n = n;
   ax.p = p;
   ax.N = N;
+  ax.breaks.clear();
+  if (breaks) ax.breaks.assign(breaks, breaks + n + 1);
   ax.M.assign(size_t(N) * W, 0.0);
   ax.S.assign(size_t(N) * W, 0.0);
   ax.A.assign(size_t(N) * W, 0.0);
   ax.B.assign(size_t(N) * W, 0.0);
   ax.G.assign(size_t(N) * (p + 1), 0.0);
-  std::vector<double> U = knots(n, p), gx, gw;
+  std::vector<double> U = knots(n, p, ax.breaks), gx, gw;
   gauss_legendre(p + 1, gx, gw);
   std::vector<double> v(p + 1), d(p + 1);
-  const double h = 1.0 / n;
   for (int e = 0; e < n; ++e) {
     for (int q = 0; q <= p; ++q) {
-      double t = (e + 0.5) * h + 0.5 * h * gx[q];
-      double w = 0.5 * h * gw[q];
+      double t, w;
+      elem_point(ax, e, gx[q], gw[q], t, w);
       local_basis(U, p, e, t, v.data(), d.data());
       for (int a = 0; a <= p; ++a) {
         int l = e + a;  // test
@@ -140,6 +157,35 @@ void build_axis(int n, int p, Axis1D& ax) {
       }
     }
   }
+  find_interior(ax);
+}
+
+// Interior rows of an axis: the range around the middle row, inside
+// 2p .. N-1-2p (where no band reaches a boundary row), whose band rows of M, S,
+// A, B equal the middle row's to rounding; kernels use the constant stencil
+// there and the tables elsewhere.  Uniform elements: all of 2p .. N-1-2p.
+void find_interior(Axis1D& ax) {
+  const int p = ax.p, N = ax.N, W = 2 * p + 1;
+  ax.inner_lo = 1;
+  ax.inner_hi = 0;
+  const int lo = 2 * p, hi = N - 1 - 2 * p;
+  if (lo > hi) return;
+  const int mid = (lo + hi) / 2;
+  const std::vector<double>* src[4] = {&ax.M, &ax.S, &ax.A, &ax.B};
+  double scale = 0.0;
+  for (int o = 0; o < 4; ++o)
+    for (int q = 0; q < W; ++q) scale = std::fmax(scale, std::fabs((*src[o])[(size_t)mid * W + q]));
+  auto same = [&](int r) {
+    for (int o = 0; o < 4; ++o)
+      for (int q = 0; q < W; ++q)
+        if (std::fabs((*src[o])[(size_t)r * W + q] - (*src[o])[(size_t)mid * W + q]) > 1e-12 * scale) return false;
+    return true;
+  };
+  int a = mid, b = mid;
+  while (a - 1 >= lo && same(a - 1)) --a;
+  while (b + 1 <= hi && same(b + 1)) ++b;
+  ax.inner_lo = a;
+  ax.inner_hi = b;
 }
 
 // The same integrals restricted to one element: loc[((e * 4 + op) * (p+1) + a) *
@@ -150,15 +196,14 @@ void build_axis(int n, int p, Axis1D& ax) {
 void element_matrices(const Axis1D& ax, std::vector<double>& loc) {
   const int n = ax.n, p = ax.p, Q = p + 1;
   loc.assign(size_t(n) * 4 * Q * Q, 0.0);
-  std::vector<double> U = knots(n, p), gx, gw;
+  std::vector<double> U = knots(n, p, ax.breaks), gx, gw;
   gauss_legendre(p + 1, gx, gw);
   std::vector<double> v(p + 1), d(p + 1);
-  const double h = 1.0 / n;
   for (int e = 0; e < n; ++e) {
     double* blk = loc.data() + size_t(e) * 4 * Q * Q;
     for (int q = 0; q <= p; ++q) {
-      double t = (e + 0.5) * h + 0.5 * h * gx[q];
-      double w = 0.5 * h * gw[q];
+      double t, w;
+      elem_point(ax, e, gx[q], gw[q], t, w);
       local_basis(U, p, e, t, v.data(), d.data());
       for (int a = 0; a <= p; ++a)
         for (int b = 0; b <= p; ++b) {
@@ -306,6 +351,16 @@ int point_basis(int n, int p, double x0, double* vals) {
   if (e >= n) e = n - 1;
   if (e < 0) e = 0;
   local_basis(U, p, e, x0, vals, d.data());
+  return e;
+}
+
+int point_basis(const Axis1D& ax, double x0, double* vals) {
+  if (ax.breaks.empty()) return point_basis(ax.n, ax.p, x0, vals);
+  std::vector<double> U = knots(ax.n, ax.p, ax.breaks), d(ax.p + 1);
+  int e = int(std::upper_bound(ax.breaks.begin(), ax.breaks.end(), x0) - ax.breaks.begin()) - 1;
+  if (e >= ax.n) e = ax.n - 1;
+  if (e < 0) e = 0;
+  local_basis(U, ax.p, e, x0, vals, d.data());
   return e;
 }
 
