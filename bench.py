@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--weights", default=None, help="learned: corrector parameter file (FP32)")
     ap.add_argument("--coarse-steps", type=int, default=400, help="learned: coarse steps of the guarded run")
     ap.add_argument("--tol", type=float, default=1e-4, help="learned: guard tolerance (relative l2 per coarse step)")
+    ap.add_argument("--p", type=int, default=P, help="B-spline degree of the single-instance workload (default 2)")
     ap.add_argument("--no-extras", action="store_true",
                     help="single mode: skip the mixed, batched and learned measurements added to the line")
     return ap.parse_args()
@@ -515,7 +516,9 @@ def mixed_result(n, tau, eps, mu, sigma, src, st, ref64, steps, warmup, local=0)
 
 
 def main():
+    global P
     args = parse()
+    P = args.p
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
