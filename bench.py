@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--coarse-steps", type=int, default=400, help="learned: coarse steps of the guarded run")
     ap.add_argument("--tol", type=float, default=1e-4, help="learned: guard tolerance (relative l2 per coarse step)")
     ap.add_argument("--p", type=int, default=P, help="B-spline degree of the single-instance workload (default 2)")
+    ap.add_argument("--serial-chains", action="store_true",
+                    help="run the three per-component chains of a half step one after another (default: concurrent)")
     ap.add_argument("--no-extras", action="store_true",
                     help="single mode: skip the mixed, batched and learned measurements added to the line")
     return ap.parse_args()
@@ -172,8 +174,8 @@ def cpu_baseline(n, eps, mu, sigma, src, tau):
 def config_of(n, tau, world):
     """The workload description shared by both arms (tau printed to 12 digits:
     each arm computes the explicit limit in its own code)."""
-    return {"workload": "ADI IGA Maxwell step, %d^3 elements, p=2, head-like 3-phase map seed %d, "
-                        "dipole, tau=4 dt_CFL" % (n, SEED), "n": n, "p": P, "tau": float("%.12g" % tau),
+    return {"workload": "ADI IGA Maxwell step, %d^3 elements, p=%d, head-like 3-phase map seed %d, "
+                        "dipole, tau=4 dt_CFL" % (n, P, SEED), "n": n, "p": P, "tau": float("%.12g" % tau),
             "l2": "working set 0.7 GB >> 129 MB L2 (no flush needed)",
             "parallelism": "replicas" if world > 1 else "single GPU"}
 
@@ -539,7 +541,7 @@ def main():
     n = args.n
     eps, mu, sigma, src = workload(n)
     # tau = 4 x explicit limit (the library computes the limit for these data)
-    s = adi.Solver((n, n, n), P, 1.0, eps, mu, sigma, precision=args.precision)
+    s = adi.Solver((n, n, n), P, 1.0, eps, mu, sigma, precision=args.precision, serial_chains=args.serial_chains)
     tau = 4.0 * s.cfl_dt()
     s.set_dt(tau)
     s.factor()

@@ -87,7 +87,10 @@ typedef struct {
   int mixed_no_refine;  /* ADI_PREC_MIXED only: 1 skips the refinement (E = E*, for error studies) */
   int mixed_fp64_residual; /* ADI_PREC_MIXED only: 1 evaluates the residual in FP64 (default 0: float-float) */
   int rhs_material;     /* ADI_RHS_ROW (default) or ADI_RHS_QUAD (not with ADI_PREC_MIXED; p <= 3 in FP64) */
-  int reserved[3];      /* must be 0 */
+  int serial_chains;    /* 0 (default): the line solves of the three E components of a half step run as three
+                           concurrent chains on streams of the handle (parallel branches of the step's graph);
+                           1: one after another on the handle's stream.  Same results bit for bit. */
+  int reserved[2];      /* must be 0 */
 } adi_options;
 
 /* Create a problem on the unit cube.

@@ -32,7 +32,8 @@ EXPORTS = ("adi_create", "adi_create_knots", "adi_factor", "adi_set_dt", "adi_se
 
 class AdiOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("use_graph", ctypes.c_int), ("mixed_no_refine", ctypes.c_int),
-                ("mixed_fp64_residual", ctypes.c_int), ("rhs_material", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("mixed_fp64_residual", ctypes.c_int), ("rhs_material", ctypes.c_int), ("serial_chains", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 class AdiInstanceDesc(ctypes.Structure):
@@ -133,7 +134,7 @@ class Solver:
     """One ADI Maxwell problem on the GPU (owns an adi_handle)."""
 
     def __init__(self, n, p, dt, eps=None, mu=None, sigma=None, precision="fp32", use_graph=True, _handle=None,
-                 refine=True, residual="ff", rhs_material="row", breaks=None):
+                 refine=True, residual="ff", rhs_material="row", breaks=None, serial_chains=False):
         lib = load_library()
         self._lib = lib
         if _handle is not None:  # an instance owned by a Batch
@@ -154,6 +155,7 @@ class Solver:
         opt.mixed_no_refine = 0 if refine else 1
         opt.mixed_fp64_residual = 1 if residual == "fp64" else 0
         opt.rhs_material = {"row": 0, "quad": 1}[rhs_material]
+        opt.serial_chains = 1 if serial_chains else 0
         self.dtype = np.float64 if precision == "fp64" else np.float32
         keep = []
 

@@ -58,7 +58,7 @@ cudaError_t record_step(adi_batch b) {
     cudaStream_t own = c.stream;
     e = cudaStreamWaitEvent(b->streams[i], b->fork, 0);
     c.stream = b->streams[i];
-    for (int w = 0; w < 4 && e == cudaSuccess; ++w) e = adi::run_substep(c, w);
+    if (e == cudaSuccess) e = adi::run_step(c);
     c.stream = own;
     if (e == cudaSuccess) e = cudaEventRecord(b->joins[i], b->streams[i]);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->joins[i], 0);

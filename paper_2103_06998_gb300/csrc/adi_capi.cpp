@@ -53,6 +53,11 @@ void free_ctx(Ctx* c0) {
       if (c->stiff_fac[i][m]) cudaFree(c->stiff_fac[i][m]);
   }
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  for (int i = 0; i < 3; ++i) {
+    if (c->branch[i]) cudaStreamDestroy(c->branch[i]);
+    if (c->ev_join[i]) cudaEventDestroy(c->ev_join[i]);
+  }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   delete c;
 }
 
@@ -181,12 +186,14 @@ static adi_status create_impl(int nx, int ny, int nz, int p, double dt, const do
   }
   if (p < 1 || p > adi::kMaxP) return fail(nullptr, ADI_EINVAL, "adi_create: p must be in 1..4");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(nullptr, ADI_EINVAL, "adi_create: dt must be finite and > 0");
-  int prec = ADI_PREC_FP32, use_graph = 1, refine = 1, res64 = 0, quad = 0;
+  int prec = ADI_PREC_FP32, use_graph = 1, refine = 1, res64 = 0, quad = 0, serial = 0;
   if (opt) {
     if (opt->precision != ADI_PREC_FP32 && opt->precision != ADI_PREC_FP64 && opt->precision != ADI_PREC_MIXED)
       return fail(nullptr, ADI_EINVAL, "adi_create: precision must be ADI_PREC_FP32, ADI_PREC_FP64 or ADI_PREC_MIXED");
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 2; ++i)
       if (opt->reserved[i] != 0) return fail(nullptr, ADI_EINVAL, "adi_create: reserved option fields must be 0");
+    if (opt->serial_chains != 0 && opt->serial_chains != 1)
+      return fail(nullptr, ADI_EINVAL, "adi_create: serial_chains must be 0 or 1");
     if (opt->rhs_material != ADI_RHS_ROW && opt->rhs_material != ADI_RHS_QUAD)
       return fail(nullptr, ADI_EINVAL, "adi_create: rhs_material must be ADI_RHS_ROW or ADI_RHS_QUAD");
     if (opt->rhs_material == ADI_RHS_QUAD && opt->precision == ADI_PREC_MIXED)
@@ -202,6 +209,7 @@ static adi_status create_impl(int nx, int ny, int nz, int p, double dt, const do
     refine = opt->mixed_no_refine ? 0 : 1;
     res64 = opt->mixed_fp64_residual;
     quad = opt->rhs_material == ADI_RHS_QUAD ? 1 : 0;
+    serial = opt->serial_chains;
   }
   const size_t ne = (size_t)nx * ny * nz;
   for (const double* arr : {eps, mu}) {
@@ -230,6 +238,7 @@ static adi_status create_impl(int nx, int ny, int nz, int p, double dt, const do
   c->mixed_refine = prec == ADI_PREC_MIXED ? refine : 0;
   c->mixed_fp64_residual = res64;
   c->rhs_quad = quad;
+  c->serial_chains = serial;
   c->esize = prec == ADI_PREC_FP64 ? 8 : 4;
   c->dt = dt;
   cudaError_t e = cudaGetDevice(&c->device);
@@ -243,6 +252,13 @@ static adi_status create_impl(int nx, int ny, int nz, int p, double dt, const do
     return cuda_fail(nullptr, e, "adi_create: cudaStreamCreate");
   }
   c->own_stream = true;
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&c->branch[i], cudaStreamNonBlocking);
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&c->ev_join[i], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    free_ctx(c);
+    return cuda_fail(nullptr, e, "adi_create: branch streams");
+  }
   const size_t fb = c->Np * c->esize;
   bool ok = true;
   auto alloc = [&](void** p, size_t bytes) {
@@ -417,7 +433,7 @@ static adi_status capture_graph(adi_handle h) {
   cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_fail(h, e, "adi_step: begin capture");
   cudaError_t ek = cudaSuccess;
-  for (int w = 0; w < 4 && ek == cudaSuccess; ++w) ek = adi::run_substep(*h, w);
+  ek = adi::run_step(*h);
   e = cudaStreamEndCapture(h->stream, &g);
   if (ek != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -447,7 +463,7 @@ adi_status adi_step(adi_handle h, int n) {
     if (graph) {
       e = cudaGraphLaunch(h->graph, h->stream);
     } else {
-      for (int w = 0; w < 4 && e == cudaSuccess; ++w) e = adi::run_substep(*h, w);
+      e = adi::run_step(*h);
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "adi_step");
     h->steps_host += 1;

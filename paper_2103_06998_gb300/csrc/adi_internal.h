@@ -197,6 +197,12 @@ struct Ctx {
 
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  // the three component chains of a half step run on these streams, forked from
+  // and joined back to `stream` (serial while profiling or with serial_chains)
+  cudaStream_t branch[3] = {};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[3] = {};
+  int serial_chains = 0;
   int device = 0;
   int smem_optin = 48 * 1024;  // per-block opt-in shared memory (set by adi_factor)
 
@@ -260,7 +266,10 @@ struct Ctx {
 // Kernel-side entry points (adi_kernels.cu), all asynchronous on ctx.stream.
 cudaError_t upload_tables(Ctx& c);
 cudaError_t compute_coefficients(Ctx& c);
+// which 0..3: E half 1, H half 1, E half 2, H half 2; 4, 5: half step 1 or 2 (E then H)
 cudaError_t run_substep(Ctx& c, int which);
+// one time step (run_substep 4 then 5): the same arrays, bit for bit, as 0..3 in turn
+cudaError_t run_step(Ctx& c);
 cudaError_t set_fields_dev(Ctx& c, const double* d_src);
 // convert 6 N_c doubles at d_src (device memory or mapped host memory) into the six
 // arrays dst (state layout, constrained coefficients zero); d_bad (optional) |= 1 on NaN/Inf

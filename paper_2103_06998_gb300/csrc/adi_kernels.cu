@@ -3110,29 +3110,82 @@ constexpr int kStiffDir[2][3] = {{1, 2, 0}, {2, 0, 1}};
 // Solve T E = R per component: the stiffness direction first, then the two
 // mass directions (order of the Appendix, eqs. split1/split2); R is overwritten
 // and the result goes to out (may be R itself).
+// The three components of an E half step (and the three H components of the
+// uniform-mu H half step) are independent chains of line solves that write
+// disjoint arrays.  Chains runs chain i on branch stream i, forked from and
+// joined back to c.stream; inside a captured step they become parallel branches
+// of the graph, so the short, latency-bound line solves of different
+// components share the SMs.  Each chain keeps its own order, hence the same
+// results bit for bit as the serial order.  While profiling (per-launch events
+// on c.stream) and with serial_chains the chains run one after another.
+class Chains {
+ public:
+  explicit Chains(Ctx& c) : c_(c), main_(c.stream), on_(!c.profiling && !c.serial_chains && c.branch[0]) {
+    if (!on_) return;
+    err_ = cudaEventRecord(c.ev_fork, main_);
+    for (int i = 0; i < 3 && err_ == cudaSuccess; ++i) err_ = cudaStreamWaitEvent(c.branch[i], c.ev_fork, 0);
+  }
+  ~Chains() { join(); }
+  Chains(const Chains&) = delete;
+  Chains& operator=(const Chains&) = delete;
+  cudaError_t status() const { return err_; }
+  void use(int i) {
+    if (on_) c_.stream = c_.branch[i];
+  }
+  // main stream waits for every branch; c.stream is the main stream again
+  cudaError_t join() {
+    if (!on_) return cudaSuccess;
+    on_ = false;
+    c_.stream = main_;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+      e = cudaEventRecord(c_.ev_join[i], c_.branch[i]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(main_, c_.ev_join[i], 0);
+    }
+    return e;
+  }
+
+ private:
+  Ctx& c_;
+  cudaStream_t main_;
+  bool on_;
+  cudaError_t err_ = cudaSuccess;
+};
+
+// Line solves of E component i of half step `half`, in place on R[i] and into
+// out[i]: the row-scaled M + c S along the material direction first (R10),
+// then the two mass directions.
 template <typename T, int P>
-cudaError_t e_solve(Ctx& c, int half, T* const* R, T* const* out) {
+cudaError_t e_chain(Ctx& c, int half, int i, T* const* R, T* const* out) {
   T** cf = reinterpret_cast<T**>(c.coef);
   static const char* stiff_name[3] = {"line_x_stiff", "line_y_stiff", "line_z_stiff"};
   static const char* mass_name[3] = {"line_x_mass", "line_y_mass", "line_z_mass"};
-  cudaError_t e = cudaSuccess;
+  const int sd = kStiffDir[half - 1][i];
+  LineJobs<T> js{};
+  js.job[0] = job_of<T>(R[i], R[i], cf[2], 0.0, 1, reinterpret_cast<const T*>(c.pivots[sd]));
+  for (int m = 0; m < 2 * P; ++m) js.job[0].fac[m] = reinterpret_cast<T*>(c.stiff_fac[sd][m]);
+  cudaError_t e = launch_line<T, P>(c, sd, LM_STIFF, js, 1, stiff_name[sd]);
+  if (e != cudaSuccess) return e;
+  int md[2], m = 0;
+  for (int d = 0; d < 3; ++d)
+    if (d != sd) md[m++] = d;
+  js.job[0] = job_of<T>(R[i], R[i], nullptr, 0.0, md[0] != i);
+  e = launch_line<T, P>(c, md[0], LM_MASS, js, 1, mass_name[md[0]]);
+  if (e != cudaSuccess) return e;
+  js.job[0] = job_of<T>(R[i], out[i], nullptr, 0.0, md[1] != i);
+  return launch_line<T, P>(c, md[1], LM_MASS, js, 1, mass_name[md[1]]);
+}
+
+template <typename T, int P>
+cudaError_t e_solve(Ctx& c, int half, T* const* R, T* const* out) {
+  Chains ch(c);
+  cudaError_t e = ch.status();
   for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
-    const int sd = kStiffDir[half - 1][i];
-    LineJobs<T> js{};
-    js.job[0] = job_of<T>(R[i], R[i], cf[2], 0.0, 1, reinterpret_cast<const T*>(c.pivots[sd]));
-    for (int m = 0; m < 2 * P; ++m) js.job[0].fac[m] = reinterpret_cast<T*>(c.stiff_fac[sd][m]);
-    e = launch_line<T, P>(c, sd, LM_STIFF, js, 1, stiff_name[sd]);
-    if (e != cudaSuccess) return e;
-    int md[2], m = 0;
-    for (int d = 0; d < 3; ++d)
-      if (d != sd) md[m++] = d;
-    js.job[0] = job_of<T>(R[i], R[i], nullptr, 0.0, md[0] != i);
-    e = launch_line<T, P>(c, md[0], LM_MASS, js, 1, mass_name[md[0]]);
-    if (e != cudaSuccess) return e;
-    js.job[0] = job_of<T>(R[i], out[i], nullptr, 0.0, md[1] != i);
-    e = launch_line<T, P>(c, md[1], LM_MASS, js, 1, mass_name[md[1]]);
+    ch.use(i);
+    e = e_chain<T, P>(c, half, i, R, out);
   }
-  return e;
+  const cudaError_t ej = ch.join();
+  return e != cudaSuccess ? e : ej;
 }
 
 // FP64 band table of (axis d, op o) inside c.tab64
@@ -3314,16 +3367,15 @@ cudaError_t launch_rhs_quad(Ctx& c, const T* const* fields, int nfields, T* cons
   }
 }
 
-// E half step: the right-hand side, then the line solves (e_solve).
+// Right-hand side of an E half step (eqs. discrete1 / discrete3) into c.rhs.
 template <typename T, int P>
-cudaError_t e_substep(Ctx& c, int half) {
+cudaError_t e_rhs(Ctx& c, int half) {
   T** cur = reinterpret_cast<T**>(c.cur);
   T** hlf = reinterpret_cast<T**>(c.half);
   T** R = reinterpret_cast<T**>(c.rhs);
   T** cf = reinterpret_cast<T**>(c.coef);
   T* const* Ein = half == 1 ? cur : hlf;
   T* const* Hin = cur;  // H^n (half 1) or H^{n+1/2} (half 2), updated in place
-  T* const* Eout = half == 1 ? hlf : cur;
   RhsParams<T> prm{};
   for (int i = 0; i < 3; ++i) {
     prm.fields[i] = Ein[i];
@@ -3357,8 +3409,22 @@ cudaError_t e_substep(Ctx& c, int half) {
   prm.advance_clock = 0;
   double bytes = (double)c.Nc * sizeof(T) * 12.0;
   const bool mixed = c.precision == ADI_PREC_MIXED;
-  cudaError_t e = c.rhs_quad ? launch_rhs_quad<T, P>(c, prm.fields, 6, R, prm.terms, prm.nterms, true, prm.t_frac)
-                             : launch_rhs_e<T, P>(c, prm, half, bytes, mixed);
+  return c.rhs_quad ? launch_rhs_quad<T, P>(c, prm.fields, 6, R, prm.terms, prm.nterms, true, prm.t_frac)
+                    : launch_rhs_e<T, P>(c, prm, half, bytes, mixed);
+}
+
+// E half step: the right-hand side, then the line solves (e_solve), then in
+// mixed precision one refinement.
+template <typename T, int P>
+cudaError_t e_substep(Ctx& c, int half) {
+  T** cur = reinterpret_cast<T**>(c.cur);
+  T** hlf = reinterpret_cast<T**>(c.half);
+  T** R = reinterpret_cast<T**>(c.rhs);
+  T* const* Ein = half == 1 ? cur : hlf;
+  T* const* Hin = cur;
+  T* const* Eout = half == 1 ? hlf : cur;
+  const bool mixed = c.precision == ADI_PREC_MIXED;
+  cudaError_t e = e_rhs<T, P>(c, half);
   if (e != cudaSuccess) return e;
   e = e_solve<T, P>(c, half, R, Eout);
   if (e != cudaSuccess || !mixed || !c.mixed_refine) return e;
@@ -3438,7 +3504,8 @@ cudaError_t h_substep_general(Ctx& c, int half) {
 //   H1 += d (-D_y E3_alpha + D_z E2_beta)
 //   H2 += d (-D_z E1_alpha + D_x E3_beta)
 //   H3 += d (-D_x E2_alpha + D_y E1_beta)
-// done as three axis passes (z, x, y), two components each.
+// done as three axis passes (z, x, y), two components each.  Every pass adds to
+// an H component that another pass also adds to, so the passes run in order.
 template <typename T, int P>
 cudaError_t h_substep_uniform(Ctx& c, int half) {
   T** cur = reinterpret_cast<T**>(c.cur);
@@ -3447,12 +3514,10 @@ cudaError_t h_substep_uniform(Ctx& c, int half) {
   T* const* Ea = cur;     // alpha: E^n (half 1) or E^{n+1} (half 2)
   T* const* Eb = hlf;     // beta:  E^{n+1/2}
   const double d = c.d_uniform;
-  T** R = reinterpret_cast<T**>(c.rhs);  // free during the H half step: intermediates of y / z passes
+  // the staged y / z derivative kernel and the x kernel need no intermediate array
   LineJobs<T> js{};
   js.job[0] = job_of<T>(Eb[1], H[0], nullptr, d, 0);
   js.job[1] = job_of<T>(Ea[0], H[1], nullptr, -d, 0);
-  js.job[0].work = R[0];
-  js.job[1].work = R[1];
   cudaError_t e = launch_line<T, P>(c, 2, LM_DERIV, js, 2, "line_z_deriv");
   if (e != cudaSuccess) return e;
   js.job[0] = job_of<T>(Eb[2], H[1], nullptr, d, 0);
@@ -3461,8 +3526,6 @@ cudaError_t h_substep_uniform(Ctx& c, int half) {
   if (e != cudaSuccess) return e;
   js.job[0] = job_of<T>(Ea[2], H[0], nullptr, -d, 0);
   js.job[1] = job_of<T>(Eb[0], H[2], nullptr, d, 0);
-  js.job[0].work = R[0];
-  js.job[1].work = R[1];
   e = launch_line<T, P>(c, 1, LM_DERIV, js, 2, "line_y_deriv");
   if (e != cudaSuccess) return e;
   if (half == 2) e = advance_clock(c);
@@ -3509,7 +3572,12 @@ cudaError_t substep_tp(Ctx& c, int which) {
     case 0: return e_substep<T, P>(c, 1);
     case 1: return h_substep<T, P>(c, 1);
     case 2: return e_substep<T, P>(c, 2);
-    default: return h_substep<T, P>(c, 2);
+    case 3: return h_substep<T, P>(c, 2);
+    default: {  // 4, 5: half step 1 or 2, E then H
+      const int half = which - 3;
+      cudaError_t e = e_substep<T, P>(c, half);
+      return e == cudaSuccess ? h_substep<T, P>(c, half) : e;
+    }
   }
 }
 
@@ -3811,6 +3879,11 @@ cudaError_t upload_tables(Ctx& c) {
 
 cudaError_t run_substep(Ctx& c, int which) {
   return c.precision == ADI_PREC_FP64 ? run_substep_f64(c, which) : substep_t<float>(c, which);
+}
+
+cudaError_t run_step(Ctx& c) {
+  cudaError_t e = run_substep(c, 4);
+  return e == cudaSuccess ? run_substep(c, 5) : e;
 }
 
 cudaError_t set_fields_into(Ctx& c, const double* d_src, void* const* dst, int* d_bad) {

@@ -58,6 +58,14 @@ def test_invalid_arguments_rejected_before_any_cuda_call(lib):
     assert L.adi_create(4, 4, 4, 2, 0.1, adi._dptr(bad), None, None, None, ctypes.byref(h)) == adi.ADI_EINVAL
     assert b"eps and mu" in L.adi_last_error(None)
     assert L.adi_step(None, 1) == adi.ADI_EINVAL
+    opt = adi.AdiOptions()
+    opt.precision = adi.PREC_FP32
+    opt.serial_chains = 2
+    assert L.adi_create(4, 4, 4, 2, 0.1, None, None, None, ctypes.byref(opt), ctypes.byref(h)) == adi.ADI_EINVAL
+    assert b"serial_chains" in L.adi_last_error(None)
+    opt.serial_chains = 0
+    opt.reserved[1] = 1
+    assert L.adi_create(4, 4, 4, 2, 0.1, None, None, None, ctypes.byref(opt), ctypes.byref(h)) == adi.ADI_EINVAL
 
 
 def test_net_parameter_vector_layout():
