@@ -2098,15 +2098,41 @@ struct Smem {
   static constexpr int TILE = HZ * HY * BX, ZR = TZ * SZ, YR = TZ * SY;
   // dynamic shared memory: 128 bytes of alignment slack, the tiles (TMA
   // destinations, 128-byte aligned), the pass buffers, then two mbarriers
-  static constexpr size_t DATA2 = sizeof(T) * (2 * (size_t)TILE + 2 * (size_t)ZR + 2 * (size_t)YR);
+  // band rows of the tile's output rows along z and y for tiles that reach a
+  // boundary row: [op M, A, B][row][q], rows padded to WP (16-byte vectors)
+  static constexpr int WP = (2 * P + 1 + 3) / 4 * 4;
+  static constexpr int BT = 3 * (TZ + TY) * WP;
+  static constexpr size_t DATA2 = sizeof(T) * (2 * (size_t)TILE + 2 * (size_t)ZR + 2 * (size_t)YR + BT);
   static constexpr int NBUF = (ADI_RHS_NBUF == 2 && DATA2 + 128 + 16 <= 227 * 1024) ? 2 : 1;  // double-buffer if it fits
-  static constexpr size_t DATA = sizeof(T) * (NBUF * (size_t)TILE + 2 * (size_t)ZR + 2 * (size_t)YR);
+  static constexpr size_t DATA = sizeof(T) * (NBUF * (size_t)TILE + 2 * (size_t)ZR + 2 * (size_t)YR + BT);
   static constexpr size_t BYTES = 128 + DATA + 16;
 };
 
+// the W band values of one staged row (16-byte vector loads from shared memory)
+template <typename T, int W, int WP>
+__device__ __forceinline__ void ldrow(const T* p, T (&r)[W]) {
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int k = 0; k < WP / 4; ++k) {
+      const float4 v = reinterpret_cast<const float4*>(p)[k];
+      const T e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (4 * k + j < W) r[4 * k + j] = e[j];
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < WP / 2; ++k) {
+      const double2 v = reinterpret_cast<const double2*>(p)[k];
+      if (2 * k < W) r[2 * k] = v.x;
+      if (2 * k + 1 < W) r[2 * k + 1] = v.y;
+    }
+  }
+}
+
 // z pass: column i = (yy, xx) of the haloed plane, 8 outputs from a window of HZ values
 template <typename T, int P, int OP, bool INNER>
-__device__ __forceinline__ void zpass(const RhsParams<T>& prm, const T* tl, T* zr, int z0, int i) {
+__device__ __forceinline__ void zpass(const RhsParams<T>& prm, const T* tl, T* zr, const T* tz, int i) {
   using S = Smem<T, P>;
   constexpr int W = 2 * P + 1;
   const T* col = tl + (i / S::HX) * S::BX + S::XOFF + (i % S::HX);
@@ -2115,24 +2141,38 @@ __device__ __forceinline__ void zpass(const RhsParams<T>& prm, const T* tl, T* z
   for (int k = 0; k < S::HZ; ++k) w[k] = col[k * S::HY * S::BX];
 #pragma unroll
   for (int zz = 0; zz < TZ; ++zz) {
+    T c[W];
+    if (INNER) {
+#pragma unroll
+      for (int q = 0; q < W; ++q) c[q] = prm.st[2].w[sidx(OP)][q];
+    } else {
+      ldrow<T, W, S::WP>(tz + (sidx(OP) * TZ + zz) * S::WP, c);
+    }
     T s = T(0);
 #pragma unroll
-    for (int q = 0; q < W; ++q) s += bandv<T, P, 2, OP, INNER>(prm, z0 + zz, q) * w[zz + q];
+    for (int q = 0; q < W; ++q) s += c[q] * w[zz + q];
     zr[zz * S::SZ + i] = s;
   }
 }
 
 // y pass: column (zz, xx), 8 outputs from a window of HY values
 template <typename T, int P, int OP, bool INNER>
-__device__ __forceinline__ void yapply(const RhsParams<T>& prm, const T (&w)[Smem<T, P>::HY], T* yr, int y0, int zz,
+__device__ __forceinline__ void yapply(const RhsParams<T>& prm, const T (&w)[Smem<T, P>::HY], T* yr, const T* ty, int zz,
                                        int xx) {
   using S = Smem<T, P>;
   constexpr int W = 2 * P + 1;
 #pragma unroll
   for (int yy = 0; yy < TY; ++yy) {
+    T c[W];
+    if (INNER) {
+#pragma unroll
+      for (int q = 0; q < W; ++q) c[q] = prm.st[1].w[sidx(OP)][q];
+    } else {
+      ldrow<T, W, S::WP>(ty + (sidx(OP) * TY + yy) * S::WP, c);
+    }
     T s = T(0);
 #pragma unroll
-    for (int q = 0; q < W; ++q) s += bandv<T, P, 1, OP, INNER>(prm, y0 + yy, q) * w[yy + q];
+    for (int q = 0; q < W; ++q) s += c[q] * w[yy + q];
     yr[zz * S::SY + yy * S::HXP + xx] = s;
   }
 }
@@ -2188,7 +2228,7 @@ struct V2<double> {
 
 // z pass of column pair i2 = (yy, xx/2) for one or two z operators (ZSHARE: one)
 template <typename T, int P, int OP0, int OP1, bool ZSHARE, bool INNER>
-__device__ __forceinline__ void zpass2(const RhsParams<T>& prm, const T* tl, T* zr0, T* zr1, int z0, int i2) {
+__device__ __forceinline__ void zpass2(const RhsParams<T>& prm, const T* tl, T* zr0, T* zr1, const T* tz, int i2) {
   using S = Smem<T, P>;
   using v2 = typename V2<T>::t;
   constexpr int W = 2 * P + 1;
@@ -2205,14 +2245,25 @@ __device__ __forceinline__ void zpass2(const RhsParams<T>& prm, const T* tl, T* 
   const int o = yy * S::HX + xx;
 #pragma unroll
   for (int zz = 0; zz < TZ; ++zz) {
+    T cr[W], dr[W];
+    if (INNER) {
+#pragma unroll
+      for (int q = 0; q < W; ++q) {
+        cr[q] = prm.st[2].w[sidx(OP0)][q];
+        dr[q] = prm.st[2].w[sidx(OP1)][q];
+      }
+    } else {
+      ldrow<T, W, S::WP>(tz + (sidx(OP0) * TZ + zz) * S::WP, cr);
+      if (!ZSHARE) ldrow<T, W, S::WP>(tz + (sidx(OP1) * TZ + zz) * S::WP, dr);
+    }
     T a0 = T(0), a1 = T(0), b0 = T(0), b1 = T(0);
 #pragma unroll
     for (int q = 0; q < W; ++q) {
-      const T c = bandv<T, P, 2, OP0, INNER>(prm, z0 + zz, q);
+      const T c = cr[q];
       a0 += c * w[zz + q].x;
       a1 += c * w[zz + q].y;
       if (!ZSHARE) {
-        const T d = bandv<T, P, 2, OP1, INNER>(prm, z0 + zz, q);
+        const T d = dr[q];
         b0 += d * w[zz + q].x;
         b1 += d * w[zz + q].y;
       }
@@ -2231,8 +2282,8 @@ __device__ __forceinline__ void zpass2(const RhsParams<T>& prm, const T* tl, T* 
 
 // y pass of column pair i2 = (zz, xx/2) for the field's two y operators
 template <typename T, int P, int OP0, int OP1, bool ZSHARE, bool INNER>
-__device__ __forceinline__ void ypass2(const RhsParams<T>& prm, const T* zr0, const T* zr1, T* yr0, T* yr1, int y0,
-                                       int i2) {
+__device__ __forceinline__ void ypass2(const RhsParams<T>& prm, const T* zr0, const T* zr1, T* yr0, T* yr1,
+                                       const T* ty, int i2) {
   using S = Smem<T, P>;
   using v2 = typename V2<T>::t;
   constexpr int W = 2 * P + 1;
@@ -2245,11 +2296,22 @@ __device__ __forceinline__ void ypass2(const RhsParams<T>& prm, const T* zr0, co
   }
 #pragma unroll
   for (int yy = 0; yy < TY; ++yy) {
+    T cr[W], dr[W];
+    if (INNER) {
+#pragma unroll
+      for (int q = 0; q < W; ++q) {
+        cr[q] = prm.st[1].w[sidx(OP0)][q];
+        dr[q] = prm.st[1].w[sidx(OP1)][q];
+      }
+    } else {
+      ldrow<T, W, S::WP>(ty + (sidx(OP0) * TY + yy) * S::WP, cr);
+      ldrow<T, W, S::WP>(ty + (sidx(OP1) * TY + yy) * S::WP, dr);
+    }
     T a0 = T(0), a1 = T(0), b0 = T(0), b1 = T(0);
 #pragma unroll
     for (int q = 0; q < W; ++q) {
-      const T c = bandv<T, P, 1, OP0, INNER>(prm, y0 + yy, q);
-      const T d = bandv<T, P, 1, OP1, INNER>(prm, y0 + yy, q);
+      const T c = cr[q];
+      const T d = dr[q];
       a0 += c * w0[yy + q].x;
       a1 += c * w0[yy + q].y;
       b0 += d * w1[yy + q].x;
@@ -2343,8 +2405,8 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 // Stage z: wait for the field's tile (every thread; the give-up decision is
 // block-wide), z pass into s_zr.
 template <typename T, int P, int H, int F>
-__device__ __forceinline__ bool zstage(const RhsParams<T>& prm, T* s_tile, T* s_zr, unsigned long long* bars, int z0,
-                                       bool inZ) {
+__device__ __forceinline__ bool zstage(const RhsParams<T>& prm, T* s_tile, T* s_zr, unsigned long long* bars,
+                                       const T* tz, bool inZ) {
   using S = Smem<T, P>;
   using PL = Plan<H, F>;
   const int tid = threadIdx.x;
@@ -2355,16 +2417,16 @@ __device__ __forceinline__ bool zstage(const RhsParams<T>& prm, T* s_tile, T* s_
   constexpr bool zshare = PL::z0 == PL::z1;
   if constexpr (P == 2) {  // pairs of columns
     for (int i2 = tid; i2 < S::HY * S::HX / 2; i2 += NT) {
-      if (inZ) zpass2<T, P, PL::z0, PL::z1, zshare, true>(prm, tl, s_zr, s_zr + S::ZR, z0, i2);
-      else zpass2<T, P, PL::z0, PL::z1, zshare, false>(prm, tl, s_zr, s_zr + S::ZR, z0, i2);
+      if (inZ) zpass2<T, P, PL::z0, PL::z1, zshare, true>(prm, tl, s_zr, s_zr + S::ZR, tz, i2);
+      else zpass2<T, P, PL::z0, PL::z1, zshare, false>(prm, tl, s_zr, s_zr + S::ZR, tz, i2);
     }
   } else {  // p = 1, 3: one column per thread
     for (int i = tid; i < S::HY * S::HX; i += NT) {
-      if (inZ) zpass<T, P, PL::z0, true>(prm, tl, s_zr, z0, i);
-      else zpass<T, P, PL::z0, false>(prm, tl, s_zr, z0, i);
+      if (inZ) zpass<T, P, PL::z0, true>(prm, tl, s_zr, tz, i);
+      else zpass<T, P, PL::z0, false>(prm, tl, s_zr, tz, i);
       if (!zshare) {
-        if (inZ) zpass<T, P, PL::z1, true>(prm, tl, s_zr + S::ZR, z0, i);
-        else zpass<T, P, PL::z1, false>(prm, tl, s_zr + S::ZR, z0, i);
+        if (inZ) zpass<T, P, PL::z1, true>(prm, tl, s_zr + S::ZR, tz, i);
+        else zpass<T, P, PL::z1, false>(prm, tl, s_zr + S::ZR, tz, i);
       }
     }
   }
@@ -2373,26 +2435,26 @@ __device__ __forceinline__ bool zstage(const RhsParams<T>& prm, T* s_tile, T* s_
 
 // Stage y: s_zr -> s_yr for the field's two y operators.
 template <typename T, int P, int H, int F>
-__device__ __forceinline__ void ystage(const RhsParams<T>& prm, const T* s_zr, T* s_yr, int y0, bool inY) {
+__device__ __forceinline__ void ystage(const RhsParams<T>& prm, const T* s_zr, T* s_yr, const T* ty, bool inY) {
   using S = Smem<T, P>;
   using PL = Plan<H, F>;
   const int tid = threadIdx.x;
   constexpr bool zshare = PL::z0 == PL::z1;
   if constexpr (P == 2) {
     for (int i2 = tid; i2 < TZ * S::HX / 2; i2 += NT) {
-      if (inY) ypass2<T, P, PL::y0, PL::y1, zshare, true>(prm, s_zr, s_zr + S::ZR, s_yr, s_yr + S::YR, y0, i2);
-      else ypass2<T, P, PL::y0, PL::y1, zshare, false>(prm, s_zr, s_zr + S::ZR, s_yr, s_yr + S::YR, y0, i2);
+      if (inY) ypass2<T, P, PL::y0, PL::y1, zshare, true>(prm, s_zr, s_zr + S::ZR, s_yr, s_yr + S::YR, ty, i2);
+      else ypass2<T, P, PL::y0, PL::y1, zshare, false>(prm, s_zr, s_zr + S::ZR, s_yr, s_yr + S::YR, ty, i2);
     }
   } else {
     for (int i = tid; i < TZ * S::HX; i += NT) {
       const int zz = i / S::HX, xx = i % S::HX;
       T w[S::HY];
       yload<T, P>(s_zr, zz, xx, w);
-      if (inY) yapply<T, P, PL::y0, true>(prm, w, s_yr, y0, zz, xx);
-      else yapply<T, P, PL::y0, false>(prm, w, s_yr, y0, zz, xx);
+      if (inY) yapply<T, P, PL::y0, true>(prm, w, s_yr, ty, zz, xx);
+      else yapply<T, P, PL::y0, false>(prm, w, s_yr, ty, zz, xx);
       if (!zshare) yload<T, P>(s_zr + S::ZR, zz, xx, w);
-      if (inY) yapply<T, P, PL::y1, true>(prm, w, s_yr + S::YR, y0, zz, xx);
-      else yapply<T, P, PL::y1, false>(prm, w, s_yr + S::YR, y0, zz, xx);
+      if (inY) yapply<T, P, PL::y1, true>(prm, w, s_yr + S::YR, ty, zz, xx);
+      else yapply<T, P, PL::y1, false>(prm, w, s_yr + S::YR, ty, zz, xx);
     }
   }
 }
@@ -2429,19 +2491,19 @@ __device__ __forceinline__ void xstage(const RhsParams<T>& prm, const T* s_yr, i
 // s_yr, which y(F) overwrites only after the barrier that follows it.
 template <typename T, int P, int H, int F>
 __device__ __forceinline__ bool pipe_field(const RhsParams<T>& prm, const TmaMaps& maps, T* s_tile, T* s_zr,
-                                           T* s_yr, unsigned long long* bars, int x0, int y0, int z0, bool inZ,
+                                           T* s_yr, const T* s_bt, unsigned long long* bars, int x0, int y0, int z0, bool inZ,
                                            bool inY, bool inX, int xp, int rg, T (&cf)[3][RPT][2],
                                            T (&acc)[3][RPT][2]) {
   using S = Smem<T, P>;
   const int tid = threadIdx.x;
   if (S::NBUF == 2 && F + 1 < 6 && tid == 0)
     tma_tile<T, P>(&maps.m[F + 1], s_tile + ((F + 1) & 1) * S::TILE, &bars[(F + 1) & 1], x0 - 4, y0 - P, z0 - P);
-  if (!zstage<T, P, H, F>(prm, s_tile, s_zr, bars, z0, inZ)) return false;
+  if (!zstage<T, P, H, F>(prm, s_tile, s_zr, bars, s_bt, inZ)) return false;
   if (F > 0) xstage<T, P, H, (F > 0 ? F - 1 : 0)>(prm, s_yr, x0, inX, xp, rg, cf, acc);
   __syncthreads();
   if (S::NBUF == 1 && F + 1 < 6 && tid == 0)  // single buffer (FP64): load the next tile during the y pass
     tma_tile<T, P>(&maps.m[F + 1], s_tile, &bars[0], x0 - 4, y0 - P, z0 - P);
-  ystage<T, P, H, F>(prm, s_zr, s_yr, y0, inY);
+  ystage<T, P, H, F>(prm, s_zr, s_yr, s_bt + 3 * TZ * S::WP, inY);
   __syncthreads();
   return true;
 }
@@ -2459,6 +2521,7 @@ __global__ void __launch_bounds__(rhs2::NT, sizeof(T) == 4 ? ADI_RHS_MINB : 1)
   T* s_tile = reinterpret_cast<T*>(sbase);     // NBUF x TILE (TMA destinations)
   T* s_zr = s_tile + S::NBUF * S::TILE;         // 2 x ZR
   T* s_yr = s_zr + 2 * S::ZR;                   // 2 x YR
+  T* s_bt = s_yr + 2 * S::YR;                   // BT: staged z and y band rows (boundary tiles)
   const int tid = threadIdx.x;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
   const int Nx = prm.Nx, Ny = prm.Ny, Nz = prm.Nz, pitch = prm.pitch;
@@ -2486,6 +2549,17 @@ __global__ void __launch_bounds__(rhs2::NT, sizeof(T) == 4 ? ADI_RHS_MINB : 1)
       }
     }
   }
+  if (!inZ || !inY) {  // band rows of the tile's output rows (clamped to the last row), ops M, A, B
+    constexpr int W = 2 * P + 1;
+    for (int i = tid; i < S::BT; i += NT) {
+      const int q = i % S::WP, r = (i / S::WP) % (TZ + TY), o = i / (S::WP * (TZ + TY));
+      const bool isz = r < TZ;  // z rows first, then y rows ([op][row] per axis)
+      const int d = isz ? 2 : 1, row = isz ? z0 + r : y0 + (r - TZ), Nd = isz ? Nz : Ny;
+      const T* b = o == 0 ? prm.ax[d].band[OP_M] : (o == 1 ? prm.ax[d].band[OP_A] : prm.ax[d].band[OP_B]);
+      const int dst = isz ? (o * TZ + r) * S::WP + q : 3 * TZ * S::WP + (o * TY + (r - TZ)) * S::WP + q;
+      s_bt[dst] = q < W ? b[min(row, Nd - 1) * W + q] : T(0);
+    }
+  }
   if (tid == 0) {
     mbar_init(&bars[0]);
     mbar_init(&bars[1]);
@@ -2493,12 +2567,12 @@ __global__ void __launch_bounds__(rhs2::NT, sizeof(T) == 4 ? ADI_RHS_MINB : 1)
   }
   __syncthreads();
   if (tid == 0) tma_tile<T, P>(&maps.m[0], s_tile, &bars[0], x0 - 4, y0 - P, z0 - P);
-  bool ok = pipe_field<T, P, H, 0>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
-  if (ok) ok = pipe_field<T, P, H, 1>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
-  if (ok) ok = pipe_field<T, P, H, 2>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
-  if (ok) ok = pipe_field<T, P, H, 3>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
-  if (ok) ok = pipe_field<T, P, H, 4>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
-  if (ok) ok = pipe_field<T, P, H, 5>(prm, maps, s_tile, s_zr, s_yr, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+  bool ok = pipe_field<T, P, H, 0>(prm, maps, s_tile, s_zr, s_yr, s_bt, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+  if (ok) ok = pipe_field<T, P, H, 1>(prm, maps, s_tile, s_zr, s_yr, s_bt, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+  if (ok) ok = pipe_field<T, P, H, 2>(prm, maps, s_tile, s_zr, s_yr, s_bt, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+  if (ok) ok = pipe_field<T, P, H, 3>(prm, maps, s_tile, s_zr, s_yr, s_bt, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+  if (ok) ok = pipe_field<T, P, H, 4>(prm, maps, s_tile, s_zr, s_yr, s_bt, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
+  if (ok) ok = pipe_field<T, P, H, 5>(prm, maps, s_tile, s_zr, s_yr, s_bt, bars, x0, y0, z0, inZ, inY, inX, xp, rg, cf, acc);
   if (ok) xstage<T, P, H, 5>(prm, s_yr, x0, inX, xp, rg, cf, acc);
   if (!ok) {
     // a tile never arrived: report, give the copies in flight a bounded time, leave
