@@ -612,27 +612,40 @@ def main():
                                         "GBps": k["bytes_per_launch"] / (k["total_ms"] / k["launches"] * 1e-3) / 1e9}
                             for k in stats}})
 
-    # ---- end to end through the C-ABI with pinned host buffers
-    host_in = torch.empty(6 * Nc, dtype=torch.float64, pin_memory=True)
-    host_out = torch.empty(6 * Nc, dtype=torch.float64, pin_memory=True)
-    host_in.numpy()[:] = inputs.random_fields((n + P,) * 3, 5).ravel() * 1e-3
-    for _ in range(max(1, min(args.warmup, 2))):  # untimed warm-up of the same sequence
-        s.set_fields_ptr(host_in.data_ptr(), 1.0)
-        s.step(1)
-        s.fields_ptr(host_out.data_ptr())
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        s.set_fields_ptr(host_in.data_ptr(), 1.0)
-        s.step(1)
-        s.fields_ptr(host_out.data_ptr())
-    barrier()
-    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
-    te = torch.tensor([e2e_s], device="cuda")
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e = {"value": world * dof_steps / float(te.item()), "unit": UNIT,
-           "h2d_bytes_per_step": 6 * Nc * 8, "d2h_bytes_per_step": 6 * Nc * 8}
+    # ---- end to end through the C-ABI with pinned host buffers: each step sets the
+    # fields from host memory, steps, and reads the fields back.  The state's own
+    # precision on the host side (floats for the FP32 and mixed handles, whose state
+    # is FP32: the same values as through doubles), and the double form as a second
+    # figure.
+    def e2e_run(host_t, set_fn, get_fn):
+        host_in = torch.empty(6 * Nc, dtype=host_t, pin_memory=True)
+        host_out = torch.empty(6 * Nc, dtype=host_t, pin_memory=True)
+        host_in.numpy()[:] = inputs.random_fields((n + P,) * 3, 5).ravel() * 1e-3
+        for _ in range(max(1, min(args.warmup, 2))):  # untimed warm-up of the same sequence
+            set_fn(host_in.data_ptr(), 1.0)
+            s.step(1)
+            get_fn(host_out.data_ptr())
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            set_fn(host_in.data_ptr(), 1.0)
+            s.step(1)
+            get_fn(host_out.data_ptr())
+        barrier()
+        te = torch.tensor([(time.perf_counter() - t0) / args.e2e_steps], device="cuda")
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        nb = 6 * Nc * host_in.element_size()
+        return {"value": world * dof_steps / float(te.item()), "unit": UNIT,
+                "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
+
+    e2e64 = e2e_run(torch.float64, s.set_fields_ptr, s.fields_ptr)
+    if args.precision == "fp64":
+        e2e = e2e64
+    else:
+        e2e = e2e_run(torch.float32, s.set_fields_f32_ptr, s.fields_f32_ptr)
+        e2e["host_dtype"] = "f32"
+        e2e["f64_host"] = e2e64
 
     # ---- per-step error against the FP64 GPU step from the same state (untimed)
     err64 = None

@@ -173,6 +173,15 @@ adi_status adi_substep(adi_handle h, int which);
  * page-locked EH is written by the device directly. */
 adi_status adi_fields(adi_handle h, double* EH, double* t);
 
+/* adi_set_fields and adi_fields with 6 N_c floats on the host side (the same
+ * layout, checks and synchronisation).  In all four calls EH must be aligned
+ * to its element size (else ADI_EINVAL, nothing is read or written).  For a handle whose state is FP32
+ * (ADI_PREC_FP32, ADI_PREC_MIXED) they move exactly the state's values in half
+ * the bytes of the double forms; for an FP64 handle the values are rounded to
+ * float on the way out and widened on the way in. */
+adi_status adi_set_fields_f32(adi_handle h, const float* EH, double t);
+adi_status adi_fields_f32(adi_handle h, float* EH, double* t);
+
 /* Copy the state, in the working precision (float or double as created), to
  * 6 N_c elements of device memory at dev_ptr, on cuda_stream (NULL = the
  * handle's stream).  Asynchronous. */

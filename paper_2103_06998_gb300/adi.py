@@ -19,7 +19,8 @@ _PREC = {"fp64": PREC_FP64, "fp32": PREC_FP32, "mixed": PREC_MIXED}
 
 # every symbol declared in include/adi_maxwell.h
 EXPORTS = ("adi_create", "adi_create_knots", "adi_factor", "adi_set_dt", "adi_set_stream", "adi_set_fields",
-           "adi_set_source", "adi_step", "adi_substep", "adi_fields", "adi_fields_device",
+           "adi_set_fields_f32", "adi_set_source", "adi_step", "adi_substep", "adi_fields", "adi_fields_f32",
+           "adi_fields_device",
            "adi_cfl_dt", "adi_cfl_dt_noalloc", "adi_sync", "adi_wait_selftest", "adi_norms", "adi_plane", "adi_set_profiling", "adi_kernel_stats", "adi_dims",
            "adi_destroy", "adi_last_error", "adi_status_string", "adi_set_line_tile",
            "adi_batch_create", "adi_batch_set_stream", "adi_batch_handle", "adi_batch_factor", "adi_batch_step", "adi_batch_sync",
@@ -69,10 +70,12 @@ def load_library(path=LIB_PATH):
         "adi_set_dt": (I, [H, D]),
         "adi_set_stream": (I, [H, ctypes.c_void_p]),
         "adi_set_fields": (I, [H, P(D), D]),
+        "adi_set_fields_f32": (I, [H, ctypes.c_void_p, D]),
         "adi_set_source": (I, [H, D, D, D, I, D, D, D, D]),
         "adi_step": (I, [H, I]),
         "adi_substep": (I, [H, I]),
         "adi_fields": (I, [H, P(D), P(D)]),
+        "adi_fields_f32": (I, [H, ctypes.c_void_p, P(D)]),
         "adi_fields_device": (I, [H, ctypes.c_void_p, ctypes.c_void_p]),
         "adi_cfl_dt": (D, [H]),
         "adi_cfl_dt_noalloc": (I, [I, I, I, I, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, P(D)]),
@@ -204,6 +207,10 @@ class Solver:
         self._check(self._lib.adi_set_fields(self.h, ctypes.cast(ctypes.c_void_p(int(host_ptr)),
                                                                  ctypes.POINTER(ctypes.c_double)), float(t)))
 
+    def set_fields_f32_ptr(self, host_ptr, t=0.0):
+        """Set fields from a raw host pointer to 6 N_c floats (e.g. pinned memory)."""
+        self._check(self._lib.adi_set_fields_f32(self.h, ctypes.c_void_p(int(host_ptr)), float(t)))
+
     def set_source(self, x0, comp, amp, f0, t0, s):
         self._check(self._lib.adi_set_source(self.h, float(x0[0]), float(x0[1]), float(x0[2]), int(comp),
                                              float(amp), float(f0), float(t0), float(s)))
@@ -224,6 +231,12 @@ class Solver:
         t = ctypes.c_double()
         self._check(self._lib.adi_fields(self.h, ctypes.cast(ctypes.c_void_p(int(host_ptr)),
                                                              ctypes.POINTER(ctypes.c_double)), ctypes.byref(t)))
+        return t.value
+
+    def fields_f32_ptr(self, host_ptr):
+        """Read the fields into a raw host pointer to 6 N_c floats; returns the time."""
+        t = ctypes.c_double()
+        self._check(self._lib.adi_fields_f32(self.h, ctypes.c_void_p(int(host_ptr)), ctypes.byref(t)))
         return t.value
 
     def fields_device(self, dev_ptr, stream_ptr=0):

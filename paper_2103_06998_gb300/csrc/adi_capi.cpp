@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -368,41 +369,85 @@ adi_status adi_set_stream(adi_handle h, void* s) {
   return ADI_OK;
 }
 
-adi_status adi_set_fields(adi_handle h, const double* EH, double t) {
-  if (!h) return fail(nullptr, ADI_EINVAL, "adi_set_fields: NULL handle");
-  if (!EH) return fail(h, ADI_EINVAL, "adi_set_fields: EH is NULL");
-  if (!std::isfinite(t)) return fail(h, ADI_EINVAL, "adi_set_fields: t must be finite");
-  // check on the device (a host scan of 6 N_c doubles would dominate the call); the
+}  // extern "C"
+
+extern "C" {
+static adi_status check_device_status(adi_handle h, const char* where);
+}
+
+// Shared by adi_set_fields (S = double) and adi_set_fields_f32 (S = float).
+template <typename S>
+static adi_status set_fields_impl(adi_handle h, const S* EH, double t, const char* name) {
+  if (!h) return fail(nullptr, ADI_EINVAL, std::string(name) + ": NULL handle");
+  if (!EH) return fail(h, ADI_EINVAL, std::string(name) + ": EH is NULL");
+  if (reinterpret_cast<uintptr_t>(EH) % sizeof(S) != 0)
+    return fail(h, ADI_EINVAL, std::string(name) + ": EH is not aligned to its element size");
+  if (!std::isfinite(t)) return fail(h, ADI_EINVAL, std::string(name) + ": t must be finite");
+  // check on the device (a host scan of 6 N_c values would dominate the call); the
   // state is written only when every value is finite.  A page-locked EH is converted
   // in one pass straight from host memory into scratch arrays (the right-hand side
   // and half-step buffers, free between steps; a partial step is discarded), then
   // copied into the state; other memory is copied to the staging buffer first.
   const long long n6 = 6LL * (long long)h->Nc;
-  const double* mapped = static_cast<const double*>(mapped_host(EH));
+  const S* mapped = static_cast<const S*>(mapped_host(EH));
   void* scratch[6] = {h->rhs[0], h->rhs[1], h->rhs[2], h->half[0], h->half[1], h->half[2]};
   cudaError_t e = cudaMemsetAsync(h->d_bad, 0, sizeof(int), h->stream);
   if (mapped) {
-    if (e == cudaSuccess) e = adi::set_fields_into(*h, mapped, scratch, h->d_bad);
+    if (e == cudaSuccess) e = adi::set_fields_into<S>(*h, mapped, scratch, h->d_bad);
   } else {
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h->stage, EH, n6 * sizeof(double), cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = adi::check_finite_dev(*h, (const double*)h->stage, n6, h->d_bad);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->stage, EH, n6 * sizeof(S), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = adi::check_finite_dev<S>(*h, (const S*)h->stage, n6, h->d_bad);
   }
   int bad = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, h->d_bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  if (e != cudaSuccess) return cuda_fail(h, e, "adi_set_fields");
-  if (bad) return fail(h, ADI_ENUMERIC, "adi_set_fields: NaN or Inf in EH");
+  if (e != cudaSuccess) return cuda_fail(h, e, name);
+  if (bad) return fail(h, ADI_ENUMERIC, std::string(name) + ": NaN or Inf in EH");
   if (mapped) {
     for (int i = 0; i < 6 && e == cudaSuccess; ++i)
       e = cudaMemcpyAsync(h->cur[i], scratch[i], h->Np * h->esize, cudaMemcpyDeviceToDevice, h->stream);
   } else {
-    e = adi::set_fields_dev(*h, (const double*)h->stage);
+    e = adi::set_fields_dev<S>(*h, (const S*)h->stage);
   }
   if (e == cudaSuccess) e = adi::set_clock(*h, t);
-  if (e != cudaSuccess) return cuda_fail(h, e, "adi_set_fields");
+  if (e != cudaSuccess) return cuda_fail(h, e, name);
   h->t_host = t;
   h->steps_host = 0;
   return ADI_OK;
+}
+
+// Shared by adi_fields (S = double) and adi_fields_f32 (S = float).
+template <typename S>
+static adi_status fields_impl(adi_handle h, S* EH, double* t, const char* name) {
+  if (!h) return fail(nullptr, ADI_EINVAL, std::string(name) + ": NULL handle");
+  if (!EH) return fail(h, ADI_EINVAL, std::string(name) + ": EH is NULL");
+  if (reinterpret_cast<uintptr_t>(EH) % sizeof(S) != 0)
+    return fail(h, ADI_EINVAL, std::string(name) + ": EH is not aligned to its element size");
+  // a page-locked EH is written directly by the kernel, other memory through the staging buffer
+  S* mapped = const_cast<S*>(static_cast<const S*>(mapped_host(EH)));
+  cudaError_t e = cudaMemsetAsync(h->d_bad, 0, sizeof(int), h->stream);
+  if (e == cudaSuccess) e = adi::get_fields_dev<S>(*h, mapped ? mapped : (S*)h->stage, h->d_bad);
+  if (e == cudaSuccess && !mapped)
+    e = cudaMemcpyAsync(EH, h->stage, 6 * h->Nc * sizeof(S), cudaMemcpyDeviceToHost, h->stream);
+  int bad = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, h->d_bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, name);
+  if (t) *t = h->t_host + (double)h->steps_host * h->dt;
+  adi_status ds = check_device_status(h, name);
+  if (ds != ADI_OK) return ds;
+  if (bad) return fail(h, ADI_ENUMERIC, std::string(name) + ": NaN or Inf in the state");
+  return ADI_OK;
+}
+
+extern "C" {
+
+adi_status adi_set_fields(adi_handle h, const double* EH, double t) {
+  return set_fields_impl<double>(h, EH, t, "adi_set_fields");
+}
+
+adi_status adi_set_fields_f32(adi_handle h, const float* EH, double t) {
+  return set_fields_impl<float>(h, EH, t, "adi_set_fields_f32");
 }
 
 adi_status adi_set_source(adi_handle h, double x0, double y0, double z0, int comp, double amp, double f0,
@@ -506,25 +551,9 @@ adi_status adi_wait_selftest(adi_handle h, int which, int budget) {
   return ADI_OK;
 }
 
-adi_status adi_fields(adi_handle h, double* EH, double* t) {
-  if (!h) return fail(nullptr, ADI_EINVAL, "adi_fields: NULL handle");
-  if (!EH) return fail(h, ADI_EINVAL, "adi_fields: EH is NULL");
-  // a page-locked EH is written directly by the kernel, other memory through the staging buffer
-  double* mapped = const_cast<double*>(static_cast<const double*>(mapped_host(EH)));
-  cudaError_t e = cudaMemsetAsync(h->d_bad, 0, sizeof(int), h->stream);
-  if (e == cudaSuccess) e = adi::get_fields_dev(*h, mapped ? mapped : (double*)h->stage, h->d_bad);
-  if (e == cudaSuccess && !mapped)
-    e = cudaMemcpyAsync(EH, h->stage, 6 * h->Nc * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
-  int bad = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, h->d_bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  if (e != cudaSuccess) return cuda_fail(h, e, "adi_fields");
-  if (t) *t = h->t_host + (double)h->steps_host * h->dt;
-  adi_status ds = check_device_status(h, "adi_fields");
-  if (ds != ADI_OK) return ds;
-  if (bad) return fail(h, ADI_ENUMERIC, "adi_fields: NaN or Inf in the state");
-  return ADI_OK;
-}
+adi_status adi_fields(adi_handle h, double* EH, double* t) { return fields_impl<double>(h, EH, t, "adi_fields"); }
+
+adi_status adi_fields_f32(adi_handle h, float* EH, double* t) { return fields_impl<float>(h, EH, t, "adi_fields_f32"); }
 
 adi_status adi_fields_device(adi_handle h, void* dev_ptr, void* stream) {
   if (!h) return fail(nullptr, ADI_EINVAL, "adi_fields_device: NULL handle");

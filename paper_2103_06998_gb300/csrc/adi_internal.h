@@ -270,13 +270,18 @@ cudaError_t compute_coefficients(Ctx& c);
 cudaError_t run_substep(Ctx& c, int which);
 // one time step (run_substep 4 then 5): the same arrays, bit for bit, as 0..3 in turn
 cudaError_t run_step(Ctx& c);
-cudaError_t set_fields_dev(Ctx& c, const double* d_src);
-// convert 6 N_c doubles at d_src (device memory or mapped host memory) into the six
+// S = double or float: the element type of the dense 6 N_c layout on the host side
+template <typename S>
+cudaError_t set_fields_dev(Ctx& c, const S* d_src);
+// convert 6 N_c values at d_src (device memory or mapped host memory) into the six
 // arrays dst (state layout, constrained coefficients zero); d_bad (optional) |= 1 on NaN/Inf
-cudaError_t set_fields_into(Ctx& c, const double* d_src, void* const* dst, int* d_bad);
-cudaError_t get_fields_dev(Ctx& c, double* d_dst, int* d_bad);
-// d_bad |= 1 if any of the n doubles at d_src is NaN or Inf
-cudaError_t check_finite_dev(Ctx& c, const double* d_src, long long n, int* d_bad);
+template <typename S>
+cudaError_t set_fields_into(Ctx& c, const S* d_src, void* const* dst, int* d_bad);
+template <typename S>
+cudaError_t get_fields_dev(Ctx& c, S* d_dst, int* d_bad);
+// d_bad |= 1 if any of the n values at d_src is NaN or Inf
+template <typename S>
+cudaError_t check_finite_dev(Ctx& c, const S* d_src, long long n, int* d_bad);
 cudaError_t set_clock(Ctx& c, double t0);
 // squared-norm sums of the state into d_acc[6] (zeroed first):
 // [int |E|^2, int |H|^2, int |grad E|^2, int |grad H|^2, int |curl E|^2, int |curl H|^2]

@@ -2643,46 +2643,123 @@ __device__ __forceinline__ bool constrained(int comp, int i, int j, int k, int N
   }
 }
 
-// src may be host memory mapped into the device address space; bad (optional)
-// receives 1 if any source value is NaN or Inf
-template <typename T>
-__global__ void set_fields_kernel(const double* __restrict__ src, T* d0, T* d1, T* d2, T* d3, T* d4, T* d5,
-                                  int Nx, int Ny, int Nz, int pitch, int* bad) {
-  const long long Nc = (long long)Nx * Ny * Nz;
+// Flat element g of the dense host layout (component, then z, y, x) and its
+// successor.
+__device__ __forceinline__ void flat_pos(long long g, long long Nc, int Nx, int Ny, int& comp, int& i, int& j, int& k) {
+  comp = (int)(g / Nc);
+  const long long r = g - comp * Nc, jk = r / Nx;
+  i = (int)(r - jk * Nx);
+  k = (int)(jk / Ny);
+  j = (int)(jk - (long long)k * Ny);
+}
+__device__ __forceinline__ void flat_next(int& comp, int& i, int& j, int& k, int Nx, int Ny, int Nz) {
+  if (++i == Nx) {
+    i = 0;
+    if (++j == Ny) {
+      j = 0;
+      if (++k == Nz) {
+        k = 0;
+        ++comp;
+      }
+    }
+  }
+}
+
+// V consecutive elements of type S as one 16-byte access (V = 1: scalar)
+template <typename S, int V>
+struct Vec;
+template <typename S>
+struct Vec<S, 1> {
+  static __device__ __forceinline__ void ld(const S* p, S (&e)[1]) { e[0] = p[0]; }
+  static __device__ __forceinline__ void st(S* p, const S (&e)[1]) { p[0] = e[0]; }
+};
+template <>
+struct Vec<float, 4> {
+  static __device__ __forceinline__ void ld(const float* p, float (&e)[4]) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    e[0] = v.x, e[1] = v.y, e[2] = v.z, e[3] = v.w;
+  }
+  static __device__ __forceinline__ void st(float* p, const float (&e)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(e[0], e[1], e[2], e[3]);
+  }
+};
+template <>
+struct Vec<double, 2> {
+  static __device__ __forceinline__ void ld(const double* p, double (&e)[2]) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    e[0] = v.x, e[1] = v.y;
+  }
+  static __device__ __forceinline__ void st(double* p, const double (&e)[2]) {
+    *reinterpret_cast<double2*>(p) = make_double2(e[0], e[1]);
+  }
+};
+
+// Dense host layout (src, element type S; may be host memory mapped into the
+// device address space, read V elements per access) -> the pitched state
+// (element type T), zeroing the coefficients fixed by the boundary conditions;
+// bad (optional) receives 1 if any source value is NaN or Inf.
+template <typename S, typename T, int V>
+__global__ void set_fields_kernel(const S* __restrict__ src, T* d0, T* d1, T* d2, T* d3, T* d4, T* d5, int Nx, int Ny,
+                                  int Nz, int pitch, int* bad) {
+  const long long Nc = (long long)Nx * Ny * Nz, n = 6 * Nc, nv = n / V;
   T* dst[6] = {d0, d1, d2, d3, d4, d5};
   int local_bad = 0;
-  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < 6 * Nc;
-       g += (long long)gridDim.x * blockDim.x) {
-    int comp = (int)(g / Nc);
-    long long r = g % Nc;
-    int i = (int)(r % Nx), j = (int)((r / Nx) % Ny), k = (int)(r / ((long long)Nx * Ny));
-    double v = src[g];
-    if (!isfinite(v)) local_bad = 1;
-    dst[comp][((long long)k * Ny + j) * pitch + i] = constrained(comp, i, j, k, Nx, Ny, Nz) ? T(0) : T(v);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nv + (n - nv * V); v += stride) {
+    // vectors first, then the (fewer than V) remaining elements one by one
+    const bool vec = v < nv;
+    const long long g = vec ? v * V : nv * V + (v - nv);
+    int comp, i, j, k;
+    flat_pos(g, Nc, Nx, Ny, comp, i, j, k);
+    S e[V];
+    if (vec) {
+      Vec<S, V>::ld(src + g, e);
+    } else {
+      e[0] = src[g];
+    }
+#pragma unroll
+    for (int u = 0; u < V; ++u) {
+      if (!vec && u > 0) break;
+      if (!isfinite(e[u])) local_bad = 1;
+      dst[comp][((long long)k * Ny + j) * pitch + i] = constrained(comp, i, j, k, Nx, Ny, Nz) ? T(0) : T(e[u]);
+      flat_next(comp, i, j, k, Nx, Ny, Nz);
+    }
   }
   if (bad && __syncthreads_or(local_bad) && threadIdx.x == 0) atomicOr(bad, 1);
 }
 
-__global__ void finite_kernel(const double* __restrict__ src, long long n, int* bad) {
+template <typename S>
+__global__ void finite_kernel(const S* __restrict__ src, long long n, int* bad) {
   int local_bad = 0;
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < n; g += (long long)gridDim.x * blockDim.x)
     if (!isfinite(src[g])) local_bad = 1;
   if (__syncthreads_or(local_bad) && threadIdx.x == 0) atomicOr(bad, 1);
 }
 
-template <typename T>
-__global__ void get_fields_kernel(double* __restrict__ dst, const T* s0, const T* s1, const T* s2, const T* s3,
+// The pitched state (T) -> the dense layout (S, possibly mapped host memory,
+// written V elements per access); bad receives 1 if any value is NaN or Inf.
+template <typename S, typename T, int V>
+__global__ void get_fields_kernel(S* __restrict__ dst, const T* s0, const T* s1, const T* s2, const T* s3,
                                   const T* s4, const T* s5, int Nx, int Ny, int Nz, int pitch, int* bad) {
   const T* src[6] = {s0, s1, s2, s3, s4, s5};
-  const long long Nc = (long long)Nx * Ny * Nz;
+  const long long Nc = (long long)Nx * Ny * Nz, n = 6 * Nc, nv = n / V;
   int local_bad = 0;
-  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < 6 * Nc;
-       g += (long long)gridDim.x * blockDim.x) {
-    const long long r = g % Nc;
-    const int i = (int)(r % Nx), j = (int)((r / Nx) % Ny), k = (int)(r / ((long long)Nx * Ny));
-    double v = (double)src[g / Nc][((long long)k * Ny + j) * pitch + i];
-    if (!isfinite(v)) local_bad = 1;
-    dst[g] = v;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nv + (n - nv * V); v += stride) {
+    const bool vec = v < nv;
+    const long long g = vec ? v * V : nv * V + (v - nv);
+    int comp, i, j, k;
+    flat_pos(g, Nc, Nx, Ny, comp, i, j, k);
+    S e[V];
+#pragma unroll
+    for (int u = 0; u < V; ++u) {
+      if (!vec && u > 0) break;
+      e[u] = (S)src[comp][((long long)k * Ny + j) * pitch + i];
+      if (!isfinite(e[u])) local_bad = 1;
+      flat_next(comp, i, j, k, Nx, Ny, Nz);
+    }
+    if (vec) Vec<S, V>::st(dst + g, e);
+    else dst[g] = e[0];
   }
   if (local_bad) atomicOr(bad, 1);
 }
@@ -3960,38 +4037,66 @@ cudaError_t run_step(Ctx& c) {
   return e == cudaSuccess ? run_substep(c, 5) : e;
 }
 
-cudaError_t set_fields_into(Ctx& c, const double* d_src, void* const* dst, int* d_bad) {
-  unsigned g = grid_for(6LL * (long long)c.Nc, 256);
-  if (c.precision == ADI_PREC_FP64) {
-    double* const* d = reinterpret_cast<double* const*>(dst);
-    set_fields_kernel<double><<<g, 256, 0, c.stream>>>(d_src, d[0], d[1], d[2], d[3], d[4], d[5], c.N[0], c.N[1], c.N[2],
-                                                        c.pitch, d_bad);
+// 16-byte accesses when the dense array starts on a 16-byte boundary
+template <typename S, typename T>
+void launch_set(Ctx& c, const S* d_src, void* const* dst, int* d_bad) {
+  constexpr int V = 16 / sizeof(S);
+  T* const* d = reinterpret_cast<T* const*>(dst);
+  const long long n = 6LL * (long long)c.Nc;
+  if ((reinterpret_cast<uintptr_t>(d_src) & 15) == 0) {
+    set_fields_kernel<S, T, V><<<grid_for(n / V + V, 256), 256, 0, c.stream>>>(d_src, d[0], d[1], d[2], d[3], d[4], d[5],
+                                                                              c.N[0], c.N[1], c.N[2], c.pitch, d_bad);
   } else {
-    float* const* d = reinterpret_cast<float* const*>(dst);
-    set_fields_kernel<float><<<g, 256, 0, c.stream>>>(d_src, d[0], d[1], d[2], d[3], d[4], d[5], c.N[0], c.N[1], c.N[2],
-                                                       c.pitch, d_bad);
+    set_fields_kernel<S, T, 1><<<grid_for(n, 256), 256, 0, c.stream>>>(d_src, d[0], d[1], d[2], d[3], d[4], d[5], c.N[0],
+                                                                      c.N[1], c.N[2], c.pitch, d_bad);
   }
-  return cudaGetLastError();
 }
-
-cudaError_t set_fields_dev(Ctx& c, const double* d_src) { return set_fields_into(c, d_src, c.cur, nullptr); }
-
-cudaError_t check_finite_dev(Ctx& c, const double* d_src, long long n, int* d_bad) {
-  finite_kernel<<<grid_for(n, 256), 256, 0, c.stream>>>(d_src, n, d_bad);
-  return cudaGetLastError();
-}
-
-cudaError_t get_fields_dev(Ctx& c, double* d_dst, int* d_bad) {
-  unsigned g = grid_for(6LL * (long long)c.Nc, 256);
-  if (c.precision == ADI_PREC_FP64) {
-    double** s = reinterpret_cast<double**>(c.cur);
-    get_fields_kernel<double><<<g, 256, 0, c.stream>>>(d_dst, s[0], s[1], s[2], s[3], s[4], s[5], c.N[0], c.N[1], c.N[2], c.pitch, d_bad);
+template <typename S, typename T>
+void launch_get(Ctx& c, S* d_dst, int* d_bad) {
+  constexpr int V = 16 / sizeof(S);
+  T** s = reinterpret_cast<T**>(c.cur);
+  const long long n = 6LL * (long long)c.Nc;
+  if ((reinterpret_cast<uintptr_t>(d_dst) & 15) == 0) {
+    get_fields_kernel<S, T, V><<<grid_for(n / V + V, 256), 256, 0, c.stream>>>(d_dst, s[0], s[1], s[2], s[3], s[4], s[5],
+                                                                              c.N[0], c.N[1], c.N[2], c.pitch, d_bad);
   } else {
-    float** s = reinterpret_cast<float**>(c.cur);
-    get_fields_kernel<float><<<g, 256, 0, c.stream>>>(d_dst, s[0], s[1], s[2], s[3], s[4], s[5], c.N[0], c.N[1], c.N[2], c.pitch, d_bad);
+    get_fields_kernel<S, T, 1><<<grid_for(n, 256), 256, 0, c.stream>>>(d_dst, s[0], s[1], s[2], s[3], s[4], s[5], c.N[0],
+                                                                      c.N[1], c.N[2], c.pitch, d_bad);
   }
+}
+
+template <typename S>
+cudaError_t set_fields_into(Ctx& c, const S* d_src, void* const* dst, int* d_bad) {
+  if (c.precision == ADI_PREC_FP64) launch_set<S, double>(c, d_src, dst, d_bad);
+  else launch_set<S, float>(c, d_src, dst, d_bad);
   return cudaGetLastError();
 }
+template cudaError_t set_fields_into<double>(Ctx&, const double*, void* const*, int*);
+template cudaError_t set_fields_into<float>(Ctx&, const float*, void* const*, int*);
+
+template <typename S>
+cudaError_t set_fields_dev(Ctx& c, const S* d_src) {
+  return set_fields_into<S>(c, d_src, c.cur, nullptr);
+}
+template cudaError_t set_fields_dev<double>(Ctx&, const double*);
+template cudaError_t set_fields_dev<float>(Ctx&, const float*);
+
+template <typename S>
+cudaError_t check_finite_dev(Ctx& c, const S* d_src, long long n, int* d_bad) {
+  finite_kernel<S><<<grid_for(n, 256), 256, 0, c.stream>>>(d_src, n, d_bad);
+  return cudaGetLastError();
+}
+template cudaError_t check_finite_dev<double>(Ctx&, const double*, long long, int*);
+template cudaError_t check_finite_dev<float>(Ctx&, const float*, long long, int*);
+
+template <typename S>
+cudaError_t get_fields_dev(Ctx& c, S* d_dst, int* d_bad) {
+  if (c.precision == ADI_PREC_FP64) launch_get<S, double>(c, d_dst, d_bad);
+  else launch_get<S, float>(c, d_dst, d_bad);
+  return cudaGetLastError();
+}
+template cudaError_t get_fields_dev<double>(Ctx&, double*, int*);
+template cudaError_t get_fields_dev<float>(Ctx&, float*, int*);
 
 cudaError_t make_tensor_maps(Ctx& c) {
   void* fn = nullptr;

@@ -14,7 +14,7 @@ HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.j
 def _declared():
     txt = "".join(open(h).read() for h in HEADERS)
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(adi_[a-z_]+)\s*\(", txt)))
+    return sorted(set(re.findall(r"\b(adi_[a-z0-9_]+)\s*\(", txt)))
 
 
 @pytest.fixture(scope="module")
