@@ -1,7 +1,16 @@
 """Host transfers through the C-ABI: page-locked host buffers (read and written
 by the kernels directly) and pageable ones (staged through a copy) give the
 same state and the same read-back bit for bit; a NaN in a page-locked buffer is
-rejected with ADI_ENUMERIC and leaves the state unchanged."""
+rejected with ADI_ENUMERIC and leaves the state unchanged.
+
+The float forms (adi_set_fields_f32 / adi_fields_f32) against the double ones:
+the FP32 state set from floats equals the state set from the same values as
+doubles, reading back as floats returns exactly the FP32 state, the
+coefficients fixed by the boundary conditions come back zero, 16-byte aligned
+and unaligned host pointers take the vector and the scalar kernels with the same
+result, pointers off their element alignment are refused on the host, and an
+FP64 handle round-trips floats exactly.
+"""
 import numpy as np
 import pytest
 
@@ -43,4 +52,127 @@ def test_pinned_and_pageable_agree(prec):
     assert e.value.status == adi.ADI_ENUMERIC
     a2, t2 = s.fields()
     assert np.array_equal(a2, a1) and t2 == t1
+    s.close()
+
+
+N, P = (37, 29, 23), 2  # 6 N_c is not a multiple of 4: the vector kernels' scalar tail runs
+
+
+def _solver(prec):
+    from paper_2103_06998_gb300 import adi
+    s = adi.Solver(N, P, 0.01, precision=prec)
+    s.factor()
+    return s
+
+
+def _pinned(nbytes):
+    torch = pytest.importorskip("torch")
+    return torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+
+
+def _constrained(shape):
+    """Mask of the coefficients the boundary conditions fix to zero (6, Nz, Ny, Nx)."""
+    nz, ny, nx = shape
+    m = np.zeros((6,) + shape, dtype=bool)
+    for c in range(6):
+        axes = [a for a in range(3) if a != c] if c < 3 else [c - 3]
+        for a in axes:  # a = 0: x, 1: y, 2: z
+            sl = [slice(None)] * 3
+            for end in (0, -1):
+                sl[2 - a] = end
+                m[(c,) + tuple(sl)] = True
+                sl[2 - a] = slice(None)
+    return m
+
+
+def _view(buf, dtype, count, offset=0):
+    return np.frombuffer(buf.numpy(), dtype=np.uint8)[offset:offset + count * np.dtype(dtype).itemsize].view(dtype)
+
+
+@pytest.mark.parametrize("offset", [0, 4])
+def test_float_transfers_equal_double_transfers(offset):
+    s = _solver("fp32")
+    st = inputs.random_fields(s.shape, 21).astype(np.float32)
+    n = st.size
+    buf = _pinned(n * 4 + 16)
+    a = _view(buf, np.float32, n, offset)  # offset 4: not 16-byte aligned (scalar kernels)
+    a[:] = st.ravel()
+    s.set_fields_f32_ptr(a.ctypes.data, 0.5)
+    got64, t = s.fields()
+    assert t == 0.5
+    ref = st.astype(np.float64)
+    ref[_constrained(s.shape)] = 0.0
+    assert np.array_equal(got64, ref)
+    # pageable floats, and doubles of the same values: the same state
+    r = _solver("fp32")
+    r.set_fields(st.astype(np.float64), 0.5)
+    assert np.array_equal(r.fields()[0], got64)
+    pg = np.ascontiguousarray(st.ravel())
+    r.set_fields_f32_ptr(pg.ctypes.data, 0.5)
+    assert np.array_equal(r.fields()[0], got64)
+    # reading back as floats: pinned (aligned or not) and pageable
+    out = _view(_pinned(n * 4 + 16), np.float32, n, offset)
+    s.fields_f32_ptr(out.ctypes.data)
+    assert np.array_equal(out.astype(np.float64), got64.ravel())
+    out2 = np.empty(n, dtype=np.float32)
+    s.fields_f32_ptr(out2.ctypes.data)
+    assert np.array_equal(out2, out)
+    # doubles into pinned memory, 16-byte aligned or only 8-byte aligned
+    d = _view(_pinned(n * 8 + 16), np.float64, n, 2 * offset)
+    s.fields_ptr(d.ctypes.data)
+    assert np.array_equal(d, got64.ravel())
+    s.close()
+    r.close()
+
+
+def test_misaligned_pointers_are_rejected_on_the_host():
+    # a double* or float* off its element alignment is refused before any device
+    # work (a device access through it would fault)
+    from paper_2103_06998_gb300 import adi
+    s = _solver("fp32")
+    buf = np.zeros(6 * int(np.prod(s.shape)) * 8 + 16, dtype=np.uint8)
+    base = buf.ctypes.data
+    for call in (lambda p: s.set_fields_ptr(p, 0.0), lambda p: s.fields_ptr(p)):
+        with pytest.raises(adi.AdiError) as e:
+            call(base + (8 - base % 8) + 4)
+        assert e.value.status == adi.ADI_EINVAL
+    for call in (lambda p: s.set_fields_f32_ptr(p, 0.0), lambda p: s.fields_f32_ptr(p)):
+        with pytest.raises(adi.AdiError) as e:
+            call(base + (4 - base % 4) + 2)
+        assert e.value.status == adi.ADI_EINVAL
+    s.close()
+
+
+def test_float_nan_is_rejected_and_state_kept():
+    from paper_2103_06998_gb300 import adi
+    s = _solver("fp32")
+    st = inputs.random_fields(s.shape, 23).astype(np.float32)
+    s.set_fields_f32_ptr(np.ascontiguousarray(st.ravel()).ctypes.data, 1.0)
+    before, _ = s.fields()
+    bad = st.copy().ravel()
+    bad[bad.size // 2 + 1] = np.nan
+    for ptr in (np.ascontiguousarray(bad).ctypes.data,):
+        with pytest.raises(adi.AdiError) as e:
+            s.set_fields_f32_ptr(ptr, 2.0)
+        assert e.value.status == adi.ADI_ENUMERIC
+    buf = _pinned(bad.size * 4)
+    a = _view(buf, np.float32, bad.size)
+    a[:] = bad
+    with pytest.raises(adi.AdiError) as e:
+        s.set_fields_f32_ptr(a.ctypes.data, 2.0)
+    assert e.value.status == adi.ADI_ENUMERIC
+    after, t = s.fields()
+    assert t == 1.0 and np.array_equal(after, before)
+    s.close()
+
+
+def test_fp64_handle_round_trips_floats():
+    s = _solver("fp64")
+    st = inputs.random_fields(s.shape, 24).astype(np.float32)
+    s.set_fields_f32_ptr(np.ascontiguousarray(st.ravel()).ctypes.data, 0.0)
+    out = np.empty(st.size, dtype=np.float32)
+    s.fields_f32_ptr(out.ctypes.data)
+    ref = st.copy()
+    ref[_constrained(s.shape)] = 0.0
+    assert np.array_equal(out, ref.ravel())
     s.close()
