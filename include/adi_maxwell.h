@@ -182,6 +182,28 @@ adi_status adi_fields(adi_handle h, double* EH, double* t);
 adi_status adi_set_fields_f32(adi_handle h, const float* EH, double t);
 adi_status adi_fields_f32(adi_handle h, float* EH, double* t);
 
+/* Asynchronous host transfers, for loops that keep the host link busy while
+ * the GPU steps (for example a service that sets a state, steps it and reads it
+ * back, over and over).  EH must be page-locked host memory (pinned or
+ * registered) aligned to elem_bytes (4: floats, 8: doubles; the layout of
+ * adi_set_fields); else ADI_EINVAL.  Neither call waits: the caller leaves EH
+ * unchanged (set) or unread (read) until adi_sync returns.
+ *   adi_set_fields_async converts EH into scratch memory on an input stream of
+ *   the handle as soon as the steps enqueued before it are done with that
+ *   scratch, then commits it to the state, with the time t, after everything
+ *   enqueued on the handle before the call.  A NaN or Inf in EH leaves the
+ *   state and its device clock unchanged (the handle's host-side time follows
+ *   the call regardless) and makes the next adi_sync return ADI_ENUMERIC.
+ *   adi_fields_async writes the state into EH on an output stream after
+ *   everything enqueued before it; a NaN or Inf makes the next adi_sync return
+ *   ADI_ENUMERIC (the data are still written).
+ * Everything enqueued on the handle after either call is ordered after it.  In
+ * the sequence set, step, read, set, step, read, ... each read runs at the same
+ * time as the conversion of the next set (the two directions of the host link).
+ * No counterpart in the paper. */
+adi_status adi_set_fields_async(adi_handle h, const void* EH, int elem_bytes, double t);
+adi_status adi_fields_async(adi_handle h, void* EH, int elem_bytes);
+
 /* Copy the state, in the working precision (float or double as created), to
  * 6 N_c elements of device memory at dev_ptr, on cuda_stream (NULL = the
  * handle's stream).  Asynchronous. */
@@ -293,11 +315,13 @@ adi_status adi_batch_autotune(adi_batch b, const char* cache_path);
 /* Release the batch and all its instances.  NULL is ignored. */
 void adi_batch_destroy(adi_batch b);
 
-/* Block until all work on the handle's stream is done.  Returns ADI_ETIMEOUT
+/* Block until all work on the handle's streams is done.  Returns ADI_ETIMEOUT
  * when a bounded device wait of a kernel gave up since the last report (an
  * asynchronous copy was not delivered within its iteration limit; the kernel
  * left its results unwritten and returned instead of hanging); the status is
- * reported once and then cleared.  adi_fields reports it the same way. */
+ * reported once and then cleared.  adi_fields reports it the same way.  Then
+ * ADI_ENUMERIC when an asynchronous transfer since the last report met a NaN
+ * or Inf (reported once). */
 adi_status adi_sync(adi_handle h);
 
 /* Diagnostic (not in the paper): run one of the kernels' bounded waits on a

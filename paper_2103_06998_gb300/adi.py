@@ -20,7 +20,7 @@ _PREC = {"fp64": PREC_FP64, "fp32": PREC_FP32, "mixed": PREC_MIXED}
 # every symbol declared in include/adi_maxwell.h
 EXPORTS = ("adi_create", "adi_create_knots", "adi_factor", "adi_set_dt", "adi_set_stream", "adi_set_fields",
            "adi_set_fields_f32", "adi_set_source", "adi_step", "adi_substep", "adi_fields", "adi_fields_f32",
-           "adi_fields_device",
+           "adi_fields_device", "adi_set_fields_async", "adi_fields_async",
            "adi_cfl_dt", "adi_cfl_dt_noalloc", "adi_sync", "adi_wait_selftest", "adi_norms", "adi_plane", "adi_set_profiling", "adi_kernel_stats", "adi_dims",
            "adi_destroy", "adi_last_error", "adi_status_string", "adi_set_line_tile",
            "adi_batch_create", "adi_batch_set_stream", "adi_batch_handle", "adi_batch_factor", "adi_batch_step", "adi_batch_sync",
@@ -76,6 +76,8 @@ def load_library(path=LIB_PATH):
         "adi_substep": (I, [H, I]),
         "adi_fields": (I, [H, P(D), P(D)]),
         "adi_fields_f32": (I, [H, ctypes.c_void_p, P(D)]),
+        "adi_set_fields_async": (I, [H, ctypes.c_void_p, I, D]),
+        "adi_fields_async": (I, [H, ctypes.c_void_p, I]),
         "adi_fields_device": (I, [H, ctypes.c_void_p, ctypes.c_void_p]),
         "adi_cfl_dt": (D, [H]),
         "adi_cfl_dt_noalloc": (I, [I, I, I, I, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, P(D)]),
@@ -238,6 +240,14 @@ class Solver:
         t = ctypes.c_double()
         self._check(self._lib.adi_fields_f32(self.h, ctypes.c_void_p(int(host_ptr)), ctypes.byref(t)))
         return t.value
+
+    def set_fields_async_ptr(self, host_ptr, elem_bytes, t=0.0):
+        """Asynchronous set from page-locked host memory (6 N_c floats or doubles)."""
+        self._check(self._lib.adi_set_fields_async(self.h, ctypes.c_void_p(int(host_ptr)), int(elem_bytes), float(t)))
+
+    def fields_async_ptr(self, host_ptr, elem_bytes):
+        """Asynchronous read into page-locked host memory; valid after sync()."""
+        self._check(self._lib.adi_fields_async(self.h, ctypes.c_void_p(int(host_ptr)), int(elem_bytes)))
 
     def fields_device(self, dev_ptr, stream_ptr=0):
         self._check(self._lib.adi_fields_device(self.h, ctypes.c_void_p(int(dev_ptr)), ctypes.c_void_p(int(stream_ptr))))

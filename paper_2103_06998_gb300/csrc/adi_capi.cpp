@@ -37,7 +37,7 @@ void free_ctx(Ctx* c0) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   for (auto* l : c->pending) delete l;
   void* ptrs[] = {c->d_eps,        c->d_mu,  c->d_sigma, c->stage,  c->tab,   c->tab64, c->tabff, c->tabq,
-                  c->d_clock_t0,   c->d_clock_step, c->d_err, c->d_bad, c->d_diag};
+                  c->d_clock_t0,   c->d_clock_step, c->d_err, c->d_bad, c->d_diag, c->d_async};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int i = 0; i < 6; ++i) {
@@ -54,6 +54,10 @@ void free_ctx(Ctx* c0) {
       if (c->stiff_fac[i][m]) cudaFree(c->stiff_fac[i][m]);
   }
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  for (cudaStream_t st : {c->io_in, c->io_out})
+    if (st) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : {c->ev_step, c->ev_set, c->ev_get, c->ev_src})
+    if (ev) cudaEventDestroy(ev);
   for (int i = 0; i < 3; ++i) {
     if (c->branch[i]) cudaStreamDestroy(c->branch[i]);
     if (c->ev_join[i]) cudaEventDestroy(c->ev_join[i]);
@@ -256,6 +260,10 @@ static adi_status create_impl(int nx, int ny, int nz, int p, double dt, const do
   for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&c->branch[i], cudaStreamNonBlocking);
   for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&c->ev_join[i], cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->io_in, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->io_out, cudaStreamNonBlocking);
+  for (cudaEvent_t* ev : {&c->ev_step, &c->ev_set, &c->ev_get, &c->ev_src})
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     free_ctx(c);
     return cuda_fail(nullptr, e, "adi_create: branch streams");
@@ -278,6 +286,7 @@ static adi_status create_impl(int nx, int ny, int nz, int p, double dt, const do
   alloc((void**)&c->d_clock_step, sizeof(long long));
   alloc((void**)&c->d_err, sizeof(int));
   alloc((void**)&c->d_bad, sizeof(int));
+  alloc((void**)&c->d_async, 4 * sizeof(int));
   alloc((void**)&c->d_diag, 8 * sizeof(double));
   if (!ok) {
     cudaGetLastError();
@@ -326,6 +335,7 @@ static adi_status create_impl(int nx, int ny, int nz, int p, double dt, const do
   }
   if (e == cudaSuccess) e = adi::set_clock(*c, 0.0);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_async, 0, 4 * sizeof(int), c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
     free_ctx(c);
@@ -360,7 +370,9 @@ adi_status adi_set_dt(adi_handle h, double dt) {
 
 adi_status adi_set_stream(adi_handle h, void* s) {
   if (!h) return fail(nullptr, ADI_EINVAL, "adi_set_stream: NULL handle");
-  cudaError_t e = cudaStreamSynchronize(h->stream);
+  cudaError_t e = cudaStreamSynchronize(h->stream);  // (its waits cover pending asynchronous transfers)
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->io_in);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->io_out);
   if (e != cudaSuccess) return cuda_fail(h, e, "adi_set_stream");
   if (h->own_stream) cudaStreamDestroy(h->stream);
   h->own_stream = false;
@@ -513,6 +525,8 @@ adi_status adi_step(adi_handle h, int n) {
     if (e != cudaSuccess) return cuda_fail(h, e, "adi_step");
     h->steps_host += 1;
   }
+  cudaError_t e = cudaEventRecord(h->ev_step, h->stream);  // the scratch arrays are free after this
+  if (e != cudaSuccess) return cuda_fail(h, e, "adi_step");
   return ADI_OK;
 }
 
@@ -521,6 +535,7 @@ adi_status adi_substep(adi_handle h, int which) {
   if (which < 0 || which > 3) return fail(h, ADI_EINVAL, "adi_substep: which must be 0..3");
   if (!h->factored) return fail(h, ADI_ESTATE, "adi_substep: call adi_factor first");
   cudaError_t e = adi::run_substep(*h, which);
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev_step, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "adi_substep");
   if (which == 3) h->steps_host += 1;
   return ADI_OK;
@@ -637,9 +652,91 @@ double adi_cfl_dt(adi_handle h) {
 
 adi_status adi_sync(adi_handle h) {
   if (!h) return fail(nullptr, ADI_EINVAL, "adi_sync: NULL handle");
-  cudaError_t e = cudaStreamSynchronize(h->stream);
+  cudaError_t e = cudaStreamSynchronize(h->io_in);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->io_out);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "adi_sync");
-  return check_device_status(h, "adi_sync");
+  adi_status ds = check_device_status(h, "adi_sync");
+  if (ds != ADI_OK) return ds;
+  // outcomes of the asynchronous transfers since the last report (then cleared)
+  int fl[4] = {0, 0, 0, 0};
+  e = cudaMemcpy(fl, h->d_async, sizeof(fl), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && (fl[1] || fl[2])) e = cudaMemset(h->d_async, 0, sizeof(fl));
+  if (e != cudaSuccess) return cuda_fail(h, e, "adi_sync");
+  if (fl[1]) return fail(h, ADI_ENUMERIC, "adi_sync: a field set by adi_set_fields_async held NaN or Inf and was not applied");
+  if (fl[2]) return fail(h, ADI_ENUMERIC, "adi_sync: a state read by adi_fields_async holds NaN or Inf");
+  return ADI_OK;
+}
+
+// Blocks of an asynchronous conversion: about two per SM of 152, so that a read
+// and the next set share the GPU and both directions of the host link are busy.
+static const unsigned kAsyncBlocks = 304;
+
+// Checks shared by the asynchronous transfers: EH page-locked (its device
+// address returned) and aligned to elem_bytes = 4 or 8.
+static const void* async_host(adi_handle h, const void* EH, int elem_bytes, const char* name, adi_status* st) {
+  *st = ADI_EINVAL;
+  if (!h) {
+    fail(nullptr, ADI_EINVAL, std::string(name) + ": NULL handle");
+    return nullptr;
+  }
+  if (elem_bytes != 4 && elem_bytes != 8) {
+    fail(h, ADI_EINVAL, std::string(name) + ": elem_bytes must be 4 (float) or 8 (double)");
+    return nullptr;
+  }
+  if (!EH || reinterpret_cast<uintptr_t>(EH) % elem_bytes != 0) {
+    fail(h, ADI_EINVAL, std::string(name) + ": EH is NULL or not aligned to elem_bytes");
+    return nullptr;
+  }
+  const void* m = mapped_host(EH);
+  if (!m) fail(h, ADI_EINVAL, std::string(name) + ": EH must be page-locked host memory (pinned or registered)");
+  else *st = ADI_OK;
+  return m;
+}
+
+adi_status adi_set_fields_async(adi_handle h, const void* EH, int elem_bytes, double t) {
+  adi_status st;
+  const void* m = async_host(h, EH, elem_bytes, "adi_set_fields_async", &st);
+  if (st != ADI_OK) return st;
+  if (!std::isfinite(t)) return fail(h, ADI_EINVAL, "adi_set_fields_async: t must be finite");
+  void* scratch[6] = {h->rhs[0], h->rhs[1], h->rhs[2], h->half[0], h->half[1], h->half[2]};
+  cudaStream_t main = h->stream;
+  // convert into the scratch arrays once the last enqueued step is done with them
+  cudaError_t e = cudaStreamWaitEvent(h->io_in, h->ev_step, 0);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_async, 0, sizeof(int), h->io_in);
+  h->stream = h->io_in;
+  if (e == cudaSuccess)
+    e = elem_bytes == 4 ? adi::set_fields_into<float>(*h, static_cast<const float*>(m), scratch, h->d_async, kAsyncBlocks)
+                        : adi::set_fields_into<double>(*h, static_cast<const double*>(m), scratch, h->d_async, kAsyncBlocks);
+  // commit after everything enqueued on the handle so far (steps, reads of the state)
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev_src, main);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->io_in, h->ev_src, 0);
+  if (e == cudaSuccess) e = adi::commit_fields(*h, h->d_async, h->d_async + 1, t);
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev_set, h->io_in);
+  h->stream = main;
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(main, h->ev_set, 0);  // later work sees the new state
+  if (e != cudaSuccess) return cuda_fail(h, e, "adi_set_fields_async");
+  h->t_host = t;
+  h->steps_host = 0;
+  return ADI_OK;
+}
+
+adi_status adi_fields_async(adi_handle h, void* EH, int elem_bytes) {
+  adi_status st;
+  void* m = const_cast<void*>(async_host(h, EH, elem_bytes, "adi_fields_async", &st));
+  if (st != ADI_OK) return st;
+  cudaStream_t main = h->stream;
+  cudaError_t e = cudaEventRecord(h->ev_src, main);  // after everything enqueued so far
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->io_out, h->ev_src, 0);
+  h->stream = h->io_out;
+  if (e == cudaSuccess)
+    e = elem_bytes == 4 ? adi::get_fields_dev<float>(*h, static_cast<float*>(m), h->d_async + 2, kAsyncBlocks)
+                        : adi::get_fields_dev<double>(*h, static_cast<double*>(m), h->d_async + 2, kAsyncBlocks);
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev_get, h->io_out);
+  h->stream = main;
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(main, h->ev_get, 0);  // later steps wait for the read
+  if (e != cudaSuccess) return cuda_fail(h, e, "adi_fields_async");
+  return ADI_OK;
 }
 
 adi_status adi_set_profiling(adi_handle h, int on) {

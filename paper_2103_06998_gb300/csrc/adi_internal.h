@@ -252,6 +252,13 @@ struct Ctx {
   bool tmaps_ok = false;
   int* d_err = nullptr;  // device status word written by bounded waits
   int* d_bad = nullptr;  // device flag: a value that is not finite (field checks)
+  // asynchronous host transfers (adi_set_fields_async / adi_fields_async): an input
+  // and an output stream, events ordering them against the main stream, and flags
+  // [0] this set's values not finite, [1] a set was refused, [2] a read saw a value
+  // that is not finite (both reported by adi_sync)
+  cudaStream_t io_in = nullptr, io_out = nullptr;
+  cudaEvent_t ev_step = nullptr, ev_set = nullptr, ev_get = nullptr, ev_src = nullptr;
+  int* d_async = nullptr;
   double* d_diag = nullptr;  // 8 doubles: sums of the norm diagnostics
 
   // graph of one step
@@ -275,14 +282,18 @@ template <typename S>
 cudaError_t set_fields_dev(Ctx& c, const S* d_src);
 // convert 6 N_c values at d_src (device memory or mapped host memory) into the six
 // arrays dst (state layout, constrained coefficients zero); d_bad (optional) |= 1 on NaN/Inf
+// cap: at most that many blocks (0: no cap)
 template <typename S>
-cudaError_t set_fields_into(Ctx& c, const S* d_src, void* const* dst, int* d_bad);
+cudaError_t set_fields_into(Ctx& c, const S* d_src, void* const* dst, int* d_bad, unsigned cap = 0);
 template <typename S>
-cudaError_t get_fields_dev(Ctx& c, S* d_dst, int* d_bad);
+cudaError_t get_fields_dev(Ctx& c, S* d_dst, int* d_bad, unsigned cap = 0);
 // d_bad |= 1 if any of the n values at d_src is NaN or Inf
 template <typename S>
 cudaError_t check_finite_dev(Ctx& c, const S* d_src, long long n, int* d_bad);
 cudaError_t set_clock(Ctx& c, double t0);
+// copy the six scratch arrays (rhs, half) into the state and set the clock to t,
+// unless *bad is set (then *refused |= 1); on c.stream
+cudaError_t commit_fields(Ctx& c, const int* bad, int* refused, double t);
 // squared-norm sums of the state into d_acc[6] (zeroed first):
 // [int |E|^2, int |H|^2, int |grad E|^2, int |grad H|^2, int |curl E|^2, int |curl H|^2]
 cudaError_t field_norms_dev(Ctx& c, double* d_acc);

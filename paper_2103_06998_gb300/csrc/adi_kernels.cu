@@ -2764,6 +2764,30 @@ __global__ void get_fields_kernel(S* __restrict__ dst, const T* s0, const T* s1,
   if (local_bad) atomicOr(bad, 1);
 }
 
+// The state's six arrays from the six scratch arrays (16-byte words, n per
+// array) and the clock, only if the conversion into scratch found every value
+// finite; otherwise the refusal is recorded and nothing changes.
+struct CommitArgs {
+  const uint4* src[6];
+  uint4* dst[6];
+};
+__global__ void commit_kernel(const CommitArgs a, long long n, const int* bad, int* refused, double* t0,
+                              long long* step, double t) {
+  if (*bad) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(refused, 1);
+    return;
+  }
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 6 * n; i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i / n);
+    const long long j = i - c * n;
+    a.dst[c][j] = a.src[c][j];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *t0 = t;
+    *step = 0;
+  }
+}
+
 __global__ void clock_kernel(double* t0, long long* step, double t) {
   *t0 = t;
   *step = 0;
@@ -4038,41 +4062,47 @@ cudaError_t run_step(Ctx& c) {
 }
 
 // 16-byte accesses when the dense array starts on a 16-byte boundary
+// grid of a conversion: at most `cap` blocks (a share of the SMs, so that a set
+// and a read of the asynchronous transfers can run side by side), 0: no cap
+inline unsigned conv_grid(long long n, unsigned cap) {
+  const unsigned g = grid_for(n, 256);
+  return cap && g > cap ? cap : g;
+}
 template <typename S, typename T>
-void launch_set(Ctx& c, const S* d_src, void* const* dst, int* d_bad) {
+void launch_set(Ctx& c, const S* d_src, void* const* dst, int* d_bad, unsigned cap) {
   constexpr int V = 16 / sizeof(S);
   T* const* d = reinterpret_cast<T* const*>(dst);
   const long long n = 6LL * (long long)c.Nc;
   if ((reinterpret_cast<uintptr_t>(d_src) & 15) == 0) {
-    set_fields_kernel<S, T, V><<<grid_for(n / V + V, 256), 256, 0, c.stream>>>(d_src, d[0], d[1], d[2], d[3], d[4], d[5],
-                                                                              c.N[0], c.N[1], c.N[2], c.pitch, d_bad);
+    set_fields_kernel<S, T, V><<<conv_grid(n / V + V, cap), 256, 0, c.stream>>>(
+        d_src, d[0], d[1], d[2], d[3], d[4], d[5], c.N[0], c.N[1], c.N[2], c.pitch, d_bad);
   } else {
-    set_fields_kernel<S, T, 1><<<grid_for(n, 256), 256, 0, c.stream>>>(d_src, d[0], d[1], d[2], d[3], d[4], d[5], c.N[0],
-                                                                      c.N[1], c.N[2], c.pitch, d_bad);
+    set_fields_kernel<S, T, 1><<<conv_grid(n, cap), 256, 0, c.stream>>>(d_src, d[0], d[1], d[2], d[3], d[4], d[5], c.N[0],
+                                                                       c.N[1], c.N[2], c.pitch, d_bad);
   }
 }
 template <typename S, typename T>
-void launch_get(Ctx& c, S* d_dst, int* d_bad) {
+void launch_get(Ctx& c, S* d_dst, int* d_bad, unsigned cap) {
   constexpr int V = 16 / sizeof(S);
   T** s = reinterpret_cast<T**>(c.cur);
   const long long n = 6LL * (long long)c.Nc;
   if ((reinterpret_cast<uintptr_t>(d_dst) & 15) == 0) {
-    get_fields_kernel<S, T, V><<<grid_for(n / V + V, 256), 256, 0, c.stream>>>(d_dst, s[0], s[1], s[2], s[3], s[4], s[5],
-                                                                              c.N[0], c.N[1], c.N[2], c.pitch, d_bad);
+    get_fields_kernel<S, T, V><<<conv_grid(n / V + V, cap), 256, 0, c.stream>>>(
+        d_dst, s[0], s[1], s[2], s[3], s[4], s[5], c.N[0], c.N[1], c.N[2], c.pitch, d_bad);
   } else {
-    get_fields_kernel<S, T, 1><<<grid_for(n, 256), 256, 0, c.stream>>>(d_dst, s[0], s[1], s[2], s[3], s[4], s[5], c.N[0],
-                                                                      c.N[1], c.N[2], c.pitch, d_bad);
+    get_fields_kernel<S, T, 1><<<conv_grid(n, cap), 256, 0, c.stream>>>(d_dst, s[0], s[1], s[2], s[3], s[4], s[5], c.N[0],
+                                                                       c.N[1], c.N[2], c.pitch, d_bad);
   }
 }
 
 template <typename S>
-cudaError_t set_fields_into(Ctx& c, const S* d_src, void* const* dst, int* d_bad) {
-  if (c.precision == ADI_PREC_FP64) launch_set<S, double>(c, d_src, dst, d_bad);
-  else launch_set<S, float>(c, d_src, dst, d_bad);
+cudaError_t set_fields_into(Ctx& c, const S* d_src, void* const* dst, int* d_bad, unsigned cap) {
+  if (c.precision == ADI_PREC_FP64) launch_set<S, double>(c, d_src, dst, d_bad, cap);
+  else launch_set<S, float>(c, d_src, dst, d_bad, cap);
   return cudaGetLastError();
 }
-template cudaError_t set_fields_into<double>(Ctx&, const double*, void* const*, int*);
-template cudaError_t set_fields_into<float>(Ctx&, const float*, void* const*, int*);
+template cudaError_t set_fields_into<double>(Ctx&, const double*, void* const*, int*, unsigned);
+template cudaError_t set_fields_into<float>(Ctx&, const float*, void* const*, int*, unsigned);
 
 template <typename S>
 cudaError_t set_fields_dev(Ctx& c, const S* d_src) {
@@ -4090,13 +4120,13 @@ template cudaError_t check_finite_dev<double>(Ctx&, const double*, long long, in
 template cudaError_t check_finite_dev<float>(Ctx&, const float*, long long, int*);
 
 template <typename S>
-cudaError_t get_fields_dev(Ctx& c, S* d_dst, int* d_bad) {
-  if (c.precision == ADI_PREC_FP64) launch_get<S, double>(c, d_dst, d_bad);
-  else launch_get<S, float>(c, d_dst, d_bad);
+cudaError_t get_fields_dev(Ctx& c, S* d_dst, int* d_bad, unsigned cap) {
+  if (c.precision == ADI_PREC_FP64) launch_get<S, double>(c, d_dst, d_bad, cap);
+  else launch_get<S, float>(c, d_dst, d_bad, cap);
   return cudaGetLastError();
 }
-template cudaError_t get_fields_dev<double>(Ctx&, double*, int*);
-template cudaError_t get_fields_dev<float>(Ctx&, float*, int*);
+template cudaError_t get_fields_dev<double>(Ctx&, double*, int*, unsigned);
+template cudaError_t get_fields_dev<float>(Ctx&, float*, int*, unsigned);
 
 cudaError_t make_tensor_maps(Ctx& c) {
   void* fn = nullptr;
@@ -4118,6 +4148,18 @@ cudaError_t wait_selftest(Ctx& c, int which, int budget) {
 
 cudaError_t set_clock(Ctx& c, double t0) {
   clock_kernel<<<1, 1, 0, c.stream>>>(c.d_clock_t0, c.d_clock_step, t0);
+  return cudaGetLastError();
+}
+
+cudaError_t commit_fields(Ctx& c, const int* bad, int* refused, double t) {
+  CommitArgs a;
+  void* scratch[6] = {c.rhs[0], c.rhs[1], c.rhs[2], c.half[0], c.half[1], c.half[2]};
+  for (int i = 0; i < 6; ++i) {
+    a.src[i] = reinterpret_cast<const uint4*>(scratch[i]);
+    a.dst[i] = reinterpret_cast<uint4*>(c.cur[i]);
+  }
+  const long long n = (long long)(c.Np * c.esize / 16);  // pitch is a multiple of 4 elements
+  commit_kernel<<<grid_for(6 * n, 256), 256, 0, c.stream>>>(a, n, bad, refused, c.d_clock_t0, c.d_clock_step, t);
   return cudaGetLastError();
 }
 

@@ -176,3 +176,73 @@ def test_fp64_handle_round_trips_floats():
     ref[_constrained(s.shape)] = 0.0
     assert np.array_equal(out, ref.ravel())
     s.close()
+
+
+# ---- asynchronous transfers: set, step, read, set, step, read, ... without waiting
+@pytest.mark.parametrize("prec,elem", [("fp32", 4), ("fp32", 8), ("fp64", 8)])
+def test_async_pipeline_equals_synchronous_calls(prec, elem):
+    dt = np.float32 if elem == 4 else np.float64
+    a, b = _solver(prec), _solver(prec)
+    a.set_source((0.4, 0.55, 0.3), 2, 3.0, 2.0, 0.2, 0.3)
+    b.set_source((0.4, 0.55, 0.3), 2, 3.0, 2.0, 0.2, 0.3)
+    n = 6 * int(np.prod(a.shape))
+    ins, outs = [], []
+    for i in range(3):
+        x = _view(_pinned(n * elem), dt, n)
+        x[:] = inputs.random_fields(a.shape, 30 + i).ravel().astype(dt)
+        ins.append(x)
+        outs.append(_view(_pinned(n * elem), dt, n))
+    for i in range(3):  # no synchronisation inside the loop
+        a.set_fields_async_ptr(ins[i].ctypes.data, elem, 0.25 * i)
+        a.step(2)
+        a.fields_async_ptr(outs[i].ctypes.data, elem)
+    a.sync()
+    for i in range(3):
+        b.set_fields(ins[i].astype(np.float64), 0.25 * i)
+        b.step(2)
+        ref, t = b.fields()
+        assert np.array_equal(outs[i], ref.ravel().astype(dt)), i
+    assert abs(a.fields()[1] - t) < 1e-12
+    a.close()
+    b.close()
+
+
+def test_async_nan_is_refused_and_reported_once():
+    from paper_2103_06998_gb300 import adi
+    s, r = _solver("fp32"), _solver("fp32")
+    n = 6 * int(np.prod(s.shape))
+    good = _view(_pinned(n * 4), np.float32, n)
+    good[:] = inputs.random_fields(s.shape, 40).ravel()
+    bad = _view(_pinned(n * 4), np.float32, n)
+    bad[:] = good
+    bad[n // 3] = np.inf
+    for x in (s, r):
+        x.set_fields_f32_ptr(good.ctypes.data, 0.0)
+        x.step(1)
+    s.set_fields_async_ptr(bad.ctypes.data, 4, 5.0)  # refused on the device
+    s.step(1)
+    with pytest.raises(adi.AdiError) as e:
+        s.sync()
+    assert e.value.status == adi.ADI_ENUMERIC
+    s.sync()  # reported once
+    r.step(1)  # the reference never saw the refused set
+    assert np.array_equal(s.fields()[0], r.fields()[0])
+    s.close()
+    r.close()
+
+
+def test_async_transfers_need_page_locked_aligned_memory():
+    from paper_2103_06998_gb300 import adi
+    s = _solver("fp32")
+    n = 6 * int(np.prod(s.shape))
+    pageable = np.zeros(n, dtype=np.float32)
+    pinned = _view(_pinned(n * 4 + 16), np.float32, n)
+    for call in (lambda: s.set_fields_async_ptr(pageable.ctypes.data, 4, 0.0),
+                 lambda: s.fields_async_ptr(pageable.ctypes.data, 4),
+                 lambda: s.set_fields_async_ptr(pinned.ctypes.data, 2, 0.0),
+                 lambda: s.fields_async_ptr(pinned.ctypes.data + 2, 4)):
+        with pytest.raises(adi.AdiError) as e:
+            call()
+        assert e.value.status == adi.ADI_EINVAL
+    s.sync()
+    s.close()
