@@ -668,9 +668,9 @@ adi_status adi_sync(adi_handle h) {
   return ADI_OK;
 }
 
-// Blocks of an asynchronous conversion: four per SM of 152 (measured best of 1, 2, 4
-// and 8 per SM at 256^3), so that a read
-// and the next set share the GPU and both directions of the host link are busy.
+// Blocks of an asynchronous conversion: four per SM of 152 (the best of 1, 2, 4 and
+// 8 per SM measured at 256^3), so that a read and the next set share the GPU and
+// both directions of the host link are busy.
 static const unsigned kAsyncBlocks = 608;
 
 // Checks shared by the asynchronous transfers: EH page-locked (its device
