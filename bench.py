@@ -171,6 +171,21 @@ def cpu_baseline(n, eps, mu, sigma, src, tau):
                       "(BLAS threads = all cores); %.1f s" % (n, dt)}
 
 
+def job_rate(local_s, units, world, device=None):
+    """Whole-job rate when this rank processed `units` in `local_s` seconds: the
+    units of all ranks over the slowest rank's time (max over ranks).  Returns
+    (rate, slowest time)."""
+    import torch
+    t = torch.tensor([float(local_s)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    s = float(t.item())
+    return float(u.item()) / s, s
+
+
 def config_of(n, tau, world):
     """The workload description shared by both arms (tau printed to 12 digits:
     each arm computes the explicit limit in its own code)."""
@@ -287,9 +302,18 @@ def batched_result(precision, steps, warmup, rank=0, local=0):
 
 
 def run_batched(args, rank, world, local):
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     r = batched_result(args.precision, args.steps, args.warmup, rank, local)
+    # each rank steps its own 48 instances: all ranks' DOF-steps over the slowest rank's time
+    value, _ = job_rate(r["ms_per_step"] * args.steps * 1e-3, r["total_dof"] * args.steps, world, "cuda")
+    if world > 1:
+        dist.destroy_process_group()
     if rank == 0:
-        line = {"metric": "field DOF-steps/s, 48 heterogeneous instances", "value": r["value"],
+        line = {"metric": "field DOF-steps/s, 48 heterogeneous instances", "value": value,
                 "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
@@ -571,12 +595,8 @@ def main():
             s.step(1)
         ev1.record(stream)
         barrier()
-    ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * dof_steps * args.steps / (ms_max * 1e-3)
+    value, s_max = job_rate(ev0.elapsed_time(ev1) * 1e-3, dof_steps * args.steps, world, "cuda")
+    ms_max = s_max * 1e3
 
     # ---- per-kernel device times over the same number of steps (events around
     # every launch on the same stream, graph off), for the roofline
@@ -634,12 +654,9 @@ def main():
             get_fn(host_out.data_ptr())
         s.sync()  # the asynchronous form's transfers complete here
         barrier()
-        te = torch.tensor([(time.perf_counter() - t0) / args.e2e_steps], device="cuda")
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        rate, _ = job_rate((time.perf_counter() - t0) / args.e2e_steps, dof_steps, world, "cuda")
         nb = 6 * Nc * host_in.element_size()
-        return {"value": world * dof_steps / float(te.item()), "unit": UNIT,
-                "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
+        return {"value": rate, "unit": UNIT, "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
 
     # the asynchronous calls let each read overlap the conversion of the next set
     eb = 8 if args.precision == "fp64" else 4
