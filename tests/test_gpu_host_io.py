@@ -246,3 +246,31 @@ def test_async_transfers_need_page_locked_aligned_memory():
         assert e.value.status == adi.ADI_EINVAL
     s.sync()
     s.close()
+
+
+def test_async_calls_mix_with_substeps_and_synchronous_calls():
+    # every later call on the handle is ordered after a pending asynchronous transfer
+    s, r = _solver("fp32"), _solver("fp32")
+    n = 6 * int(np.prod(s.shape))
+    x = _view(_pinned(n * 4), np.float32, n)
+    x[:] = inputs.random_fields(s.shape, 50).ravel()
+    y = _view(_pinned(n * 4), np.float32, n)
+    s.set_fields_async_ptr(x.ctypes.data, 4, 0.5)
+    for w in range(4):
+        s.substep(w)
+    s.fields_async_ptr(y.ctypes.data, 4)
+    st2 = inputs.random_fields(s.shape, 51)
+    s.set_fields(st2, 1.0)  # synchronous set while the read is pending
+    s.step(1)
+    got, t = s.fields()
+    s.sync()
+    r.set_fields(x.astype(np.float64), 0.5)
+    r.step(1)
+    ref1, _ = r.fields()
+    assert np.array_equal(y, ref1.ravel().astype(np.float32))
+    r.set_fields(st2, 1.0)
+    r.step(1)
+    ref2, t2 = r.fields()
+    assert np.array_equal(got, ref2) and t == t2
+    s.close()
+    r.close()
