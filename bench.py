@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--n", type=int, default=N_ELEM, help="elements per axis (default 256)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--mode", default="single", choices=["single", "batched", "learned"],
                     help="batched: 48 heterogeneous instances (32-128 elements per axis, p in {2,3}); "
                          "learned: guarded corrector at 128^3 against plain steps")
@@ -658,7 +658,7 @@ def main():
         nb = 6 * Nc * host_in.element_size()
         return {"value": rate, "unit": UNIT, "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
 
-    # the asynchronous calls let each read overlap the conversion of the next set
+    # the asynchronous calls copy each set during the step before it and each read during the step after it
     eb = 8 if args.precision == "fp64" else 4
     ht = torch.float64 if eb == 8 else torch.float32
     e2e = e2e_run(ht, lambda ptr, t: s.set_fields_async_ptr(ptr, eb, t), lambda ptr: s.fields_async_ptr(ptr, eb))

@@ -187,19 +187,24 @@ adi_status adi_fields_f32(adi_handle h, float* EH, double* t);
  * back, over and over).  EH must be page-locked host memory (pinned or
  * registered) aligned to elem_bytes (4: floats, 8: doubles; the layout of
  * adi_set_fields); else ADI_EINVAL.  Neither call waits: the caller leaves EH
- * unchanged (set) or unread (read) until adi_sync returns.
- *   adi_set_fields_async converts EH into scratch memory on an input stream of
- *   the handle as soon as the steps enqueued before it are done with that
- *   scratch, then commits it to the state, with the time t, after everything
- *   enqueued on the handle before the call.  A NaN or Inf in EH leaves the
- *   state and its device clock unchanged (the handle's host-side time follows
- *   the call regardless) and makes the next adi_sync return ADI_ENUMERIC.
- *   adi_fields_async writes the state into EH on an output stream after
- *   everything enqueued before it; a NaN or Inf makes the next adi_sync return
+ * unchanged (set) or unread (read) until adi_sync returns.  The first call
+ * allocates two device arrays of 6 N_c elem_bytes bytes (a later call with
+ * larger elements replaces them); ADI_ENOMEM if that fails.
+ *   adi_set_fields_async copies EH to device memory on an input stream of the
+ *   handle as soon as the previous asynchronous set has been applied (so while
+ *   the steps enqueued before it run), then applies it to the state, with the
+ *   time t, after everything enqueued on the handle before the call.  A NaN or
+ *   Inf in EH leaves the state and its device clock unchanged (the handle's
+ *   host-side time follows the call regardless) and makes the next adi_sync
+ *   return ADI_ENUMERIC.
+ *   adi_fields_async takes the state after everything enqueued before it into
+ *   device memory and copies it to EH on an output stream while the work
+ *   enqueued after the call runs; a NaN or Inf makes the next adi_sync return
  *   ADI_ENUMERIC (the data are still written).
  * Everything enqueued on the handle after either call is ordered after it.  In
- * the sequence set, step, read, set, step, read, ... each read runs at the same
- * time as the conversion of the next set (the two directions of the host link).
+ * the sequence set, step, read, set, step, read, ... the copy of each set runs
+ * during the step before it and the copy of each read during the step after
+ * it, on the two directions of the host link.
  * No counterpart in the paper. */
 adi_status adi_set_fields_async(adi_handle h, const void* EH, int elem_bytes, double t);
 adi_status adi_fields_async(adi_handle h, void* EH, int elem_bytes);

@@ -185,10 +185,8 @@ adi_status adi_batch_step(adi_batch b, int n) {
   for (adi_handle h : b->inst) h->steps_host += n;
   // later calls on an instance handle use its own stream: order them after the batch
   cudaError_t e = cudaEventRecord(b->fork, b->stream);
-  for (adi_handle h : b->inst) {
+  for (adi_handle h : b->inst)
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, b->fork, 0);
-    if (e == cudaSuccess) e = cudaEventRecord(h->ev_step, h->stream);  // for asynchronous sets on the instance
-  }
   if (e != cudaSuccess) return bfail(b, ADI_ECUDA, std::string("adi_batch_step: ") + cudaGetErrorString(e));
   return ADI_OK;
 }

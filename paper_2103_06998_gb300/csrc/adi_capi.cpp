@@ -37,7 +37,8 @@ void free_ctx(Ctx* c0) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   for (auto* l : c->pending) delete l;
   void* ptrs[] = {c->d_eps,        c->d_mu,  c->d_sigma, c->stage,  c->tab,   c->tab64, c->tabff, c->tabq,
-                  c->d_clock_t0,   c->d_clock_step, c->d_err, c->d_bad, c->d_diag, c->d_async};
+                  c->d_clock_t0,   c->d_clock_step, c->d_err, c->d_bad, c->d_diag, c->d_async,
+                  c->in_stage,     c->out_stage};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int i = 0; i < 6; ++i) {
@@ -56,7 +57,7 @@ void free_ctx(Ctx* c0) {
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   for (cudaStream_t st : {c->io_in, c->io_out})
     if (st) cudaStreamDestroy(st);
-  for (cudaEvent_t ev : {c->ev_step, c->ev_set, c->ev_get, c->ev_src})
+  for (cudaEvent_t ev : {c->ev_in_ready, c->ev_in_free, c->ev_out_ready, c->ev_out_free})
     if (ev) cudaEventDestroy(ev);
   for (int i = 0; i < 3; ++i) {
     if (c->branch[i]) cudaStreamDestroy(c->branch[i]);
@@ -262,7 +263,7 @@ static adi_status create_impl(int nx, int ny, int nz, int p, double dt, const do
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->io_in, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->io_out, cudaStreamNonBlocking);
-  for (cudaEvent_t* ev : {&c->ev_step, &c->ev_set, &c->ev_get, &c->ev_src})
+  for (cudaEvent_t* ev : {&c->ev_in_ready, &c->ev_in_free, &c->ev_out_ready, &c->ev_out_free})
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     free_ctx(c);
@@ -525,8 +526,6 @@ adi_status adi_step(adi_handle h, int n) {
     if (e != cudaSuccess) return cuda_fail(h, e, "adi_step");
     h->steps_host += 1;
   }
-  cudaError_t e = cudaEventRecord(h->ev_step, h->stream);  // the scratch arrays are free after this
-  if (e != cudaSuccess) return cuda_fail(h, e, "adi_step");
   return ADI_OK;
 }
 
@@ -535,7 +534,6 @@ adi_status adi_substep(adi_handle h, int which) {
   if (which < 0 || which > 3) return fail(h, ADI_EINVAL, "adi_substep: which must be 0..3");
   if (!h->factored) return fail(h, ADI_ESTATE, "adi_substep: call adi_factor first");
   cudaError_t e = adi::run_substep(*h, which);
-  if (e == cudaSuccess) e = cudaEventRecord(h->ev_step, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "adi_substep");
   if (which == 3) h->steps_host += 1;
   return ADI_OK;
@@ -668,74 +666,93 @@ adi_status adi_sync(adi_handle h) {
   return ADI_OK;
 }
 
-// Blocks of an asynchronous conversion: four per SM of 152 (the best of 1, 2, 4 and
-// 8 per SM measured at 256^3), so that a read and the next set share the GPU and
-// both directions of the host link are busy.
-static const unsigned kAsyncBlocks = 608;
-
-// Checks shared by the asynchronous transfers: EH page-locked (its device
-// address returned) and aligned to elem_bytes = 4 or 8.
-static const void* async_host(adi_handle h, const void* EH, int elem_bytes, const char* name, adi_status* st) {
-  *st = ADI_EINVAL;
-  if (!h) {
-    fail(nullptr, ADI_EINVAL, std::string(name) + ": NULL handle");
-    return nullptr;
-  }
-  if (elem_bytes != 4 && elem_bytes != 8) {
-    fail(h, ADI_EINVAL, std::string(name) + ": elem_bytes must be 4 (float) or 8 (double)");
-    return nullptr;
-  }
-  if (!EH || reinterpret_cast<uintptr_t>(EH) % elem_bytes != 0) {
-    fail(h, ADI_EINVAL, std::string(name) + ": EH is NULL or not aligned to elem_bytes");
-    return nullptr;
-  }
-  const void* m = mapped_host(EH);
-  if (!m) fail(h, ADI_EINVAL, std::string(name) + ": EH must be page-locked host memory (pinned or registered)");
-  else *st = ADI_OK;
-  return m;
+// Checks shared by the asynchronous transfers: EH page-locked (pinned or
+// registered, so that the copy engines move it without a host-side staging copy)
+// and aligned to elem_bytes = 4 or 8.
+static adi_status async_host(adi_handle h, const void* EH, int elem_bytes, const char* name) {
+  if (!h) return fail(nullptr, ADI_EINVAL, std::string(name) + ": NULL handle");
+  if (elem_bytes != 4 && elem_bytes != 8)
+    return fail(h, ADI_EINVAL, std::string(name) + ": elem_bytes must be 4 (float) or 8 (double)");
+  if (!EH || reinterpret_cast<uintptr_t>(EH) % elem_bytes != 0)
+    return fail(h, ADI_EINVAL, std::string(name) + ": EH is NULL or not aligned to elem_bytes");
+  if (!mapped_host(EH))
+    return fail(h, ADI_EINVAL, std::string(name) + ": EH must be page-locked host memory (pinned or registered)");
+  return ADI_OK;
 }
 
+// The two device staging arrays, at least `bytes` each (a larger request, e.g.
+// doubles after floats, replaces them once the work that uses them is done).
+static adi_status async_stage(adi_handle h, size_t bytes, const char* name) {
+  if (h->stage_bytes >= bytes) return ADI_OK;
+  cudaError_t e = cudaStreamSynchronize(h->io_in);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->io_out);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, name);
+  for (void** p : {&h->in_stage, &h->out_stage}) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+  }
+  h->stage_bytes = 0;
+  e = cudaMalloc(&h->in_stage, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&h->out_stage, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    for (void** p : {&h->in_stage, &h->out_stage}) {
+      if (*p) cudaFree(*p);
+      *p = nullptr;
+    }
+    return fail(h, ADI_ENOMEM, std::string(name) + ": device staging allocation failed");
+  }
+  h->stage_bytes = bytes;
+  return ADI_OK;
+}
+
+// Set: the copy engine moves EH into in_stage on the input stream as soon as the
+// previous set's commit has read in_stage (so during the steps enqueued before
+// the call); the main stream then converts it into the scratch arrays and
+// commits it after everything enqueued before the call.
 adi_status adi_set_fields_async(adi_handle h, const void* EH, int elem_bytes, double t) {
-  adi_status st;
-  const void* m = async_host(h, EH, elem_bytes, "adi_set_fields_async", &st);
+  adi_status st = async_host(h, EH, elem_bytes, "adi_set_fields_async");
   if (st != ADI_OK) return st;
   if (!std::isfinite(t)) return fail(h, ADI_EINVAL, "adi_set_fields_async: t must be finite");
+  const size_t bytes = 6 * h->Nc * (size_t)elem_bytes;
+  st = async_stage(h, bytes, "adi_set_fields_async");
+  if (st != ADI_OK) return st;
   void* scratch[6] = {h->rhs[0], h->rhs[1], h->rhs[2], h->half[0], h->half[1], h->half[2]};
-  cudaStream_t main = h->stream;
-  // convert into the scratch arrays once the last enqueued step is done with them
-  cudaError_t e = cudaStreamWaitEvent(h->io_in, h->ev_step, 0);
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_async, 0, sizeof(int), h->io_in);
-  h->stream = h->io_in;
+  cudaError_t e = cudaStreamWaitEvent(h->io_in, h->ev_in_free, 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->in_stage, EH, bytes, cudaMemcpyHostToDevice, h->io_in);
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev_in_ready, h->io_in);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_in_ready, 0);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_async, 0, sizeof(int), h->stream);
   if (e == cudaSuccess)
-    e = elem_bytes == 4 ? adi::set_fields_into<float>(*h, static_cast<const float*>(m), scratch, h->d_async, kAsyncBlocks)
-                        : adi::set_fields_into<double>(*h, static_cast<const double*>(m), scratch, h->d_async, kAsyncBlocks);
-  // commit after everything enqueued on the handle so far (steps, reads of the state)
-  if (e == cudaSuccess) e = cudaEventRecord(h->ev_src, main);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->io_in, h->ev_src, 0);
+    e = elem_bytes == 4 ? adi::set_fields_into<float>(*h, static_cast<const float*>(h->in_stage), scratch, h->d_async)
+                        : adi::set_fields_into<double>(*h, static_cast<const double*>(h->in_stage), scratch, h->d_async);
   if (e == cudaSuccess) e = adi::commit_fields(*h, h->d_async, h->d_async + 1, t);
-  if (e == cudaSuccess) e = cudaEventRecord(h->ev_set, h->io_in);
-  h->stream = main;
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(main, h->ev_set, 0);  // later work sees the new state
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev_in_free, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "adi_set_fields_async");
   h->t_host = t;
   h->steps_host = 0;
   return ADI_OK;
 }
 
+// Read: the main stream converts the state into out_stage after everything
+// enqueued before the call (once the previous read's copy has left out_stage);
+// the copy engine then moves it to EH on the output stream while the main
+// stream goes on with the work enqueued after the call.
 adi_status adi_fields_async(adi_handle h, void* EH, int elem_bytes) {
-  adi_status st;
-  void* m = const_cast<void*>(async_host(h, EH, elem_bytes, "adi_fields_async", &st));
+  adi_status st = async_host(h, EH, elem_bytes, "adi_fields_async");
   if (st != ADI_OK) return st;
-  cudaStream_t main = h->stream;
-  cudaError_t e = cudaEventRecord(h->ev_src, main);  // after everything enqueued so far
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->io_out, h->ev_src, 0);
-  h->stream = h->io_out;
+  const size_t bytes = 6 * h->Nc * (size_t)elem_bytes;
+  st = async_stage(h, bytes, "adi_fields_async");
+  if (st != ADI_OK) return st;
+  cudaError_t e = cudaStreamWaitEvent(h->stream, h->ev_out_free, 0);
   if (e == cudaSuccess)
-    e = elem_bytes == 4 ? adi::get_fields_dev<float>(*h, static_cast<float*>(m), h->d_async + 2, kAsyncBlocks)
-                        : adi::get_fields_dev<double>(*h, static_cast<double*>(m), h->d_async + 2, kAsyncBlocks);
-  if (e == cudaSuccess) e = cudaEventRecord(h->ev_get, h->io_out);
-  h->stream = main;
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(main, h->ev_get, 0);  // later steps wait for the read
+    e = elem_bytes == 4 ? adi::get_fields_dev<float>(*h, static_cast<float*>(h->out_stage), h->d_async + 2)
+                        : adi::get_fields_dev<double>(*h, static_cast<double*>(h->out_stage), h->d_async + 2);
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev_out_ready, h->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->io_out, h->ev_out_ready, 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(EH, h->out_stage, bytes, cudaMemcpyDeviceToHost, h->io_out);
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev_out_free, h->io_out);
   if (e != cudaSuccess) return cuda_fail(h, e, "adi_fields_async");
   return ADI_OK;
 }
@@ -770,6 +787,8 @@ adi_status adi_dims(adi_handle h, int* Nx, int* Ny, int* Nz, int* elem_bytes) {
 void adi_destroy(adi_handle h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
+  cudaStreamSynchronize(h->io_in);  // copies of the asynchronous transfers
+  cudaStreamSynchronize(h->io_out);
   free_ctx(h);
 }
 

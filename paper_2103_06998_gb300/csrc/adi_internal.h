@@ -252,12 +252,18 @@ struct Ctx {
   bool tmaps_ok = false;
   int* d_err = nullptr;  // device status word written by bounded waits
   int* d_bad = nullptr;  // device flag: a value that is not finite (field checks)
-  // asynchronous host transfers (adi_set_fields_async / adi_fields_async): an input
-  // and an output stream, events ordering them against the main stream, and flags
-  // [0] this set's values not finite, [1] a set was refused, [2] a read saw a value
-  // that is not finite (both reported by adi_sync)
+  // asynchronous host transfers (adi_set_fields_async / adi_fields_async): dense
+  // device copies of a host state in the host's element type (in_stage, out_stage:
+  // stage_bytes each, allocated by the first such call), moved over the host link by
+  // the copy engines on an input and an output stream while the main stream steps;
+  // events: in_stage filled / read by its commit, out_stage filled / copied out;
+  // flags [0] this set's values not finite, [1] a set was refused, [2] a read saw a
+  // value that is not finite (both reported by adi_sync)
   cudaStream_t io_in = nullptr, io_out = nullptr;
-  cudaEvent_t ev_step = nullptr, ev_set = nullptr, ev_get = nullptr, ev_src = nullptr;
+  void* in_stage = nullptr;
+  void* out_stage = nullptr;
+  size_t stage_bytes = 0;
+  cudaEvent_t ev_in_ready = nullptr, ev_in_free = nullptr, ev_out_ready = nullptr, ev_out_free = nullptr;
   int* d_async = nullptr;
   double* d_diag = nullptr;  // 8 doubles: sums of the norm diagnostics
 
@@ -282,11 +288,10 @@ template <typename S>
 cudaError_t set_fields_dev(Ctx& c, const S* d_src);
 // convert 6 N_c values at d_src (device memory or mapped host memory) into the six
 // arrays dst (state layout, constrained coefficients zero); d_bad (optional) |= 1 on NaN/Inf
-// cap: at most that many blocks (0: no cap)
 template <typename S>
-cudaError_t set_fields_into(Ctx& c, const S* d_src, void* const* dst, int* d_bad, unsigned cap = 0);
+cudaError_t set_fields_into(Ctx& c, const S* d_src, void* const* dst, int* d_bad);
 template <typename S>
-cudaError_t get_fields_dev(Ctx& c, S* d_dst, int* d_bad, unsigned cap = 0);
+cudaError_t get_fields_dev(Ctx& c, S* d_dst, int* d_bad);
 // d_bad |= 1 if any of the n values at d_src is NaN or Inf
 template <typename S>
 cudaError_t check_finite_dev(Ctx& c, const S* d_src, long long n, int* d_bad);

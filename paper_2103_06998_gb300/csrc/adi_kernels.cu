@@ -4062,47 +4062,41 @@ cudaError_t run_step(Ctx& c) {
 }
 
 // 16-byte accesses when the dense array starts on a 16-byte boundary
-// grid of a conversion: at most `cap` blocks (a share of the SMs, so that a set
-// and a read of the asynchronous transfers can run side by side), 0: no cap
-inline unsigned conv_grid(long long n, unsigned cap) {
-  const unsigned g = grid_for(n, 256);
-  return cap && g > cap ? cap : g;
-}
 template <typename S, typename T>
-void launch_set(Ctx& c, const S* d_src, void* const* dst, int* d_bad, unsigned cap) {
+void launch_set(Ctx& c, const S* d_src, void* const* dst, int* d_bad) {
   constexpr int V = 16 / sizeof(S);
   T* const* d = reinterpret_cast<T* const*>(dst);
   const long long n = 6LL * (long long)c.Nc;
   if ((reinterpret_cast<uintptr_t>(d_src) & 15) == 0) {
-    set_fields_kernel<S, T, V><<<conv_grid(n / V + V, cap), 256, 0, c.stream>>>(
+    set_fields_kernel<S, T, V><<<grid_for(n / V + V, 256), 256, 0, c.stream>>>(
         d_src, d[0], d[1], d[2], d[3], d[4], d[5], c.N[0], c.N[1], c.N[2], c.pitch, d_bad);
   } else {
-    set_fields_kernel<S, T, 1><<<conv_grid(n, cap), 256, 0, c.stream>>>(d_src, d[0], d[1], d[2], d[3], d[4], d[5], c.N[0],
+    set_fields_kernel<S, T, 1><<<grid_for(n, 256), 256, 0, c.stream>>>(d_src, d[0], d[1], d[2], d[3], d[4], d[5], c.N[0],
                                                                        c.N[1], c.N[2], c.pitch, d_bad);
   }
 }
 template <typename S, typename T>
-void launch_get(Ctx& c, S* d_dst, int* d_bad, unsigned cap) {
+void launch_get(Ctx& c, S* d_dst, int* d_bad) {
   constexpr int V = 16 / sizeof(S);
   T** s = reinterpret_cast<T**>(c.cur);
   const long long n = 6LL * (long long)c.Nc;
   if ((reinterpret_cast<uintptr_t>(d_dst) & 15) == 0) {
-    get_fields_kernel<S, T, V><<<conv_grid(n / V + V, cap), 256, 0, c.stream>>>(
+    get_fields_kernel<S, T, V><<<grid_for(n / V + V, 256), 256, 0, c.stream>>>(
         d_dst, s[0], s[1], s[2], s[3], s[4], s[5], c.N[0], c.N[1], c.N[2], c.pitch, d_bad);
   } else {
-    get_fields_kernel<S, T, 1><<<conv_grid(n, cap), 256, 0, c.stream>>>(d_dst, s[0], s[1], s[2], s[3], s[4], s[5], c.N[0],
+    get_fields_kernel<S, T, 1><<<grid_for(n, 256), 256, 0, c.stream>>>(d_dst, s[0], s[1], s[2], s[3], s[4], s[5], c.N[0],
                                                                        c.N[1], c.N[2], c.pitch, d_bad);
   }
 }
 
 template <typename S>
-cudaError_t set_fields_into(Ctx& c, const S* d_src, void* const* dst, int* d_bad, unsigned cap) {
-  if (c.precision == ADI_PREC_FP64) launch_set<S, double>(c, d_src, dst, d_bad, cap);
-  else launch_set<S, float>(c, d_src, dst, d_bad, cap);
+cudaError_t set_fields_into(Ctx& c, const S* d_src, void* const* dst, int* d_bad) {
+  if (c.precision == ADI_PREC_FP64) launch_set<S, double>(c, d_src, dst, d_bad);
+  else launch_set<S, float>(c, d_src, dst, d_bad);
   return cudaGetLastError();
 }
-template cudaError_t set_fields_into<double>(Ctx&, const double*, void* const*, int*, unsigned);
-template cudaError_t set_fields_into<float>(Ctx&, const float*, void* const*, int*, unsigned);
+template cudaError_t set_fields_into<double>(Ctx&, const double*, void* const*, int*);
+template cudaError_t set_fields_into<float>(Ctx&, const float*, void* const*, int*);
 
 template <typename S>
 cudaError_t set_fields_dev(Ctx& c, const S* d_src) {
@@ -4120,13 +4114,13 @@ template cudaError_t check_finite_dev<double>(Ctx&, const double*, long long, in
 template cudaError_t check_finite_dev<float>(Ctx&, const float*, long long, int*);
 
 template <typename S>
-cudaError_t get_fields_dev(Ctx& c, S* d_dst, int* d_bad, unsigned cap) {
-  if (c.precision == ADI_PREC_FP64) launch_get<S, double>(c, d_dst, d_bad, cap);
-  else launch_get<S, float>(c, d_dst, d_bad, cap);
+cudaError_t get_fields_dev(Ctx& c, S* d_dst, int* d_bad) {
+  if (c.precision == ADI_PREC_FP64) launch_get<S, double>(c, d_dst, d_bad);
+  else launch_get<S, float>(c, d_dst, d_bad);
   return cudaGetLastError();
 }
-template cudaError_t get_fields_dev<double>(Ctx&, double*, int*, unsigned);
-template cudaError_t get_fields_dev<float>(Ctx&, float*, int*, unsigned);
+template cudaError_t get_fields_dev<double>(Ctx&, double*, int*);
+template cudaError_t get_fields_dev<float>(Ctx&, float*, int*);
 
 cudaError_t make_tensor_maps(Ctx& c) {
   void* fn = nullptr;
