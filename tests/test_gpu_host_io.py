@@ -10,6 +10,13 @@ coefficients fixed by the boundary conditions come back zero, 16-byte aligned
 and unaligned host pointers take the vector and the scalar kernels with the same
 result, pointers off their element alignment are refused on the host, and an
 FP64 handle round-trips floats exactly.
+
+The asynchronous forms (adi_set_fields_async / adi_fields_async: copy-engine
+transfers through device staging arrays on the handle's input and output
+streams) give the same states and read-backs as the synchronous calls, in a
+loop without synchronisation, mixed with sub-steps and synchronous calls, and
+across a change of the host element size on one handle; a NaN is refused on
+the device and reported once by adi_sync.
 """
 import numpy as np
 import pytest
@@ -272,5 +279,30 @@ def test_async_calls_mix_with_substeps_and_synchronous_calls():
     r.step(1)
     ref2, t2 = r.fields()
     assert np.array_equal(got, ref2) and t == t2
+    s.close()
+    r.close()
+
+
+def test_async_element_size_change_on_one_handle():
+    # floats, then doubles on the same handle (the device staging arrays grow in
+    # between), then floats again: each read equals the synchronous sequence
+    s, r = _solver("fp32"), _solver("fp32")
+    n = 6 * int(np.prod(s.shape))
+    seq = []
+    for i, elem in enumerate((4, 8, 4)):
+        dt = np.float32 if elem == 4 else np.float64
+        x = _view(_pinned(n * elem), dt, n)
+        x[:] = inputs.random_fields(s.shape, 60 + i).ravel().astype(np.float32)
+        y = _view(_pinned(n * elem), dt, n)
+        s.set_fields_async_ptr(x.ctypes.data, elem, 0.5 * i)
+        s.step(1)
+        s.fields_async_ptr(y.ctypes.data, elem)
+        seq.append((x, y, dt))
+    s.sync()
+    for i, (x, y, dt) in enumerate(seq):
+        r.set_fields(x.astype(np.float64), 0.5 * i)
+        r.step(1)
+        ref, _ = r.fields()
+        assert np.array_equal(y, ref.ravel().astype(dt)), i
     s.close()
     r.close()
