@@ -126,6 +126,23 @@ adi_status adi_create_knots(int nx, int ny, int nz, int p, double dt, const doub
                             const double* breaks_y, const double* breaks_z, const double* eps, const double* mu,
                             const double* sigma, const adi_options* opt, adi_handle* out);
 
+/* Host only (no device, no handle): the 1D matrices of one axis exactly as
+ * adi_create / adi_create_knots build them (definitions after eq. discrete4:
+ * M[l][i] = int B_i B_l, S[l][i] = int B_i' B_l', A[l][i] = int B_i' B_l,
+ * B[l][i] = int B_i B_l', row l the test function; Gauss-Legendre with p + 1
+ * points per element, exact for these integrands, in FP64), in band form: row
+ * k of X at out[k (2p+1) + d] = X[k][k + d - p], k = 0 .. N-1, N = n + p
+ * (entries outside the matrix are 0).
+ *  n >= 1, 1 <= p <= 4; breaks: n + 1 element boundaries as in
+ *  adi_create_knots, or NULL (uniform elements).
+ *  M, S, A, B (host, caller-owned; any may be NULL to skip it): N (2p+1)
+ *  doubles each.  inner (host, caller-owned, may be NULL): 2 ints, the first
+ *  and last row whose band rows the kernels replace by the constant interior
+ *  stencil (inner[0] > inner[1]: none).
+ * Errors: ADI_EINVAL (n, p or breaks), ADI_ENOMEM (host allocation). */
+adi_status adi_axis_bands(int n, int p, const double* breaks, double* M, double* S, double* A, double* B,
+                          int* inner);
+
 /* Build the 1D matrices M, S, A (B = A^T) of every axis by Gauss-Legendre
  * quadrature in FP64 (definitions after eq. discrete4), factor the mass
  * matrices (full and Dirichlet-reduced) without pivoting, and upload the

@@ -18,7 +18,7 @@ PREC_FP64, PREC_FP32, PREC_MIXED = 0, 1, 2
 _PREC = {"fp64": PREC_FP64, "fp32": PREC_FP32, "mixed": PREC_MIXED}
 
 # every symbol declared in include/adi_maxwell.h
-EXPORTS = ("adi_create", "adi_create_knots", "adi_factor", "adi_set_dt", "adi_set_stream", "adi_set_fields",
+EXPORTS = ("adi_create", "adi_create_knots", "adi_axis_bands", "adi_factor", "adi_set_dt", "adi_set_stream", "adi_set_fields",
            "adi_set_fields_f32", "adi_set_source", "adi_step", "adi_substep", "adi_fields", "adi_fields_f32",
            "adi_fields_device", "adi_set_fields_async", "adi_fields_async",
            "adi_cfl_dt", "adi_cfl_dt_noalloc", "adi_sync", "adi_wait_selftest", "adi_norms", "adi_plane", "adi_set_profiling", "adi_kernel_stats", "adi_dims",
@@ -66,6 +66,7 @@ def load_library(path=LIB_PATH):
     sig = {
         "adi_create": (I, [I, I, I, I, D, P(D), P(D), P(D), P(AdiOptions), P(H)]),
         "adi_create_knots": (I, [I, I, I, I, D, P(D), P(D), P(D), P(D), P(D), P(D), P(AdiOptions), P(H)]),
+        "adi_axis_bands": (I, [I, I, P(D), P(D), P(D), P(D), P(D), P(I)]),
         "adi_factor": (I, [H]),
         "adi_set_dt": (I, [H, D]),
         "adi_set_stream": (I, [H, ctypes.c_void_p]),
@@ -129,6 +130,22 @@ class AdiError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("%s: %s" % (status, msg))
         self.status = status
+
+
+def axis_bands(n, p, breaks=None):
+    """adi_axis_bands: the 1D matrices of one axis as the solver builds them (host
+    only).  Returns ({"M", "S", "A", "B"}: (N, 2p+1) band arrays, row k column d =
+    X[k][k+d-p]; (first, last) interior-stencil row)."""
+    L = load_library()
+    N, W = n + p, 2 * p + 1
+    out = {k: np.zeros((N, W)) for k in "MSAB"}
+    inner = (ctypes.c_int * 2)()
+    br = None if breaks is None else np.ascontiguousarray(breaks, dtype=np.float64)
+    st = L.adi_axis_bands(n, p, None if br is None else _dptr(br), *(_dptr(out[k]) for k in "MSAB"),
+                          ctypes.cast(inner, ctypes.POINTER(ctypes.c_int)))
+    if st != ADI_OK:
+        raise AdiError(st, L.adi_last_error(None).decode())
+    return out, (inner[0], inner[1])
 
 
 def _dptr(a):

@@ -4,6 +4,7 @@
 // the kernels of adi_kernels.cu.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -174,6 +175,13 @@ adi_status adi_create(int nx, int ny, int nz, int p, double dt, const double* ep
   return adi_create_knots(nx, ny, nz, p, dt, nullptr, nullptr, nullptr, eps, mu, sigma, opt, out);
 }
 
+// n + 1 element boundaries strictly increasing from 0 to 1
+static bool breaks_ok(const double* b, int n) {
+  bool ok = b[0] == 0.0 && b[n] == 1.0;
+  for (int i = 0; i < n && ok; ++i) ok = std::isfinite(b[i + 1]) && b[i + 1] > b[i];
+  return ok;
+}
+
 static adi_status create_impl(int nx, int ny, int nz, int p, double dt, const double* const* breaks,
                               const double* eps, const double* mu, const double* sigma, const adi_options* opt,
                               adi_handle* out) {
@@ -181,15 +189,10 @@ static adi_status create_impl(int nx, int ny, int nz, int p, double dt, const do
   *out = nullptr;
   if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, ADI_EINVAL, "adi_create: element counts must be >= 1");
   const int ns[3] = {nx, ny, nz};
-  for (int d = 0; d < 3; ++d) {
-    const double* b = breaks[d];
-    if (!b) continue;
-    bool ok = b[0] == 0.0 && b[ns[d]] == 1.0;
-    for (int i = 0; i < ns[d] && ok; ++i) ok = std::isfinite(b[i + 1]) && b[i + 1] > b[i];
-    if (!ok)
+  for (int d = 0; d < 3; ++d)
+    if (breaks[d] && !breaks_ok(breaks[d], ns[d]))
       return fail(nullptr, ADI_EINVAL,
                   "adi_create_knots: element boundaries must increase strictly from 0 to 1 (n_d + 1 values)");
-  }
   if (p < 1 || p > adi::kMaxP) return fail(nullptr, ADI_EINVAL, "adi_create: p must be in 1..4");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(nullptr, ADI_EINVAL, "adi_create: dt must be finite and > 0");
   int prec = ADI_PREC_FP32, use_graph = 1, refine = 1, res64 = 0, quad = 0, serial = 0;
@@ -344,6 +347,30 @@ static adi_status create_impl(int nx, int ny, int nz, int p, double dt, const do
   }
   c->err = "no error";
   *out = c;
+  return ADI_OK;
+}
+
+adi_status adi_axis_bands(int n, int p, const double* breaks, double* M, double* S, double* A, double* B,
+                          int* inner) {
+  if (n < 1) return fail(nullptr, ADI_EINVAL, "adi_axis_bands: n must be >= 1");
+  if (p < 1 || p > adi::kMaxP) return fail(nullptr, ADI_EINVAL, "adi_axis_bands: p must be in 1..4");
+  if (breaks && !breaks_ok(breaks, n))
+    return fail(nullptr, ADI_EINVAL,
+                "adi_axis_bands: element boundaries must increase strictly from 0 to 1 (n + 1 values)");
+  adi::Axis1D ax;
+  try {
+    adi::build_axis(n, p, ax, breaks);
+  } catch (const std::bad_alloc&) {
+    return fail(nullptr, ADI_ENOMEM, "adi_axis_bands: host allocation failed");
+  }
+  double* outs[4] = {M, S, A, B};
+  const std::vector<double>* src[4] = {&ax.M, &ax.S, &ax.A, &ax.B};
+  for (int o = 0; o < 4; ++o)
+    if (outs[o]) std::copy(src[o]->begin(), src[o]->end(), outs[o]);
+  if (inner) {
+    inner[0] = ax.inner_lo;
+    inner[1] = ax.inner_hi;
+  }
   return ADI_OK;
 }
 
