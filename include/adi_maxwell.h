@@ -143,6 +143,27 @@ adi_status adi_create_knots(int nx, int ny, int nz, int p, double dt, const doub
 adi_status adi_axis_bands(int n, int p, const double* breaks, double* M, double* S, double* A, double* B,
                           int* inner);
 
+/* Host only: the LU factors of the 1D mass matrix M of one axis exactly as
+ * adi_factor computes them (no pivoting; M is symmetric positive definite),
+ * for the full matrix (reduced = 0: rows and columns 0 .. N-1) or the
+ * Dirichlet-reduced one (reduced = 1: 1 .. N-2, the first and last basis
+ * functions removed).  Over those rows, M = L D U with L unit lower and U unit
+ * upper triangular of bandwidth p and D diagonal:
+ *  L[k p + q - 1] = L[k][k - q], U[k p + q - 1] = U[k][k + q] (q = 1..p),
+ *  inv_d[k] = 1 / D[k]; rows outside the range are 0.
+ *  n, p, breaks as adi_axis_bands; L, U (host, caller-owned): N p doubles,
+ *  inv_d: N doubles.  Errors: ADI_EINVAL, ADI_ENOMEM. */
+adi_status adi_axis_mass_lu(int n, int p, const double* breaks, int reduced, double* L, double* inv_d, double* U);
+
+/* Host only: the p + 1 B-splines of one axis that are nonzero at x0 in [0, 1]
+ * and their values there, as the point source uses them (the dipole's spatial
+ * factor, section "Incorporating non-regular material data"): *first = e, the
+ * element holding x0 (a point on an element boundary belongs to the element on
+ * its right, x0 = 1 to the last), vals[a] = B_{e+a}(x0), a = 0..p.
+ *  n, p, breaks as adi_axis_bands; vals (host, caller-owned): p + 1 doubles.
+ * Errors: ADI_EINVAL (also x0 outside [0, 1]), ADI_ENOMEM. */
+adi_status adi_axis_point_basis(int n, int p, const double* breaks, double x0, int* first, double* vals);
+
 /* Build the 1D matrices M, S, A (B = A^T) of every axis by Gauss-Legendre
  * quadrature in FP64 (definitions after eq. discrete4), factor the mass
  * matrices (full and Dirichlet-reduced) without pivoting, and upload the

@@ -18,7 +18,8 @@ PREC_FP64, PREC_FP32, PREC_MIXED = 0, 1, 2
 _PREC = {"fp64": PREC_FP64, "fp32": PREC_FP32, "mixed": PREC_MIXED}
 
 # every symbol declared in include/adi_maxwell.h
-EXPORTS = ("adi_create", "adi_create_knots", "adi_axis_bands", "adi_factor", "adi_set_dt", "adi_set_stream", "adi_set_fields",
+EXPORTS = ("adi_create", "adi_create_knots", "adi_axis_bands", "adi_axis_mass_lu", "adi_axis_point_basis",
+           "adi_factor", "adi_set_dt", "adi_set_stream", "adi_set_fields",
            "adi_set_fields_f32", "adi_set_source", "adi_step", "adi_substep", "adi_fields", "adi_fields_f32",
            "adi_fields_device", "adi_set_fields_async", "adi_fields_async",
            "adi_cfl_dt", "adi_cfl_dt_noalloc", "adi_sync", "adi_wait_selftest", "adi_norms", "adi_plane", "adi_set_profiling", "adi_kernel_stats", "adi_dims",
@@ -67,6 +68,8 @@ def load_library(path=LIB_PATH):
         "adi_create": (I, [I, I, I, I, D, P(D), P(D), P(D), P(AdiOptions), P(H)]),
         "adi_create_knots": (I, [I, I, I, I, D, P(D), P(D), P(D), P(D), P(D), P(D), P(AdiOptions), P(H)]),
         "adi_axis_bands": (I, [I, I, P(D), P(D), P(D), P(D), P(D), P(I)]),
+        "adi_axis_mass_lu": (I, [I, I, P(D), I, P(D), P(D), P(D)]),
+        "adi_axis_point_basis": (I, [I, I, P(D), D, P(I), P(D)]),
         "adi_factor": (I, [H]),
         "adi_set_dt": (I, [H, D]),
         "adi_set_stream": (I, [H, ctypes.c_void_p]),
@@ -146,6 +149,35 @@ def axis_bands(n, p, breaks=None):
     if st != ADI_OK:
         raise AdiError(st, L.adi_last_error(None).decode())
     return out, (inner[0], inner[1])
+
+
+def _breaks_arg(breaks):
+    return None if breaks is None else np.ascontiguousarray(breaks, dtype=np.float64)
+
+
+def axis_mass_lu(n, p, breaks=None, reduced=False):
+    """adi_axis_mass_lu: (L (N, p), inv_d (N,), U (N, p)) of the 1D mass matrix."""
+    L = load_library()
+    N = n + p
+    lo, inv_d, up = np.zeros((N, p)), np.zeros(N), np.zeros((N, p))
+    br = _breaks_arg(breaks)
+    st = L.adi_axis_mass_lu(n, p, None if br is None else _dptr(br), int(bool(reduced)), _dptr(lo), _dptr(inv_d),
+                            _dptr(up))
+    if st != ADI_OK:
+        raise AdiError(st, L.adi_last_error(None).decode())
+    return lo, inv_d, up
+
+
+def axis_point_basis(n, p, x0, breaks=None):
+    """adi_axis_point_basis: (first basis index e, values of B_e .. B_{e+p} at x0)."""
+    L = load_library()
+    first = ctypes.c_int()
+    vals = np.zeros(p + 1)
+    br = _breaks_arg(breaks)
+    st = L.adi_axis_point_basis(n, p, None if br is None else _dptr(br), float(x0), ctypes.byref(first), _dptr(vals))
+    if st != ADI_OK:
+        raise AdiError(st, L.adi_last_error(None).decode())
+    return first.value, vals
 
 
 def _dptr(a):

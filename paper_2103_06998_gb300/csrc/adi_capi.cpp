@@ -350,19 +350,26 @@ static adi_status create_impl(int nx, int ny, int nz, int p, double dt, const do
   return ADI_OK;
 }
 
-adi_status adi_axis_bands(int n, int p, const double* breaks, double* M, double* S, double* A, double* B,
-                          int* inner) {
-  if (n < 1) return fail(nullptr, ADI_EINVAL, "adi_axis_bands: n must be >= 1");
-  if (p < 1 || p > adi::kMaxP) return fail(nullptr, ADI_EINVAL, "adi_axis_bands: p must be in 1..4");
+// shared checks and axis construction of the host-only axis calls
+static adi_status host_axis(int n, int p, const double* breaks, const char* name, adi::Axis1D& ax) {
+  if (n < 1) return fail(nullptr, ADI_EINVAL, std::string(name) + ": n must be >= 1");
+  if (p < 1 || p > adi::kMaxP) return fail(nullptr, ADI_EINVAL, std::string(name) + ": p must be in 1..4");
   if (breaks && !breaks_ok(breaks, n))
     return fail(nullptr, ADI_EINVAL,
-                "adi_axis_bands: element boundaries must increase strictly from 0 to 1 (n + 1 values)");
-  adi::Axis1D ax;
+                std::string(name) + ": element boundaries must increase strictly from 0 to 1 (n + 1 values)");
   try {
     adi::build_axis(n, p, ax, breaks);
   } catch (const std::bad_alloc&) {
-    return fail(nullptr, ADI_ENOMEM, "adi_axis_bands: host allocation failed");
+    return fail(nullptr, ADI_ENOMEM, std::string(name) + ": host allocation failed");
   }
+  return ADI_OK;
+}
+
+adi_status adi_axis_bands(int n, int p, const double* breaks, double* M, double* S, double* A, double* B,
+                          int* inner) {
+  adi::Axis1D ax;
+  adi_status st = host_axis(n, p, breaks, "adi_axis_bands", ax);
+  if (st != ADI_OK) return st;
   double* outs[4] = {M, S, A, B};
   const std::vector<double>* src[4] = {&ax.M, &ax.S, &ax.A, &ax.B};
   for (int o = 0; o < 4; ++o)
@@ -371,6 +378,34 @@ adi_status adi_axis_bands(int n, int p, const double* breaks, double* M, double*
     inner[0] = ax.inner_lo;
     inner[1] = ax.inner_hi;
   }
+  return ADI_OK;
+}
+
+adi_status adi_axis_mass_lu(int n, int p, const double* breaks, int reduced, double* L, double* inv_d, double* U) {
+  if (reduced != 0 && reduced != 1) return fail(nullptr, ADI_EINVAL, "adi_axis_mass_lu: reduced must be 0 or 1");
+  if (!L || !inv_d || !U) return fail(nullptr, ADI_EINVAL, "adi_axis_mass_lu: NULL output");
+  adi::Axis1D ax;
+  adi_status st = host_axis(n, p, breaks, "adi_axis_mass_lu", ax);
+  if (st != ADI_OK) return st;
+  adi::BandLU lu;
+  try {
+    adi::band_lu(ax.M, nullptr, ax.N, p, reduced ? 1 : 0, reduced ? ax.N - 2 : ax.N - 1, lu);
+  } catch (const std::bad_alloc&) {
+    return fail(nullptr, ADI_ENOMEM, "adi_axis_mass_lu: host allocation failed");
+  }
+  std::copy(lu.L.begin(), lu.L.end(), L);
+  std::copy(lu.inv_d.begin(), lu.inv_d.end(), inv_d);
+  std::copy(lu.U.begin(), lu.U.end(), U);
+  return ADI_OK;
+}
+
+adi_status adi_axis_point_basis(int n, int p, const double* breaks, double x0, int* first, double* vals) {
+  if (!(x0 >= 0.0 && x0 <= 1.0)) return fail(nullptr, ADI_EINVAL, "adi_axis_point_basis: x0 must lie in [0,1]");
+  if (!first || !vals) return fail(nullptr, ADI_EINVAL, "adi_axis_point_basis: NULL output");
+  adi::Axis1D ax;
+  adi_status st = host_axis(n, p, breaks, "adi_axis_point_basis", ax);
+  if (st != ADI_OK) return st;
+  *first = adi::point_basis(ax, x0, vals);
   return ADI_OK;
 }
 

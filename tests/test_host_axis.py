@@ -1,9 +1,15 @@
-"""The 1D matrices of one axis as the library builds them on the host
-(adi_axis_bands; no GPU): the band form of the mass, stiffness and mixed
-matrices defined after eq. discrete4 (section "Variational formulation"),
-against the oracle's dense matrices, the closed-form interior stencils of
-cardinal B-splines, the symmetry B = A^T, and the interior rows the kernels
-replace by one constant stencil, on uniform and non-uniform elements.
+"""Host logic of one axis as the library runs it (no GPU), on uniform and
+non-uniform elements:
+* adi_axis_bands: the band form of the mass, stiffness and mixed matrices
+  defined after eq. discrete4 (section "Variational formulation") against the
+  oracle's dense matrices, the closed-form interior stencils of cardinal
+  B-splines, the symmetry B = A^T, and the interior rows the kernels replace by
+  one constant stencil;
+* adi_axis_mass_lu: the mass LU factors (full and Dirichlet-reduced) multiply
+  back to M, are symmetric (U = L^T) with positive pivots, and solve like a
+  dense solver;
+* adi_axis_point_basis: the dipole's basis values against the oracle, with the
+  element rule at element boundaries and the partition of unity.
 """
 from fractions import Fraction
 
@@ -154,3 +160,68 @@ def test_invalid_arguments_are_rejected():
         with pytest.raises(adi.AdiError) as e:
             adi.axis_bands(*args)
         assert e.value.status == adi.ADI_EINVAL
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("kind", ["uniform", "graded", "core"])
+@pytest.mark.parametrize("reduced", [False, True])
+def test_mass_lu_reproduces_the_mass_matrix(p, kind, reduced):
+    n = 17
+    br = None if kind == "uniform" else (graded(n) if kind == "graded" else core(n))
+    Lb, inv_d, Ub = _adi().axis_mass_lu(n, p, br, reduced)
+    N = n + p
+    lo, hi = (1, N - 2) if reduced else (0, N - 1)
+    M = bspline.matrices_1d(n, p, breaks=br)[0][lo:hi + 1, lo:hi + 1]
+    m = hi - lo + 1
+    L, U = np.eye(m), np.eye(m)
+    for k in range(lo, hi + 1):
+        for q in range(1, p + 1):
+            if k - q >= lo:
+                L[k - lo, k - q - lo] = Lb[k, q - 1]
+            if k + q <= hi:
+                U[k - lo, k + q - lo] = Ub[k, q - 1]
+    # M is symmetric positive definite: positive pivots, and U = L^T up to rounding
+    assert np.all(inv_d[lo:hi + 1] > 0)
+    np.testing.assert_allclose(U, L.T, rtol=1e-12, atol=1e-14)
+    D = np.diag(1.0 / inv_d[lo:hi + 1])
+    np.testing.assert_allclose(L @ D @ U, M, rtol=0, atol=1e-13 * np.max(np.abs(M)))
+    # rows outside the factorised range stay zero; a solve with the factors matches a dense solve
+    out = [k for k in range(N) if k < lo or k > hi]
+    assert np.all(inv_d[out] == 0) and np.all(Lb[out] == 0) and np.all(Ub[out] == 0)
+    b = np.random.default_rng(5).standard_normal(m)
+    x = np.linalg.solve(U, np.linalg.solve(D, np.linalg.solve(L, b)))
+    np.testing.assert_allclose(x, np.linalg.solve(M, b), rtol=1e-10, atol=1e-12 * np.max(np.abs(x)))
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("kind", ["uniform", "graded"])
+def test_point_basis_equals_the_oracle(p, kind):
+    n = 9 if kind == "graded" else 8  # uniform: dyadic boundaries, exact in binary
+    br = graded(n) if kind == "graded" else None
+    edges = br if br is not None else np.linspace(0.0, 1.0, n + 1)
+    xs = list(np.random.default_rng(11).random(20)) + [0.0, 1.0] + list(edges[1:-1])
+    for x0 in xs:
+        e, vals = _adi().axis_point_basis(n, p, x0, br)
+        ref = bspline.point_values(n, p, x0, breaks=br)
+        full = np.zeros(n + p)
+        full[e:e + p + 1] = vals
+        np.testing.assert_allclose(full, ref, rtol=1e-13, atol=1e-15)
+        # the element holding x0; a boundary point belongs to the element on its right, 1 to the last
+        assert edges[e] <= x0 <= edges[e + 1] and (x0 < edges[e + 1] or e == n - 1)
+        # partition of unity, non-negative values
+        assert abs(vals.sum() - 1.0) < 1e-14 and np.all(vals >= 0)
+
+
+def test_host_axis_calls_reject_invalid_arguments():
+    adi = _adi()
+    for call in (lambda: adi.axis_mass_lu(0, 2), lambda: adi.axis_mass_lu(4, 5),
+                 lambda: adi.axis_mass_lu(3, 2, np.array([0.0, 0.6, 0.5, 1.0])),
+                 lambda: adi.axis_point_basis(4, 2, -0.1), lambda: adi.axis_point_basis(4, 2, 1.5),
+                 lambda: adi.axis_point_basis(4, 2, float("nan")), lambda: adi.axis_point_basis(4, 0, 0.5)):
+        with pytest.raises(adi.AdiError) as e:
+            call()
+        assert e.value.status == adi.ADI_EINVAL
+    L = adi.load_library()
+    z = np.zeros(64)
+    assert L.adi_axis_mass_lu(4, 2, None, 2, adi._dptr(z), adi._dptr(z), adi._dptr(z)) == adi.ADI_EINVAL
+    assert L.adi_axis_mass_lu(4, 2, None, 0, None, adi._dptr(z), adi._dptr(z)) == adi.ADI_EINVAL
