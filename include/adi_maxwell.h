@@ -143,6 +143,18 @@ adi_status adi_create_knots(int nx, int ny, int nz, int p, double dt, const doub
 adi_status adi_axis_bands(int n, int p, const double* breaks, double* M, double* S, double* A, double* B,
                           int* inner);
 
+/* Host only: two further per-axis tables the solver derives from the 1D basis.
+ *  G (host, caller-owned, may be NULL): N (p+1) doubles, G[r (p+1) + a] = the
+ *  integral of B_r over element r - p + a (0 where that element does not
+ *  exist); these weights turn per-element material into per-test-function
+ *  values (see adi_create).
+ *  lam (host, may be NULL): the largest eigenvalue of M_D^{-1} S_D, M and S
+ *  with the first and last basis functions removed; adi_cfl_dt sums it over
+ *  the three axes (the explicit-scheme limit, a reference scale for choosing
+ *  the time step).
+ *  n, p, breaks as adi_axis_bands.  Errors: ADI_EINVAL, ADI_ENOMEM. */
+adi_status adi_axis_tables(int n, int p, const double* breaks, double* G, double* lam);
+
 /* Host only: the LU factors of the 1D mass matrix M of one axis exactly as
  * adi_factor computes them (no pivoting; M is symmetric positive definite),
  * for the full matrix (reduced = 0: rows and columns 0 .. N-1) or the

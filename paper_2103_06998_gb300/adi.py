@@ -18,7 +18,8 @@ PREC_FP64, PREC_FP32, PREC_MIXED = 0, 1, 2
 _PREC = {"fp64": PREC_FP64, "fp32": PREC_FP32, "mixed": PREC_MIXED}
 
 # every symbol declared in include/adi_maxwell.h
-EXPORTS = ("adi_create", "adi_create_knots", "adi_axis_bands", "adi_axis_mass_lu", "adi_axis_point_basis",
+EXPORTS = ("adi_create", "adi_create_knots", "adi_axis_bands", "adi_axis_tables", "adi_axis_mass_lu",
+           "adi_axis_point_basis",
            "adi_factor", "adi_set_dt", "adi_set_stream", "adi_set_fields",
            "adi_set_fields_f32", "adi_set_source", "adi_step", "adi_substep", "adi_fields", "adi_fields_f32",
            "adi_fields_device", "adi_set_fields_async", "adi_fields_async",
@@ -68,6 +69,7 @@ def load_library(path=LIB_PATH):
         "adi_create": (I, [I, I, I, I, D, P(D), P(D), P(D), P(AdiOptions), P(H)]),
         "adi_create_knots": (I, [I, I, I, I, D, P(D), P(D), P(D), P(D), P(D), P(D), P(AdiOptions), P(H)]),
         "adi_axis_bands": (I, [I, I, P(D), P(D), P(D), P(D), P(D), P(I)]),
+        "adi_axis_tables": (I, [I, I, P(D), P(D), P(D)]),
         "adi_axis_mass_lu": (I, [I, I, P(D), I, P(D), P(D), P(D)]),
         "adi_axis_point_basis": (I, [I, I, P(D), D, P(I), P(D)]),
         "adi_factor": (I, [H]),
@@ -153,6 +155,19 @@ def axis_bands(n, p, breaks=None):
 
 def _breaks_arg(breaks):
     return None if breaks is None else np.ascontiguousarray(breaks, dtype=np.float64)
+
+
+def axis_tables(n, p, breaks=None):
+    """adi_axis_tables: (G (N, p+1) element integrals of the basis, largest
+    eigenvalue of the Dirichlet-reduced M^{-1} S)."""
+    L = load_library()
+    G = np.zeros((n + p, p + 1))
+    lam = ctypes.c_double()
+    br = _breaks_arg(breaks)
+    st = L.adi_axis_tables(n, p, None if br is None else _dptr(br), _dptr(G), ctypes.byref(lam))
+    if st != ADI_OK:
+        raise AdiError(st, L.adi_last_error(None).decode())
+    return G, lam.value
 
 
 def axis_mass_lu(n, p, breaks=None, reduced=False):

@@ -381,6 +381,21 @@ adi_status adi_axis_bands(int n, int p, const double* breaks, double* M, double*
   return ADI_OK;
 }
 
+adi_status adi_axis_tables(int n, int p, const double* breaks, double* G, double* lam) {
+  adi::Axis1D ax;
+  adi_status st = host_axis(n, p, breaks, "adi_axis_tables", ax);
+  if (st != ADI_OK) return st;
+  if (G) std::copy(ax.G.begin(), ax.G.end(), G);
+  if (lam) {
+    try {
+      *lam = adi::lambda_max(ax);
+    } catch (const std::bad_alloc&) {
+      return fail(nullptr, ADI_ENOMEM, "adi_axis_tables: host allocation failed");
+    }
+  }
+  return ADI_OK;
+}
+
 adi_status adi_axis_mass_lu(int n, int p, const double* breaks, int reduced, double* L, double* inv_d, double* U) {
   if (reduced != 0 && reduced != 1) return fail(nullptr, ADI_EINVAL, "adi_axis_mass_lu: reduced must be 0 or 1");
   if (!L || !inv_d || !U) return fail(nullptr, ADI_EINVAL, "adi_axis_mass_lu: NULL output");

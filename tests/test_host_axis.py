@@ -5,6 +5,10 @@ non-uniform elements:
   oracle's dense matrices, the closed-form interior stencils of cardinal
   B-splines, the symmetry B = A^T, and the interior rows the kernels replace by
   one constant stencil;
+* adi_axis_tables: the element integrals of the basis (material weights)
+  against the oracle, and the largest Dirichlet-reduced eigenvalue of M^{-1} S
+  against the oracle's generalised eigensolver and the closed form for linear
+  elements;
 * adi_axis_mass_lu: the mass LU factors (full and Dirichlet-reduced) multiply
   back to M, are symmetric (U = L^T) with positive pivots, and solve like a
   dense solver;
@@ -225,3 +229,31 @@ def test_host_axis_calls_reject_invalid_arguments():
     z = np.zeros(64)
     assert L.adi_axis_mass_lu(4, 2, None, 2, adi._dptr(z), adi._dptr(z), adi._dptr(z)) == adi.ADI_EINVAL
     assert L.adi_axis_mass_lu(4, 2, None, 0, None, adi._dptr(z), adi._dptr(z)) == adi.ADI_EINVAL
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("kind", ["uniform", "graded", "core"])
+def test_element_integrals_and_lambda_max_equal_the_oracle(p, kind):
+    from oracle import material
+    n = 14
+    br = None if kind == "uniform" else (graded(n) if kind == "graded" else core(n))
+    G, lam = _adi().axis_tables(n, p, br)
+    ref = bspline.element_integrals(n, p, breaks=br)  # (N, n): integral of B_r over element e
+    N = n + p
+    for r in range(N):
+        for a in range(p + 1):
+            e = r - p + a
+            assert G[r, a] == pytest.approx(ref[r, e] if 0 <= e < n else 0.0, rel=1e-13, abs=1e-16)
+    # each basis function's integrals over its elements sum to its integral, and all of them to 1
+    assert G.sum() == pytest.approx(1.0, rel=1e-13)
+    assert lam == pytest.approx(material.lambda_max(n, p, br), rel=1e-10)
+
+
+def test_lambda_max_of_linear_elements_is_the_closed_form():
+    # p = 1, uniform: M_D^{-1} S_D has the eigenvalues (6/h^2)(1 - cos t)/(2 + cos t),
+    # t = k pi / n, k = 1 .. n-1 (the tridiagonal stencils h/6 [1 4 1] and 1/h [-1 2 -1])
+    for n in (4, 9, 20):
+        h = 1.0 / n
+        t = np.arange(1, n) * np.pi / n
+        exact = np.max(6.0 / h ** 2 * (1 - np.cos(t)) / (2 + np.cos(t)))
+        assert _adi().axis_tables(n, 1)[1] == pytest.approx(exact, rel=1e-12)
