@@ -186,13 +186,21 @@ def job_rate(local_s, units, world, device=None):
     return float(u.item()) / s, s
 
 
+def l2_note(n, esize=4):
+    """How the L2 is handled: the working set of the step (six field and four
+    row-coefficient arrays) against the 129 MB L2."""
+    ws = 10 * (n + P) ** 3 * esize
+    if ws > 129e6:
+        return "working set %.2f GB > 129 MB L2 (no flush needed)" % (ws / 1e9)
+    return "working set %.0f MB fits in the 129 MB L2 (not flushed: small-case timing only)" % (ws / 1e6)
+
+
 def config_of(n, tau, world):
     """The workload description shared by both arms (tau printed to 12 digits:
     each arm computes the explicit limit in its own code)."""
     return {"workload": "ADI IGA Maxwell step, %d^3 elements, p=%d, head-like 3-phase map seed %d, "
                         "dipole, tau=4 dt_CFL" % (n, P, SEED), "n": n, "p": P, "tau": float("%.12g" % tau),
-            "l2": "working set 0.7 GB >> 129 MB L2 (no flush needed)",
-            "parallelism": "replicas" if world > 1 else "single GPU"}
+            "l2": l2_note(n), "parallelism": "replicas" if world > 1 else "single GPU"}
 
 
 def run_reference(args, rank, world):

@@ -32,3 +32,25 @@ def test_corrector_weights_roundtrip(tmp_path):
     # their padding entries are zero (layer 0 ci >= 9, layer 3 co >= 6)
     real = adi.net_flatten([(np.ones((3, 3, 3, ci, co)), np.ones(co)) for ci, co in adi.NET_REAL]) != 0
     assert np.all(w[~real] == 0.0)
+
+
+def test_reference_arm_prints_the_contract_line():
+    # the oracle arm of bench.py on a small case: one JSON line with the keys
+    # of the main arm's line, the same config keys, and its own e2e/cpu_baseline
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--n", "12",
+                        "--steps", "1", "--warmup", "1"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 1 and d["warmup"] == 1
+    assert set(d["config"]) == {"workload", "n", "p", "tau", "l2", "parallelism"} and d["config"]["n"] == 12
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert "fits in the 129 MB L2" in d["config"]["l2"]
