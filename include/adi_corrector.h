@@ -6,7 +6,7 @@
  * on top of its method.  One ADI step of length k*tau (a "coarse" step, k = 8
  * by default) is followed by a 3D convolution net that predicts the difference
  * between k steps of length tau and that one step, both started from the same
- * state.  The plain ADI step stays the fallback and the judge of the error.
+ * state.  The plain ADI step stays the fallback and the reference for the error.
  *
  * Net (fixed architecture): four 3x3x3 convolutions with zero padding on the
  * coefficient grid (N_x x N_y x N_z voxels, one voxel per B-spline
