@@ -155,6 +155,16 @@ adi_status adi_axis_bands(int n, int p, const double* breaks, double* M, double*
  *  n, p, breaks as adi_axis_bands.  Errors: ADI_EINVAL, ADI_ENOMEM. */
 adi_status adi_axis_tables(int n, int p, const double* breaks, double* G, double* lam);
 
+/* Host only: the per-element blocks of the 1D matrices of one axis, which the
+ * right-hand side with per-element material inside the integrals
+ * (ADI_RHS_QUAD) contracts element by element:
+ *  loc[((e 4 + op) (p+1) + a) (p+1) + b] = the integral over element e of the
+ *  op's integrand (op 0..3: M, S, A, B as in adi_axis_bands) for test function
+ *  e + a and trial function e + b; the bands are the sums of these blocks.
+ *  n, p, breaks as adi_axis_bands; loc (host, caller-owned): 4 n (p+1)^2
+ *  doubles.  Errors: ADI_EINVAL, ADI_ENOMEM. */
+adi_status adi_axis_element_matrices(int n, int p, const double* breaks, double* loc);
+
 /* Host only: the LU factors of the 1D mass matrix M of one axis exactly as
  * adi_factor computes them (no pivoting; M is symmetric positive definite),
  * for the full matrix (reduced = 0: rows and columns 0 .. N-1) or the

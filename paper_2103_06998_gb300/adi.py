@@ -18,8 +18,8 @@ PREC_FP64, PREC_FP32, PREC_MIXED = 0, 1, 2
 _PREC = {"fp64": PREC_FP64, "fp32": PREC_FP32, "mixed": PREC_MIXED}
 
 # every symbol declared in include/adi_maxwell.h
-EXPORTS = ("adi_create", "adi_create_knots", "adi_axis_bands", "adi_axis_tables", "adi_axis_mass_lu",
-           "adi_axis_point_basis",
+EXPORTS = ("adi_create", "adi_create_knots", "adi_axis_bands", "adi_axis_tables", "adi_axis_element_matrices",
+           "adi_axis_mass_lu", "adi_axis_point_basis",
            "adi_factor", "adi_set_dt", "adi_set_stream", "adi_set_fields",
            "adi_set_fields_f32", "adi_set_source", "adi_step", "adi_substep", "adi_fields", "adi_fields_f32",
            "adi_fields_device", "adi_set_fields_async", "adi_fields_async",
@@ -70,6 +70,7 @@ def load_library(path=LIB_PATH):
         "adi_create_knots": (I, [I, I, I, I, D, P(D), P(D), P(D), P(D), P(D), P(D), P(AdiOptions), P(H)]),
         "adi_axis_bands": (I, [I, I, P(D), P(D), P(D), P(D), P(D), P(I)]),
         "adi_axis_tables": (I, [I, I, P(D), P(D), P(D)]),
+        "adi_axis_element_matrices": (I, [I, I, P(D), P(D)]),
         "adi_axis_mass_lu": (I, [I, I, P(D), I, P(D), P(D), P(D)]),
         "adi_axis_point_basis": (I, [I, I, P(D), D, P(I), P(D)]),
         "adi_factor": (I, [H]),
@@ -168,6 +169,17 @@ def axis_tables(n, p, breaks=None):
     if st != ADI_OK:
         raise AdiError(st, L.adi_last_error(None).decode())
     return G, lam.value
+
+
+def axis_element_matrices(n, p, breaks=None):
+    """adi_axis_element_matrices: (n, 4, p+1, p+1) blocks [element][M, S, A, B][test][trial]."""
+    L = load_library()
+    loc = np.zeros((n, 4, p + 1, p + 1))
+    br = _breaks_arg(breaks)
+    st = L.adi_axis_element_matrices(n, p, None if br is None else _dptr(br), _dptr(loc))
+    if st != ADI_OK:
+        raise AdiError(st, L.adi_last_error(None).decode())
+    return loc
 
 
 def axis_mass_lu(n, p, breaks=None, reduced=False):

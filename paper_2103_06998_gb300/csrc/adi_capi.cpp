@@ -396,6 +396,21 @@ adi_status adi_axis_tables(int n, int p, const double* breaks, double* G, double
   return ADI_OK;
 }
 
+adi_status adi_axis_element_matrices(int n, int p, const double* breaks, double* loc) {
+  if (!loc) return fail(nullptr, ADI_EINVAL, "adi_axis_element_matrices: NULL output");
+  adi::Axis1D ax;
+  adi_status st = host_axis(n, p, breaks, "adi_axis_element_matrices", ax);
+  if (st != ADI_OK) return st;
+  std::vector<double> blocks;
+  try {
+    adi::element_matrices(ax, blocks);
+  } catch (const std::bad_alloc&) {
+    return fail(nullptr, ADI_ENOMEM, "adi_axis_element_matrices: host allocation failed");
+  }
+  std::copy(blocks.begin(), blocks.end(), loc);
+  return ADI_OK;
+}
+
 adi_status adi_axis_mass_lu(int n, int p, const double* breaks, int reduced, double* L, double* inv_d, double* U) {
   if (reduced != 0 && reduced != 1) return fail(nullptr, ADI_EINVAL, "adi_axis_mass_lu: reduced must be 0 or 1");
   if (!L || !inv_d || !U) return fail(nullptr, ADI_EINVAL, "adi_axis_mass_lu: NULL output");

@@ -9,6 +9,8 @@ non-uniform elements:
   against the oracle, and the largest Dirichlet-reduced eigenvalue of M^{-1} S
   against the oracle's generalised eigensolver and the closed form for linear
   elements;
+* adi_axis_element_matrices: the per-element blocks of the quad right-hand
+  side against the oracle's quadrature on each element, summing to the bands;
 * adi_axis_mass_lu: the mass LU factors (full and Dirichlet-reduced) multiply
   back to M, are symmetric (U = L^T) with positive pivots, and solve like a
   dense solver;
@@ -257,3 +259,26 @@ def test_lambda_max_of_linear_elements_is_the_closed_form():
         t = np.arange(1, n) * np.pi / n
         exact = np.max(6.0 / h ** 2 * (1 - np.cos(t)) / (2 + np.cos(t)))
         assert _adi().axis_tables(n, 1)[1] == pytest.approx(exact, rel=1e-12)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("kind", ["uniform", "graded"])
+def test_element_blocks_equal_the_oracle_and_sum_to_the_bands(p, kind):
+    n = 11
+    br = graded(n) if kind == "graded" else None
+    loc = _adi().axis_element_matrices(n, p, br)
+    x, w, elem = bspline.gauss_points(n, p + 1, br)
+    v, d = bspline.eval_basis(n, p, x, elem, br)
+    N = n + p
+    dense = np.zeros((4, N, N))
+    for e in range(n):
+        q = elem == e
+        fa = {0: v, 1: d, 2: v, 3: d}  # test-function factor of M, S, A, B
+        fb = {0: v, 1: d, 2: d, 3: v}  # trial-function factor
+        for op in range(4):
+            ref = (fa[op][q][:, e:e + p + 1] * w[q][:, None]).T @ fb[op][q][:, e:e + p + 1]
+            np.testing.assert_allclose(loc[e, op], ref, rtol=1e-13, atol=1e-14 * np.max(np.abs(ref)))
+            dense[op, e:e + p + 1, e:e + p + 1] += loc[e, op]
+    # summed over the elements the blocks give the matrices of the bands
+    for op, X in enumerate(bspline.matrices_1d(n, p, breaks=br)):
+        np.testing.assert_allclose(dense[op], X, rtol=0, atol=1e-13 * np.max(np.abs(X)))
