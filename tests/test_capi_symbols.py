@@ -84,3 +84,17 @@ def test_net_parameter_vector_layout():
     # weight of layer 0, tap (dz, dy, dx) = (1, 2, 0), ci 3, co 7 sits at
     # (9 + 6 + 0) * 16 * 32 + 3 * 32 + 7
     assert flat[15 * 16 * 32 + 3 * 32 + 7] == np.float32(ps[0][0][1, 2, 0, 3, 7])
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    # the binding has no CPU fallback: without the built library every entry point raises
+    from paper_2103_06998_gb300 import adi
+    monkeypatch.setattr(adi, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        adi.load_library(str(tmp_path / "libadi_maxwell.so"))
+    monkeypatch.setattr(adi, "LIB_PATH", str(tmp_path / "libadi_maxwell.so"))
+    monkeypatch.setattr(adi.load_library, "__defaults__", (str(tmp_path / "libadi_maxwell.so"),))
+    with pytest.raises(RuntimeError, match="not built"):
+        adi.axis_bands(4, 2)
+    with pytest.raises(RuntimeError, match="not built"):
+        adi.Solver((4, 4, 4), 2, 0.01)
