@@ -31,6 +31,13 @@
  *   outputs   Y: FP32 [z][y][x][8]
  * All calls are asynchronous on the net's stream unless they return host data.
  *
+ * Errors common to these calls: ADI_EINVAL for a NULL net or handle, a NULL or
+ * misaligned array, a handle that is not FP32 or whose grid differs from the
+ * net's, or an argument outside its documented range; ADI_ECUDA when a CUDA
+ * call fails (ADI_ENOMEM for an allocation).  Messages: adi_net_last_error(n)
+ * (adi_net_last_error(NULL) for a failed create or a NULL net).  Calls that
+ * step a handle pass its status through (message in adi_last_error(h)).
+ *
  * Parameter vector (FP32, ADI_NET_PARAMS floats): for layer l = 0..3 the
  * weights w_l[27][CI_l][CO_l] then the bias b_l[CO_l], with the padded channel
  * counts CI = (16, 32, 32, 32), CO = (32, 32, 32, 16); the padding entries
@@ -55,12 +62,14 @@ adi_status adi_net_create(int Nx, int Ny, int Nz, adi_net* out);
 /* Issue the net's work on `stream` (a cudaStream_t; NULL: the net's own). */
 adi_status adi_net_set_stream(adi_net n, void* stream);
 /* Copy the FP32 parameter vector from / to the host (count must be
- * ADI_NET_PARAMS); setting resets the Adam moments and step counter. */
+ * ADI_NET_PARAMS); setting resets the Adam moments and step counter.
+ * adi_net_set_params: ADI_ENUMERIC if w holds a NaN or Inf (nothing set). */
 adi_status adi_net_set_params(adi_net n, const float* w, size_t count);
 adi_status adi_net_get_params(adi_net n, float* w, size_t count);
 
 /* X = features of the fields of FP32 handle h (same grid as the net); the
- * scale s is kept on the device for adi_net_target and adi_net_apply. */
+ * scale s is kept on the device for adi_net_target and adi_net_apply.
+ * ADI_ESTATE if h is not factored (its row coefficients are not final). */
 adi_status adi_net_features(adi_net n, adi_handle h, void* X);
 /* T = (fields(fine) - fields(coarse)) / s, s from the last adi_net_features. */
 adi_status adi_net_target(adi_net n, adi_handle fine, adi_handle coarse, float* T);
@@ -72,7 +81,7 @@ adi_status adi_net_apply(adi_net n, adi_handle h, const float* Y);
 /* One training step on one sample: forward, mean squared error against T,
  * backward, Adam (Kingma and Ba) with learning rate lr, betas 0.9 / 0.999,
  * eps 1e-8.  The loss of the sample is accumulated on the device; read (and
- * reset) the running sum with adi_net_loss. */
+ * reset) the running sum with adi_net_loss.  lr must be finite and > 0. */
 adi_status adi_net_train_step(adi_net n, const void* X, const float* T, float lr);
 /* Gradient of the loss of one sample without updating (for checks):
  * grad receives ADI_NET_PARAMS floats, *loss the loss.  Synchronises. */
@@ -95,7 +104,9 @@ adi_status adi_copy_state(adi_handle dst, adi_handle src);
  * their relative l2 distance exceeds tol, the fine result is kept and the rest
  * of the window runs as plain fine steps (counted in *n_fallback), else the
  * rest of the window runs corrected coarse steps.  m coarse steps in all.
- * *max_err receives the largest guard distance.  Synchronises at each guard. */
+ * *max_err receives the largest guard distance.  Synchronises at each guard.
+ * ADI_EINVAL unless m, k, guard_every >= 1, tol > 0, the output pointers are
+ * set and coarse's time step is k times fine's. */
 adi_status adi_corrector_run(adi_net n, adi_handle coarse, adi_handle fine, int m, int k,
                              int guard_every, double tol, int* n_fallback, double* max_err);
 

@@ -24,10 +24,17 @@
  *    components are ordered E1, E2, E3, H1, H2, H3.
  *  - Per-element material arrays are [z][y][x] with n_x n_y n_z entries.
  *  - The caller owns every host pointer; the library copies what it needs and
- *    keeps no caller pointer after a call returns.
+ *    keeps no caller pointer after a call returns, except the host buffers of
+ *    the asynchronous transfers (adi_set_fields_async, adi_fields_async), which
+ *    stay in use until adi_sync returns.
  *  - A handle owns all device memory it allocates; adi_destroy frees it.
  *  - No call aborts or throws.  Failures return a status other than ADI_OK and
- *    set a message readable with adi_last_error(h).
+ *    set a message readable with adi_last_error(h) (adi_last_error(NULL) for
+ *    calls without a handle, a NULL handle, or a failed create).
+ *  - Errors common to the calls that take a handle: ADI_EINVAL for a NULL
+ *    handle or an argument outside its documented range (the message names
+ *    it), ADI_ECUDA when a CUDA call fails (ADI_ENOMEM when it is an
+ *    allocation).  Each call lists the others it can return.
  *  - Work is issued on the handle's CUDA stream (adi_set_stream; default: the
  *    library's own non-blocking stream).  Calls that return host data
  *    synchronise that stream.
@@ -186,19 +193,22 @@ adi_status adi_axis_mass_lu(int n, int p, const double* breaks, int reduced, dou
  * Errors: ADI_EINVAL (also x0 outside [0, 1]), ADI_ENOMEM. */
 adi_status adi_axis_point_basis(int n, int p, const double* breaks, double x0, int* first, double* vals);
 
-/* Build the 1D matrices M, S, A (B = A^T) of every axis by Gauss-Legendre
- * quadrature in FP64 (definitions after eq. discrete4), factor the mass
- * matrices (full and Dirichlet-reduced) without pivoting, and upload the
- * factors in the working precision.  Must precede adi_step (else ADI_ESTATE). */
+/* Factor the mass matrices of every axis (full and Dirichlet-reduced, without
+ * pivoting, in FP64) from the 1D matrices M, S, A (B = A^T) that adi_create
+ * built by Gauss-Legendre quadrature in FP64 (definitions after eq.
+ * discrete4), and upload the bands and factors in the working precision.
+ * Must precede adi_step (else ADI_ESTATE).  Errors: ADI_ECUDA, ADI_ENOMEM. */
 adi_status adi_factor(adi_handle h);
 
 /* Change the time step; the row coefficients are rebuilt and adi_factor must
- * be called again before the next adi_step. */
+ * be called again before the next adi_step (else ADI_ESTATE).
+ * Errors: ADI_EINVAL (dt not finite and > 0). */
 adi_status adi_set_dt(adi_handle h, double dt);
 
-/* Use the given cudaStream_t (NULL = legacy default stream) for all later work.
- * On the legacy default stream adi_step cannot capture a CUDA graph and issues
- * the kernels one by one. */
+/* Use the given cudaStream_t (NULL = legacy default stream; not owned) for all
+ * later work.  Synchronises the current stream and the asynchronous-transfer
+ * streams first.  On the legacy default stream adi_step cannot capture a CUDA
+ * graph and issues the kernels one by one. */
 adi_status adi_set_stream(adi_handle h, void* cuda_stream);
 
 /* Copy 6 N_c doubles (host) into the state and set the time to t.  The
@@ -214,17 +224,20 @@ adi_status adi_set_fields(adi_handle h, const double* EH, double t);
 /* Point dipole J = amp g(t) delta(x - x0) e_comp (comp 0, 1, 2 = E1, E2, E3),
  * g(t) = sin(2 pi f0 (t - t0)) exp(-((t - t0)/s)^2).  Enters the E rows as
  * -b (J, B_rst) at the mid time of each half step.  Not part of the paper's
- * equations.  amp = 0 removes the source.  x0 must lie in [0,1]^3. */
+ * equations.  amp = 0 removes the source.  Errors: ADI_EINVAL (x0 outside
+ * [0,1]^3, comp not 0..2, amp, f0 or t0 not finite, s not > 0). */
 adi_status adi_set_source(adi_handle h, double x0, double y0, double z0, int comp,
                           double amp, double f0, double t0, double s);
 
 /* Advance n >= 1 full time steps (eqs. scheme1a-1d: E half step 1, H half step
- * 1, E half step 2, H half step 2).  Asynchronous on the handle's stream. */
+ * 1, E half step 2, H half step 2).  Asynchronous on the handle's stream.
+ * Errors: ADI_EINVAL (n < 1), ADI_ESTATE (before adi_factor). */
 adi_status adi_step(adi_handle h, int n);
 
 /* Run one sub-solve only: which = 0 (E, half step 1), 1 (H, half step 1),
  * 2 (E, half step 2), 3 (H, half step 2, also advances the time by tau).
- * Four calls in order equal one adi_step.  For testing. */
+ * Four calls in order equal one adi_step.  For testing.  Errors: ADI_EINVAL
+ * (which outside 0..3), ADI_ESTATE (before adi_factor). */
 adi_status adi_substep(adi_handle h, int which);
 
 /* Copy the state to 6 N_c host doubles (working precision widened) and the
@@ -270,8 +283,10 @@ adi_status adi_set_fields_async(adi_handle h, const void* EH, int elem_bytes, do
 adi_status adi_fields_async(adi_handle h, void* EH, int elem_bytes);
 
 /* Copy the state, in the working precision (float or double as created), to
- * 6 N_c elements of device memory at dev_ptr, on cuda_stream (NULL = the
- * handle's stream).  Asynchronous. */
+ * 6 N_c elements of device memory at dev_ptr (caller-owned, the dense layout
+ * of adi_set_fields), on cuda_stream (NULL = the handle's stream; another
+ * stream first waits, on the host, for the handle's stream).  Asynchronous.
+ * Errors: ADI_EINVAL (dev_ptr NULL). */
 adi_status adi_fields_device(adi_handle h, void* dev_ptr, void* cuda_stream);
 
 /* Norms of the current state as functions on the unit cube: the paper plots the
@@ -337,7 +352,8 @@ adi_status adi_cfl_dt_noalloc(int nx, int ny, int nz, int p, const double* d_eps
 /* Lines per CTA of the line-solve kernels: 8, 16, 32 or 64, or 0 for the
  * default (the largest that leaves room for two CTAs per SM).  A width whose
  * shared memory does not fit falls back to the default.  Used by the
- * autotuner of the batched mode; results do not depend on it. */
+ * autotuner of the batched mode; results do not depend on it.  Errors:
+ * ADI_EINVAL (another width). */
 adi_status adi_set_line_tile(adi_handle h, int lines);
 
 /* ---------------------------------------------------------------- batches
@@ -349,7 +365,10 @@ adi_status adi_set_line_tile(adi_handle h, int lines);
  * is captured once as a CUDA graph whose branches are the instances' sub-step
  * kernels on their own streams (forked from and joined to the batch stream),
  * so the GPU runs small instances concurrently; the graph is replayed n times.
- * Results equal those of each instance stepped alone, bit for bit. */
+ * Results equal those of each instance stepped alone, bit for bit.  Batch
+ * calls report failures in adi_last_error(NULL) (a NULL batch is ADI_EINVAL);
+ * a failing instance call passes its status through, with the instance's
+ * message. */
 typedef struct adi_batch_ctx* adi_batch;
 typedef struct {
   int nx, ny, nz, p; /* as adi_create */
@@ -362,20 +381,28 @@ typedef struct {
 /* Create count >= 1 instances (adi_create each, same options).  On failure
  * nothing is kept and the message is in adi_last_error(NULL). */
 adi_status adi_batch_create(int count, const adi_instance_desc* desc, const adi_options* opt, adi_batch* out);
-/* The handle of instance i (owned by the batch: do not destroy it). */
+/* The handle of instance i (owned by the batch: do not destroy it).
+ * Errors: ADI_EINVAL (i outside 0 .. count-1, h NULL). */
 adi_status adi_batch_handle(adi_batch b, int i, adi_handle* h);
 /* Run the batch on the given cudaStream_t (not owned; NULL = the batch's own stream). */
 adi_status adi_batch_set_stream(adi_batch b, void* cuda_stream);
 /* adi_factor of every instance. */
 adi_status adi_batch_factor(adi_batch b);
-/* Advance every instance by n >= 1 steps (asynchronous on the batch stream). */
+/* Advance every instance by n >= 1 steps (asynchronous on the batch stream;
+ * the instances' own streams are synchronised first and later calls on an
+ * instance are ordered after the batch).  Errors: ADI_EINVAL (n < 1),
+ * ADI_ESTATE (an instance not factored), ADI_ECUDA. */
 adi_status adi_batch_step(adi_batch b, int n);
-/* Block until the batch stream is idle; ADI_ETIMEOUT if a bounded device wait gave up. */
+/* Block until the batch stream and every instance are idle (adi_sync of each
+ * instance): ADI_ETIMEOUT if a bounded device wait gave up, ADI_ENUMERIC as
+ * adi_sync, ADI_ECUDA. */
 adi_status adi_batch_sync(adi_batch b);
 /* Pick the line-tile width of every instance by timed trials (8..64 lines,
  * three steps each, on the instance alone) unless cache_path (may be NULL)
  * already holds a choice for its (p, N_x, N_y, N_z, precision); new choices
- * are appended to cache_path.  The fields are restored afterwards. */
+ * are appended to cache_path.  The fields are restored afterwards.
+ * Errors: ADI_ESTATE (an instance not factored), and those of adi_fields,
+ * adi_set_fields and adi_step on an instance. */
 adi_status adi_batch_autotune(adi_batch b, const char* cache_path);
 /* Release the batch and all its instances.  NULL is ignored. */
 void adi_batch_destroy(adi_batch b);
@@ -413,7 +440,8 @@ typedef struct {
 adi_status adi_set_profiling(adi_handle h, int on);
 adi_status adi_kernel_stats(adi_handle h, adi_kernel_stat* out, int max, int* count);
 
-/* Sizes: N_x, N_y, N_z, and bytes of one working-precision element. */
+/* Sizes: N_x, N_y, N_z, and bytes of one working-precision element (host
+ * ints, any may be NULL).  Errors: ADI_EINVAL (NULL handle). */
 adi_status adi_dims(adi_handle h, int* Nx, int* Ny, int* Nz, int* elem_bytes);
 
 /* Release everything owned by h.  NULL is ignored. */
