@@ -31,10 +31,11 @@
  *   outputs   Y: FP32 [z][y][x][8]
  * All calls are asynchronous on the net's stream unless they return host data.
  *
- * Errors common to these calls: ADI_EINVAL for a NULL net or handle, a NULL or
- * misaligned array, a handle that is not FP32 or whose grid differs from the
- * net's, or an argument outside its documented range; ADI_ECUDA when a CUDA
- * call fails (ADI_ENOMEM for an allocation).  Messages: adi_net_last_error(n)
+ * Errors common to these calls: ADI_EINVAL for a NULL net, handle or array, a
+ * misaligned array, handles that do not fit (the net's calls and
+ * adi_fields_distance want FP32 handles on the same grid; adi_copy_state wants
+ * the same grid, degree and precision), or an argument outside its documented
+ * range; ADI_ECUDA when a CUDA call fails (ADI_ENOMEM for an allocation).  Messages: adi_net_last_error(n)
  * (adi_net_last_error(NULL) for a failed create or a NULL net).  Calls that
  * step a handle pass its status through (message in adi_last_error(h)).
  *
