@@ -54,3 +54,22 @@ def test_reference_arm_prints_the_contract_line():
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert "fits in the 129 MB L2" in d["config"]["l2"]
+
+
+def test_clock_summary_parses_samples_and_throttle_reasons():
+    # the bench's clock record from nvidia-smi CSV rows (no GPU: rows written by hand)
+    import bench
+    c = bench.ClockSampler(0)
+    rows = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+            "0, 2040, 2070, 1200.5, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "garbage line", "0, [N/A], 2070, 1, 0x0, a, b, c, d"]
+    c.f.write("\n".join(rows) + "\n")
+    s = c.summary()
+    assert s["samples"] == 3 and s["sm_mhz"] == 2040 and s["sm_max_mhz"] == 2070
+    assert s["reasons"] == ["sw_power_cap"]
+    c2 = bench.ClockSampler(0)
+    c2.f.write("0, 1500, 2070, 1400, 0x8, Active, Not Active, Active, Not Active\n")
+    assert c2.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    c3 = bench.ClockSampler(0)
+    assert c3.summary()["reasons"] == ["nvidia-smi unavailable"]
